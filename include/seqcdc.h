@@ -1,0 +1,158 @@
+/*
+ * seqcdc.h -- C ABI of the GB300 (sm_103a) SeqCDC chunker.
+ *
+ * SeqCDC (Udayashankar & Al-Kiswany, "Vectorized Sequence-Based Chunking for
+ * Data Deduplication") is a content-defined chunking method.  A chunk boundary
+ * is placed right after a run of SeqLength strictly increasing (or strictly
+ * decreasing) bytes, Sec. III.A.  The first min_size - SeqLength bytes of
+ * every chunk are not scanned, Sec. III.B.  Once SkipTrigger byte pairs in the
+ * opposite order have been seen, the next SkipSize bytes are skipped,
+ * Sec. III.C.  A chunk is cut at max_size when no run completes first,
+ * Sec. IV and Sec. VI.  This library computes exactly the boundary list a
+ * sequential scan produces, with CUDA kernels over device-resident bytes.
+ *
+ * Conventions for every entry point:
+ *   - "d_" pointers are CUDA device pointers (or managed memory) that the
+ *     caller allocated and owns.  The library never allocates, never frees
+ *     and never synchronises the stream, except seqcdc_status() (which
+ *     synchronises on purpose).  All work is enqueued on `stream` (a
+ *     cudaStream_t passed as void*; NULL = the legacy default stream).
+ *   - Input bytes are read-only.  `d_in` / `d_data` must be 16-byte aligned.
+ *   - Output cut lists hold chunk END offsets: exclusive, strictly
+ *     increasing, the last one equal to the input length.  There is no
+ *     leading 0.  Empty input gives an empty list.
+ *   - Return values are seqcdc status codes (SEQCDC_OK == 0).  Argument
+ *     errors are detected on the host before anything is enqueued.  Errors
+ *     that only the device can see (a bounded wait that expired) are
+ *     recorded in a status word inside the workspace; read it with
+ *     seqcdc_status().
+ */
+#ifndef SEQCDC_H
+#define SEQCDC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+#define SEQCDC_OK         0
+#define SEQCDC_EINVAL     1  /* bad parameter set, NULL or misaligned pointer */
+#define SEQCDC_ECAPACITY  2  /* output capacity or workspace too small         */
+#define SEQCDC_ECUDA      3  /* a CUDA runtime call failed                     */
+#define SEQCDC_ETIMEOUT   4  /* a bounded device-side wait expired             */
+#define SEQCDC_ERANGE     5  /* input larger than the library supports         */
+
+#define SEQCDC_MODE_INCREASING 0u
+#define SEQCDC_MODE_DECREASING 1u
+
+/*
+ * Parameter set of Sec. III (modes, SeqLength, SkipTrigger, SkipSize) and the
+ * minimum / maximum chunk sizes of Sec. VI.
+ *   mode          SEQCDC_MODE_INCREASING or SEQCDC_MODE_DECREASING (Sec. III.A:
+ *                 the two modes are exclusive).
+ *   seq_length    run length in BYTES (SeqLength); 2..16.  A run of
+ *                 seq_length bytes has seq_length-1 strictly ordered pairs.
+ *   skip_trigger  number of opposing-order pairs that fires a skip
+ *                 (Sec. III.C); 0 disables skipping (the "BASE" variant of
+ *                 Sec. VI.D).
+ *   skip_size     bytes ignored after a skip fires (Sec. III.C).
+ *   min_size      minimum chunk size, >= 1 (Sec. III.B).
+ *   max_size      maximum chunk size, >= min_size and <= 2^24.
+ */
+typedef struct {
+    uint32_t mode;
+    uint32_t seq_length;
+    uint32_t skip_trigger;
+    uint32_t skip_size;
+    uint64_t min_size;
+    uint64_t max_size;
+} seqcdc_params_t;
+
+/*
+ * Launch tuning (all fields 0 = library default).
+ *   segment_bytes  bytes of input one thread block owns (multiple of 1024,
+ *                  >= 4096).  Larger segments mean fewer junctions but more
+ *                  shared memory.
+ *   block_threads  threads per block of the segment kernel (128, 256, 512).
+ */
+typedef struct {
+    uint32_t segment_bytes;
+    uint32_t block_threads;
+} seqcdc_tuning_t;
+
+/*
+ * Fill *out with the paper's parameters for an expected average chunk size
+ * of 4, 8 or 16 KB (Table I for SeqLength / SkipTrigger / SkipSize; Sec. VI
+ * for min = 1/2x and max = 2x the expected size, except a 1 KB minimum for
+ * 4 KB).  KB = 1024 bytes.  Returns SEQCDC_EINVAL for any other size, a mode
+ * other than the two defined ones, or a NULL out.
+ */
+int seqcdc_params(uint32_t expected_kib, uint32_t mode, seqcdc_params_t *out);
+
+/* SEQCDC_OK if *p is a parameter set this library accepts, else SEQCDC_EINVAL. */
+int seqcdc_validate(const seqcdc_params_t *p);
+
+/*
+ * Bytes of device workspace seqcdc_chunk_batch() needs for `nfiles` files
+ * holding `total_bytes` bytes in all (seqcdc_chunk(): nfiles = 1).  Returns 0
+ * for an invalid parameter set.  `tuning` may be NULL.
+ */
+size_t seqcdc_workspace_size(const seqcdc_params_t *p, uint64_t total_bytes,
+                             uint64_t nfiles, const seqcdc_tuning_t *tuning);
+
+/*
+ * Chunk one byte stream d_in[0..n).
+ *   d_cuts   out: up to `cap` uint64 chunk end offsets.
+ *   cap      capacity of d_cuts in entries; must be >= n / min_size + 1
+ *            (always sufficient), else SEQCDC_ECAPACITY.
+ *   d_count  out: one uint64, the number of cuts written.
+ *   d_ws     workspace of >= seqcdc_workspace_size(p, n, 1, tuning) bytes,
+ *            256-byte aligned; its contents need no initialisation.  Two
+ *            calls in flight at once must use different workspaces.
+ * Asynchronous on `stream`.
+ */
+int seqcdc_chunk(const seqcdc_params_t *p, const uint8_t *d_in, uint64_t n,
+                 uint64_t *d_cuts, uint64_t cap, uint64_t *d_count,
+                 void *d_ws, size_t ws_bytes, const seqcdc_tuning_t *tuning,
+                 void *stream);
+
+/*
+ * Chunk a batch of files laid out back to back in d_data[0..total_bytes).
+ *   d_offsets      nfiles+1 uint64 on the device: file f is
+ *                  d_data[d_offsets[f] .. d_offsets[f+1]); d_offsets[0] == 0,
+ *                  non-decreasing, d_offsets[nfiles] == total_bytes.
+ *   d_cuts         out: cut lists of all files, file after file; the cuts of
+ *                  a file are relative to the file's start.
+ *   cap            capacity of d_cuts; must be >= total_bytes / min_size +
+ *                  nfiles (always sufficient), else SEQCDC_ECAPACITY.
+ *   d_cut_offsets  out: nfiles+1 uint64, a CSR index: the cuts of file f are
+ *                  d_cuts[d_cut_offsets[f] .. d_cut_offsets[f+1]).
+ *   d_ws, ws_bytes as for seqcdc_chunk with (total_bytes, nfiles).
+ * Each file is chunked independently, as if it were its own stream.
+ * Asynchronous on `stream`.
+ */
+int seqcdc_chunk_batch(const seqcdc_params_t *p, const uint8_t *d_data,
+                       uint64_t total_bytes, const uint64_t *d_offsets,
+                       uint64_t nfiles, uint64_t *d_cuts, uint64_t cap,
+                       uint64_t *d_cut_offsets, void *d_ws, size_t ws_bytes,
+                       const seqcdc_tuning_t *tuning, void *stream);
+
+/*
+ * Synchronise `stream`, then return the device-side status recorded in d_ws by
+ * the last call that used it: SEQCDC_OK, or SEQCDC_ETIMEOUT when a bounded
+ * wait inside a kernel expired (its outputs are then not valid).  Returns
+ * SEQCDC_ECUDA if the synchronisation itself fails.
+ */
+int seqcdc_status(const void *d_ws, void *stream);
+
+/* Static, human-readable text for a status code. */
+const char *seqcdc_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SEQCDC_H */

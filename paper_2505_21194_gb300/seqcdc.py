@@ -1,0 +1,244 @@
+"""Python binding of the SeqCDC C ABI (``include/seqcdc.h``).
+
+Argument marshalling only: each ``seqcdc_*`` function here forwards to the C
+entry point of the same name in ``libseqcdc.so``, passing raw device pointers
+taken from PyTorch tensors and the current CUDA stream.  PyTorch provides
+device memory and streams; every step of the chunker runs in the library's
+kernels.  There is no CPU fallback: if the library cannot be loaded, every
+call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import threading
+from dataclasses import dataclass
+
+from . import _build
+
+SEQCDC_OK = 0
+SEQCDC_EINVAL = 1
+SEQCDC_ECAPACITY = 2
+SEQCDC_ECUDA = 3
+SEQCDC_ETIMEOUT = 4
+SEQCDC_ERANGE = 5
+
+INCREASING = 0
+DECREASING = 1
+
+
+class SeqCDCError(RuntimeError):
+    """A seqcdc entry point returned a non-zero status."""
+
+    def __init__(self, status: int, where: str):
+        super().__init__("%s: %s (status %d)" % (where, seqcdc_strerror(status), status))
+        self.status = status
+
+
+class Params(ctypes.Structure):
+    """``seqcdc_params_t``: mode, seq_length, skip_trigger, skip_size, min, max."""
+
+    _fields_ = [
+        ("mode", ctypes.c_uint32),
+        ("seq_length", ctypes.c_uint32),
+        ("skip_trigger", ctypes.c_uint32),
+        ("skip_size", ctypes.c_uint32),
+        ("min_size", ctypes.c_uint64),
+        ("max_size", ctypes.c_uint64),
+    ]
+
+    def astuple(self):
+        return (self.mode, self.seq_length, self.skip_trigger, self.skip_size,
+                self.min_size, self.max_size)
+
+    def __repr__(self):
+        return ("Params(mode=%d, seq_length=%d, skip_trigger=%d, skip_size=%d, "
+                "min_size=%d, max_size=%d)" % self.astuple())
+
+
+class Tuning(ctypes.Structure):
+    """``seqcdc_tuning_t``: segment_bytes, block_threads (0 = default)."""
+
+    _fields_ = [("segment_bytes", ctypes.c_uint32),
+                ("block_threads", ctypes.c_uint32)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+_SYMBOLS = ("seqcdc_params", "seqcdc_validate", "seqcdc_workspace_size",
+            "seqcdc_chunk", "seqcdc_chunk_batch", "seqcdc_status",
+            "seqcdc_strerror")
+
+
+def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
+    """Load libseqcdc.so (building it first if needed) and declare its ABI."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.build() if build_if_missing else _build.LIB_PATH
+        lib = ctypes.CDLL(path)
+        P, T = ctypes.POINTER(Params), ctypes.POINTER(Tuning)
+        u32, u64, vp = ctypes.c_uint32, ctypes.c_uint64, ctypes.c_void_p
+        lib.seqcdc_params.argtypes = [u32, u32, P]
+        lib.seqcdc_params.restype = ctypes.c_int
+        lib.seqcdc_validate.argtypes = [P]
+        lib.seqcdc_validate.restype = ctypes.c_int
+        lib.seqcdc_workspace_size.argtypes = [P, u64, u64, T]
+        lib.seqcdc_workspace_size.restype = ctypes.c_size_t
+        lib.seqcdc_chunk.argtypes = [P, vp, u64, vp, u64, vp, vp, ctypes.c_size_t, T, vp]
+        lib.seqcdc_chunk.restype = ctypes.c_int
+        lib.seqcdc_chunk_batch.argtypes = [P, vp, u64, vp, u64, vp, u64, vp, vp,
+                                           ctypes.c_size_t, T, vp]
+        lib.seqcdc_chunk_batch.restype = ctypes.c_int
+        lib.seqcdc_status.argtypes = [vp, vp]
+        lib.seqcdc_status.restype = ctypes.c_int
+        lib.seqcdc_strerror.argtypes = [ctypes.c_int]
+        lib.seqcdc_strerror.restype = ctypes.c_char_p
+        _lib = lib
+        return lib
+
+
+def _check(status: int, where: str):
+    if status != SEQCDC_OK:
+        raise SeqCDCError(status, where)
+
+
+def _tuning(tuning):
+    if tuning is None:
+        return None
+    if isinstance(tuning, Tuning):
+        return ctypes.byref(tuning)
+    seg, thr = tuning
+    return ctypes.byref(Tuning(int(seg), int(thr)))
+
+
+def _stream_handle(stream) -> int:
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def _ptr(t) -> int:
+    return int(t.data_ptr()) if t is not None else 0
+
+
+# ----------------------------------------------------------------------------
+# Entry points (same names as the C ABI).
+# ----------------------------------------------------------------------------
+def seqcdc_params(expected_kib: int, mode: int = INCREASING) -> Params:
+    """Paper parameter set for 4 / 8 / 16 KB expected chunks (Table I, Sec. VI)."""
+    p = Params()
+    _check(load_library().seqcdc_params(expected_kib, mode, ctypes.byref(p)),
+           "seqcdc_params")
+    return p
+
+
+def make_params(mode, seq_length, skip_trigger, skip_size, min_size,
+                max_size) -> Params:
+    """A custom parameter set (validated by the library)."""
+    p = Params(mode, seq_length, skip_trigger, skip_size, min_size, max_size)
+    _check(load_library().seqcdc_validate(ctypes.byref(p)), "seqcdc_validate")
+    return p
+
+
+def seqcdc_validate(p: Params) -> int:
+    return load_library().seqcdc_validate(ctypes.byref(p))
+
+
+def seqcdc_workspace_size(p: Params, total_bytes: int, nfiles: int,
+                          tuning=None) -> int:
+    n = load_library().seqcdc_workspace_size(ctypes.byref(p), total_bytes,
+                                             nfiles, _tuning(tuning))
+    if n == 0:
+        raise SeqCDCError(SEQCDC_EINVAL, "seqcdc_workspace_size")
+    return n
+
+
+def seqcdc_chunk(p: Params, d_in, n: int, d_cuts, cap: int, d_count, d_ws,
+                 ws_bytes: int, tuning=None, stream=None) -> None:
+    """Raw entry point: tensors are device buffers the caller owns."""
+    _check(load_library().seqcdc_chunk(
+        ctypes.byref(p), _ptr(d_in), n, _ptr(d_cuts), cap, _ptr(d_count),
+        _ptr(d_ws), ws_bytes, _tuning(tuning), _stream_handle(stream)),
+        "seqcdc_chunk")
+
+
+def seqcdc_chunk_batch(p: Params, d_data, total_bytes: int, d_offsets,
+                       nfiles: int, d_cuts, cap: int, d_cut_offsets, d_ws,
+                       ws_bytes: int, tuning=None, stream=None) -> None:
+    """Raw entry point: tensors are device buffers the caller owns."""
+    _check(load_library().seqcdc_chunk_batch(
+        ctypes.byref(p), _ptr(d_data), total_bytes, _ptr(d_offsets), nfiles,
+        _ptr(d_cuts), cap, _ptr(d_cut_offsets), _ptr(d_ws), ws_bytes,
+        _tuning(tuning), _stream_handle(stream)), "seqcdc_chunk_batch")
+
+
+def seqcdc_status(d_ws, stream=None) -> int:
+    """Synchronise the stream; return the device-side status in the workspace."""
+    return load_library().seqcdc_status(_ptr(d_ws), _stream_handle(stream))
+
+
+def seqcdc_strerror(status: int) -> str:
+    try:
+        return load_library().seqcdc_strerror(status).decode()
+    except Exception:  # library not loadable: still describe the code
+        return "status %d" % status
+
+
+# ----------------------------------------------------------------------------
+# Convenience wrappers that allocate outputs with PyTorch.
+# ----------------------------------------------------------------------------
+@dataclass
+class BatchResult:
+    cuts: "object"          # torch.uint64-compatible int64 tensor (device)
+    cut_offsets: "object"   # int64 tensor (device), nfiles + 1
+
+
+def _workspace(p, total, nfiles, tuning, device):
+    import torch
+    ws_bytes = seqcdc_workspace_size(p, total, nfiles, tuning)
+    ws = torch.empty(ws_bytes, dtype=torch.uint8, device=device)
+    return ws, ws_bytes
+
+
+def chunk(data, p: Params, tuning=None, stream=None, check: bool = True):
+    """Chunk one uint8 CUDA tensor; returns an int64 tensor of cut offsets."""
+    import torch
+    if not data.is_cuda or data.dtype != torch.uint8:
+        raise TypeError("chunk() needs a uint8 CUDA tensor")
+    data = data.contiguous().view(-1)
+    n = data.numel()
+    cap = n // p.min_size + 1
+    cuts = torch.empty(max(cap, 1), dtype=torch.int64, device=data.device)
+    count = torch.zeros(1, dtype=torch.int64, device=data.device)
+    ws, ws_bytes = _workspace(p, n, 1, tuning, data.device)
+    seqcdc_chunk(p, data, n, cuts, cap, count, ws, ws_bytes, tuning, stream)
+    if check:
+        _check(seqcdc_status(ws, stream), "seqcdc_chunk (device)")
+    k = int(count.item())
+    return cuts[:k]
+
+
+def chunk_batch(data, offsets, p: Params, tuning=None, stream=None,
+                check: bool = True) -> BatchResult:
+    """Chunk a CSR batch: ``data`` uint8 CUDA, ``offsets`` int64 CUDA (nfiles+1)."""
+    import torch
+    if not data.is_cuda or data.dtype != torch.uint8:
+        raise TypeError("chunk_batch() needs uint8 CUDA data")
+    if not offsets.is_cuda or offsets.dtype != torch.int64:
+        raise TypeError("chunk_batch() needs int64 CUDA offsets")
+    data = data.contiguous().view(-1)
+    offsets = offsets.contiguous().view(-1)
+    nfiles = offsets.numel() - 1
+    total = data.numel()
+    cap = total // p.min_size + nfiles
+    cuts = torch.empty(max(cap, 1), dtype=torch.int64, device=data.device)
+    cut_offsets = torch.empty(nfiles + 1, dtype=torch.int64, device=data.device)
+    ws, ws_bytes = _workspace(p, total, nfiles, tuning, data.device)
+    seqcdc_chunk_batch(p, data, total, offsets, nfiles, cuts, cap, cut_offsets,
+                       ws, ws_bytes, tuning, stream)
+    if check:
+        _check(seqcdc_status(ws, stream), "seqcdc_chunk_batch (device)")
+    total_cuts = int(cut_offsets[-1].item())
+    return BatchResult(cuts[:total_cuts], cut_offsets)

@@ -1,0 +1,99 @@
+"""C ABI checks that need no GPU: the library builds, loads and exports every
+entry point declared in include/seqcdc.h; host-side argument validation."""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(__file__)), "include", "seqcdc.h")
+
+
+def _declared():
+    with open(HEADER) as f:
+        text = f.read()
+    return sorted(set(re.findall(r"^[a-z_ ]+\*?\s*(seqcdc_\w+)\(", text, re.M)))
+
+
+def test_header_declares_entry_points():
+    names = _declared()
+    for n in ("seqcdc_params", "seqcdc_chunk", "seqcdc_chunk_batch",
+              "seqcdc_workspace_size", "seqcdc_status", "seqcdc_strerror"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(seqcdc_lib):
+    lib = seqcdc_lib.load_library()
+    for name in _declared():
+        assert hasattr(lib, name), name
+
+
+def test_presets_match_oracle(seqcdc_lib):
+    for kib in (4, 8, 16):
+        for mode in (0, 1):
+            got = seqcdc_lib.seqcdc_params(kib, mode).astuple()
+            o = oracle.presets(kib, mode)
+            assert got == (o.mode, o.seq_length, o.skip_trigger, o.skip_size,
+                           o.min_size, o.max_size)
+    with pytest.raises(seqcdc_lib.SeqCDCError):
+        seqcdc_lib.seqcdc_params(32, 0)
+    with pytest.raises(seqcdc_lib.SeqCDCError):
+        seqcdc_lib.seqcdc_params(8, 2)
+
+
+@pytest.mark.parametrize("bad", [
+    (2, 5, 50, 256, 4096, 16384),   # mode
+    (0, 1, 50, 256, 4096, 16384),   # seq_length < 2
+    (0, 17, 50, 256, 4096, 16384),  # seq_length > 16
+    (0, 5, 50, 256, 0, 16384),      # min 0
+    (0, 5, 50, 256, 8192, 4096),    # max < min
+    (0, 5, 50, 256, 4096, 1 << 20), # max beyond the supported bound
+])
+def test_validate_rejects(seqcdc_lib, bad):
+    p = seqcdc_lib.Params(*bad)
+    assert seqcdc_lib.seqcdc_validate(p) == seqcdc_lib.SEQCDC_EINVAL
+    lib = seqcdc_lib.load_library()
+    assert lib.seqcdc_workspace_size(ctypes.byref(p), 1 << 20, 1, None) == 0
+
+
+def test_workspace_size_grows(seqcdc_lib):
+    p = seqcdc_lib.seqcdc_params(8, 0)
+    a = seqcdc_lib.seqcdc_workspace_size(p, 1 << 20, 1)
+    b = seqcdc_lib.seqcdc_workspace_size(p, 1 << 30, 1)
+    c = seqcdc_lib.seqcdc_workspace_size(p, 1 << 30, 10000)
+    assert 0 < a < b < c
+
+
+def test_host_side_errors_before_launch(seqcdc_lib):
+    """Bad arguments are rejected on the host; nothing reaches the device."""
+    lib = seqcdc_lib.load_library()
+    p = seqcdc_lib.seqcdc_params(8, 0)
+    P = ctypes.byref(p)
+    n = 1 << 20
+    ws = seqcdc_lib.seqcdc_workspace_size(p, n, 1)
+    fake = 1 << 40  # never dereferenced: every call below fails validation
+    E = seqcdc_lib
+    # NULL / misaligned workspace
+    assert lib.seqcdc_chunk(P, fake, n, fake, n, fake, None, ws, None, None) == E.SEQCDC_EINVAL
+    assert lib.seqcdc_chunk(P, fake, n, fake, n, fake, fake + 8, ws, None, None) == E.SEQCDC_EINVAL
+    # misaligned input
+    assert lib.seqcdc_chunk(P, fake + 3, n, fake, n, fake, fake, ws, None, None) == E.SEQCDC_EINVAL
+    # workspace too small, capacity too small
+    assert lib.seqcdc_chunk(P, fake, n, fake, n, fake, fake, ws - 1, None, None) == E.SEQCDC_ECAPACITY
+    assert lib.seqcdc_chunk(P, fake, n, fake, n // 4096, fake, fake, ws, None, None) == E.SEQCDC_ECAPACITY
+    # NULL count / offsets
+    assert lib.seqcdc_chunk(P, fake, n, fake, n, None, fake, ws, None, None) == E.SEQCDC_EINVAL
+    assert lib.seqcdc_chunk_batch(P, fake, n, None, 1, fake, n, fake, fake, ws, None, None) == E.SEQCDC_EINVAL
+    bad = E.Params(0, 1, 0, 0, 1, 1)
+    assert lib.seqcdc_chunk(ctypes.byref(bad), fake, n, fake, n, fake, fake, ws, None, None) == E.SEQCDC_EINVAL
+
+
+def test_strerror(seqcdc_lib):
+    for code in range(6):
+        assert seqcdc_lib.seqcdc_strerror(code)
+    assert "unknown" in seqcdc_lib.seqcdc_strerror(99)
