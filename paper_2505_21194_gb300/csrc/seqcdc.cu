@@ -52,20 +52,21 @@ namespace {
 constexpr int kMaxEntries = 512;    // entry candidates tabulated per item
 constexpr int kMaxNodes = 1024;     // distinct cut positions per item walk
 constexpr int kHashSlots = 2048;    // open-addressing slots (power of two)
-constexpr int kMaxImage = 16;       // distinct exits published per item
+constexpr int kMaxImage = 32;       // distinct exits published per item (one per lane)
 constexpr int kFileTile = 1024;     // files per plan block
 constexpr int kItemTile = 256;      // items per compaction block
 constexpr uint32_t kMaxSeqLength = 16;
 constexpr uint64_t kMaxMaxSize = 262144;
-constexpr int64_t kLookBackDepth = 64;
+constexpr int64_t kLookBackDepth = 6;
 constexpr uint64_t kWaitNs = 2000000000ull;  // 2 s bound on any device wait
 
 // Item state bits.
 constexpr uint32_t F_TABLE = 1u;     // exit set (and maybe table) published
 constexpr uint32_t F_SINGLE = 2u;    // exit set has exactly one element
 constexpr uint32_t F_NOTABLE = 4u;   // no usable table (too many exits)
-constexpr uint32_t F_INCL = 8u;      // true exit published
+constexpr uint32_t F_RESOLVED = 8u;  // entry chosen, cuts and exit published
 constexpr uint32_t F_ABNORMAL = 16u; // no walk from all entries was possible
+constexpr uint32_t F_UNRESOLVED = 32u;  // look-back could not choose an entry
 
 constexpr uint16_t kNil = 0xFFFFu;
 constexpr uint32_t kInvalidPos = 0xFFFFFFFFu;
@@ -88,8 +89,8 @@ struct WsHeader {
 };
 
 struct Layout {
-  size_t hdr, seg_base, ftile, state, incl, count, img_n, img, tab_n, tab,
-      slot, itile, total;
+  size_t hdr, seg_base, ftile, state, incl, entry, first_bad, count, img_n,
+      img, tab_n, tab, slot, itile, total;
   uint64_t imax;     // upper bound on items
   uint64_t nftiles;  // plan tiles
   uint64_t nitiles;  // compaction tiles
@@ -117,7 +118,9 @@ struct WsPtrs {
   uint32_t *seg_base;   // nfiles + 1
   uint32_t *ftile;      // per plan tile
   uint32_t *state;      // per item
-  uint64_t *incl;       // per item: true exit (file-relative)
+  uint64_t *incl;       // per item: exit from `entry` (file-relative)
+  uint64_t *entry;      // per item: entry the item's cuts were computed from
+  uint32_t *first_bad;  // per file: first inconsistent item (verify pass)
   uint32_t *count;      // per item: true cuts emitted
   uint32_t *img_n;      // per item
   uint64_t *img;        // per item x kMaxImage (file-relative)
@@ -378,10 +381,14 @@ __global__ void plan_scan_kernel(Geom g, WsPtrs ws, uint64_t nftiles,
     ws.hdr->ticket = 0;
     ws.hdr->status = 0;
   }
-  // Reset per-item state.
+  // Reset per-item state and per-file repair marks.
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < imax;
        i += (uint64_t)gridDim.x * blockDim.x) {
     ws.state[i] = 0;
+  }
+  for (uint64_t f = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; f < g.nfiles;
+       f += (uint64_t)gridDim.x * blockDim.x) {
+    ws.first_bad[f] = 0xffffffffu;
   }
 }
 
@@ -389,23 +396,46 @@ __global__ void plan_scan_kernel(Geom g, WsPtrs ws, uint64_t nftiles,
 // Segment kernel.
 // ---------------------------------------------------------------------------
 struct SegShared {
-  // control
-  uint32_t item, file, seg, nitems;
-  int64_t B;         // window base (file-relative)
+  uint32_t item, file, seg, nitems, first_item;
+  int64_t B;          // window base (file-relative); global index of rel 0 is 16-aligned
   uint64_t p_s, q_s, n_f, gbase;
-  uint32_t W;        // bitmap words
-  uint32_t K;        // entries
-  uint32_t nnodes, nact, nnew, abnormal, rounds;
-  uint32_t nimg;
+  uint32_t W;         // bitmap words
+  uint32_t K;         // entries
+  uint32_t nnodes, nact, nnew, abnormal, rounds, nimg;
   uint32_t scratch[32];
   uint64_t true_entry;
-  uint32_t entry_node;
+  uint32_t resolved;
 };
+
+// Pointers into the dynamic shared memory of one item.
+struct SegSmem {
+  uint32_t *E, *O;
+  uint32_t *node_pos;     // kMaxNodes
+  uint16_t *node_next;    // kMaxNodes
+  uint16_t *hslot;        // kHashSlots
+  uint16_t *act, *act2;   // kMaxNodes each
+  uint64_t *img_local;    // kMaxImage
+  uint16_t *img_of_node;  // kMaxNodes
+};
+
+__device__ __forceinline__ SegSmem carve(unsigned char *raw, uint32_t W) {
+  SegSmem m;
+  m.E = reinterpret_cast<uint32_t *>(raw);
+  m.O = m.E + W;
+  m.node_pos = m.O + W;
+  m.node_next = reinterpret_cast<uint16_t *>(m.node_pos + kMaxNodes);
+  m.hslot = m.node_next + kMaxNodes;
+  m.act = m.hslot + kHashSlots;
+  m.act2 = m.act + kMaxNodes;
+  m.img_local = reinterpret_cast<uint64_t *>(m.act2 + kMaxNodes);
+  m.img_of_node = reinterpret_cast<uint16_t *>(m.img_local + kMaxImage);
+  return m;
+}
 
 __device__ __forceinline__ uint32_t find_file(const uint32_t *seg_base,
                                               uint64_t nfiles, uint32_t item) {
-  // largest f with seg_base[f] <= item and seg_base[f+1] > item
-  uint64_t lo = 0, hi = nfiles;  // answer in [lo, hi)
+  // largest f < nfiles with seg_base[f] <= item (then seg_base[f+1] > item)
+  uint64_t lo = 0, hi = nfiles;
   while (hi - lo > 1) {
     const uint64_t mid = (lo + hi) >> 1;
     if (seg_base[mid] <= item) lo = mid; else hi = mid;
@@ -413,115 +443,100 @@ __device__ __forceinline__ uint32_t find_file(const uint32_t *seg_base,
   return (uint32_t)lo;
 }
 
-__global__ void __launch_bounds__(512)
-segment_kernel(Geom g, DevParams p, WsPtrs ws) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ SegShared sh;
-  const int tid = threadIdx.x;
-  const int nthreads = blockDim.x;
+// Geometry of item (file, seg); thread 0 only.
+__device__ void seg_setup(SegShared &sh, const Geom &g, const DevParams &p,
+                          uint32_t item, uint32_t file, uint32_t seg,
+                          uint32_t first_item) {
+  sh.item = item;
+  sh.file = file;
+  sh.seg = seg;
+  sh.first_item = first_item;
+  sh.n_f = file_size(g, file);
+  sh.gbase = file_start(g, file);
+  sh.p_s = (uint64_t)seg * g.L;
+  sh.q_s = min(sh.p_s + g.L, sh.n_f);
+  const uint64_t w1 = min(sh.q_s + p.mx, sh.n_f);
+  // Window base: 32 bytes before the item, rounded down so that its global
+  // byte index is 16-aligned.
+  int64_t gb = (int64_t)(sh.gbase + sh.p_s) - 32;
+  gb = gb >= 0 ? (gb & ~(int64_t)15) : -(((-gb) + 15) & ~(int64_t)15);
+  sh.B = gb - (int64_t)sh.gbase;
+  sh.W = (uint32_t)(((int64_t)w1 - sh.B + 31) >> 5);
+  sh.abnormal = 0;
+  sh.nnodes = 0;
+  sh.K = 0;
+  sh.nimg = 0;
+  sh.resolved = 0;
+}
 
-  if (tid == 0) {
-    sh.item = atomicAdd(&ws.hdr->ticket, 1u);
-    sh.nitems = ws.hdr->nitems;
-  }
-  __syncthreads();
-  if (sh.item >= sh.nitems) return;
-  if (tid == 0) {
-    const uint32_t f = find_file(ws.seg_base, g.nfiles, sh.item);
-    sh.file = f;
-    sh.seg = sh.item - ws.seg_base[f];
-    sh.n_f = file_size(g, f);
-    sh.gbase = file_start(g, f);
-    sh.p_s = (uint64_t)sh.seg * g.L;
-    sh.q_s = min(sh.p_s + g.L, sh.n_f);
-    const uint64_t w1 = min(sh.q_s + p.mx, sh.n_f);
-    // Window base: 32 bytes before the item, rounded down so that its global
-    // byte index is 16-aligned.
-    int64_t gb = (int64_t)(sh.gbase + sh.p_s) - 32;
-    gb = gb >= 0 ? (gb & ~(int64_t)15) : -(((-gb) + 15) & ~(int64_t)15);
-    sh.B = gb - (int64_t)sh.gbase;
-    sh.W = (uint32_t)(((int64_t)w1 - sh.B + 31) >> 5);
-    sh.abnormal = 0;
-    sh.nnodes = 0;
-    sh.K = 0;
-    sh.nimg = 0;
-  }
-  __syncthreads();
-
+// E and O bitmaps of the window [B, B + 32 W), 16 positions per lane step.
+__device__ void seg_bitmaps(const SegShared &sh, const Geom &g,
+                            const DevParams &p, const SegSmem &m) {
+  const int tid = threadIdx.x, nthreads = blockDim.x;
   const uint32_t W = sh.W;
-  uint32_t *E = reinterpret_cast<uint32_t *>(smem_raw);
-  uint32_t *O = E + W;
-  uint32_t *node_pos = O + W;                                   // kMaxNodes
-  uint16_t *node_next = reinterpret_cast<uint16_t *>(node_pos + kMaxNodes);
-  uint16_t *hslot = node_next + kMaxNodes;                      // kHashSlots
-  uint16_t *act = hslot + kHashSlots;                           // kMaxNodes
-  uint16_t *act2 = act + kMaxNodes;                             // kMaxNodes
-  uint64_t *img_local = reinterpret_cast<uint64_t *>(act2 + kMaxNodes);  // kMaxImage
-  uint16_t *img_of_node = reinterpret_cast<uint16_t *>(img_local + kMaxImage);  // kMaxNodes
-
-  const int64_t B = sh.B;
-  const uint64_t n_f = sh.n_f;
-  const uint64_t p_s = sh.p_s, q_s = sh.q_s;
-  const int64_t gwin = (int64_t)sh.gbase + B;  // global byte index of rel 0
-
-  // ---- Phase 1: E and O bitmaps of the window (16 positions per lane step).
-  {
-    uint16_t *E16 = reinterpret_cast<uint16_t *>(E);
-    uint16_t *O16 = reinterpret_cast<uint16_t *>(O);
-    const uint32_t H = 2 * W;  // 16-byte groups
-    const int lane = tid & 31, warp = tid >> 5, nwarps = nthreads >> 5;
-    uint32_t per = (H + nwarps - 1) / nwarps;
-    per = (per + 31) & ~31u;
-    const uint32_t h0 = warp * per;
-    const uint32_t h1 = min(h0 + per, H);
-    uint32_t carry_byte = 0, carry_T = 0;
-    if (h0 < h1 && h0 > 0) {
-      // T bits of the 16 positions before this warp's first group (only the
-      // top SeqLength-2 of them matter, so the unknown byte before is moot).
-      const uint4 pv = load16(g.data, gwin + 16 * (int64_t)(h0 - 1), g.total);
-      uint32_t t16, o16;
-      classify16(0, pv, p.mode, t16, o16);
-      carry_T = t16;
-      carry_byte = pv.w >> 24;
-    }
-    for (uint32_t hb = h0; hb < h1; hb += 32) {
-      const uint32_t h = hb + lane;
-      const bool live = h < h1;
-      const uint4 v = live ? load16(g.data, gwin + 16 * (int64_t)h, g.total)
-                           : make_uint4(0, 0, 0, 0);
-      uint32_t pb = __shfl_up_sync(0xffffffffu, v.w >> 24, 1);
-      if (lane == 0) pb = carry_byte;
-      uint32_t t16, o16;
-      classify16(pb, v, p.mode, t16, o16);
-      uint32_t pt = __shfl_up_sync(0xffffffffu, t16, 1);
-      if (lane == 0) pt = carry_T;
-      // E at group position t needs T at t, t-1, ..., t-(R-2): the previous
-      // group's T bits sit below this group's in a 32-bit window.
-      const uint32_t tw = (t16 << 16) | (pt & 0xffffu);
-      uint32_t ew = tw;
-      for (uint32_t k = 1; k + 1 < p.R; ++k) ew &= tw << k;
-      const uint32_t e16 = ew >> 16;
-      if (live) {
-        E16[h] = (uint16_t)e16;
-        O16[h] = (uint16_t)o16;
-      }
-      carry_byte = __shfl_sync(0xffffffffu, v.w >> 24, 31);
-      carry_T = __shfl_sync(0xffffffffu, t16, 31);
-    }
+  const int64_t gwin = (int64_t)sh.gbase + sh.B;  // global byte index of rel 0
+  uint16_t *E16 = reinterpret_cast<uint16_t *>(m.E);
+  uint16_t *O16 = reinterpret_cast<uint16_t *>(m.O);
+  const uint32_t H = 2 * W;  // 16-byte groups
+  const int lane = tid & 31, warp = tid >> 5, nwarps = nthreads >> 5;
+  uint32_t per = (H + nwarps - 1) / nwarps;
+  per = (per + 31) & ~31u;
+  const uint32_t h0 = warp * per;
+  const uint32_t h1 = min(h0 + per, H);
+  uint32_t carry_byte = 0, carry_T = 0;
+  if (h0 < h1 && h0 > 0) {
+    // T bits of the 16 positions before this warp's first group (only the top
+    // SeqLength-2 of them matter, so the unknown byte before them is moot).
+    const uint4 pv = load16(g.data, gwin + 16 * (int64_t)(h0 - 1), g.total);
+    uint32_t t16, o16;
+    classify16(0, pv, p.mode, t16, o16);
+    carry_T = t16;
+    carry_byte = pv.w >> 24;
   }
-  __syncthreads();
+  for (uint32_t hb = h0; hb < h1; hb += 32) {
+    const uint32_t h = hb + lane;
+    const bool live = h < h1;
+    const uint4 v = live ? load16(g.data, gwin + 16 * (int64_t)h, g.total)
+                         : make_uint4(0, 0, 0, 0);
+    uint32_t pb = __shfl_up_sync(0xffffffffu, v.w >> 24, 1);
+    if (lane == 0) pb = carry_byte;
+    uint32_t t16, o16;
+    classify16(pb, v, p.mode, t16, o16);
+    uint32_t pt = __shfl_up_sync(0xffffffffu, t16, 1);
+    if (lane == 0) pt = carry_T;
+    // E at group position t needs T at t, t-1, ..., t-(R-2): the previous
+    // group's T bits sit below this group's in a 32-bit window.
+    const uint32_t tw = (t16 << 16) | (pt & 0xffffu);
+    uint32_t ew = tw;
+    for (uint32_t k = 1; k + 1 < p.R; ++k) ew &= tw << k;
+    if (live) {
+      E16[h] = (uint16_t)(ew >> 16);
+      O16[h] = (uint16_t)o16;
+    }
+    carry_byte = __shfl_sync(0xffffffffu, v.w >> 24, 31);
+    carry_T = __shfl_sync(0xffffffffu, t16, 31);
+  }
+}
 
-  // ---- Phase 2: entry candidates.  Item 0 of a file starts at the file start;
-  // any other item may be entered at every natural cut x = e + 1 (E[e] set)
-  // with p_s <= x < p_s + max_size.
+// Phases 2-4: entry candidates, walk of every entry's chain with merging,
+// exits and the entry -> exit table, published to the workspace.  All threads.
+__device__ void seg_walk_publish(SegShared &sh, const DevParams &p,
+                                 const SegSmem &m, const WsPtrs &ws) {
+  const int tid = threadIdx.x, nthreads = blockDim.x;
+  const int64_t B = sh.B;
+  const uint64_t n_f = sh.n_f, p_s = sh.p_s, q_s = sh.q_s;
   const uint32_t end_rel = (uint32_t)((int64_t)n_f - B);
   const uint32_t q_rel = (uint32_t)((int64_t)q_s - B);
   const uint32_t ps_rel = (uint32_t)((int64_t)p_s - B);
-  const Bits bits{E, O};
-  const bool first = (sh.seg == 0);
-  if (first) {
+  const Bits bits{m.E, m.O};
+  const uint32_t item = sh.item;
+
+  // Entry candidates.  Item 0 of a file starts at the file start; any other
+  // item may be entered at every natural cut x = e + 1 (E[e] set) with
+  // p_s <= x < p_s + max_size.
+  if (sh.seg == 0) {
     if (tid == 0) {
-      node_pos[0] = ps_rel;
+      m.node_pos[0] = ps_rel;
       sh.K = 1;
     }
   } else {
@@ -534,11 +549,11 @@ segment_kernel(Geom g, DevParams p, WsPtrs ws) {
     const uint32_t a = wlo + tid * per, z = min(a + per, whi);
     uint32_t cnt = 0;
     for (uint32_t w = a; w < z; ++w) {
-      uint32_t m = E[w];
+      uint32_t v = m.E[w];
       const uint32_t base = w << 5;
-      if (lo > base) m &= ~0u << (lo - base);
-      if (hi - base < 32) m &= (1u << (hi - base)) - 1u;
-      cnt += __popc(m);
+      if (lo > base) v &= ~0u << (lo - base);
+      if (hi - base < 32) v &= (1u << (hi - base)) - 1u;
+      cnt += __popc(v);
     }
     uint32_t K;
     const uint32_t off = block_excl_scan(cnt, sh.scratch, &K);
@@ -547,14 +562,14 @@ segment_kernel(Geom g, DevParams p, WsPtrs ws) {
     } else {
       uint32_t o = off;
       for (uint32_t w = a; w < z; ++w) {
-        uint32_t m = E[w];
+        uint32_t v = m.E[w];
         const uint32_t base = w << 5;
-        if (lo > base) m &= ~0u << (lo - base);
-        if (hi - base < 32) m &= (1u << (hi - base)) - 1u;
-        while (m) {
-          const uint32_t b = __ffs(m) - 1;
-          m &= m - 1;
-          node_pos[o++] = base + b + 1;
+        if (lo > base) v &= ~0u << (lo - base);
+        if (hi - base < 32) v &= (1u << (hi - base)) - 1u;
+        while (v) {
+          const uint32_t bpos = __ffs(v) - 1;
+          v &= v - 1;
+          m.node_pos[o++] = base + bpos + 1;
         }
       }
       if (tid == 0) sh.K = K;
@@ -562,12 +577,12 @@ segment_kernel(Geom g, DevParams p, WsPtrs ws) {
   }
   __syncthreads();
 
-  // ---- Phase 3: walk every entry's chunk chain to its exit, merging chains
-  // that reach a common cut.  Nodes are distinct cut positions.
+  // Walk every entry's chunk chain to its exit (first cut >= q_s), merging
+  // chains that reach a common cut.  Nodes are distinct cut positions.
   if (!sh.abnormal) {
     const uint32_t K = sh.K;
-    for (int i = tid; i < kHashSlots; i += nthreads) hslot[i] = kNil;
-    for (int i = tid; i < kMaxNodes; i += nthreads) node_next[i] = kNil;
+    for (int i = tid; i < kHashSlots; i += nthreads) m.hslot[i] = kNil;
+    for (int i = tid; i < kMaxNodes; i += nthreads) m.node_next[i] = kNil;
     if (tid == 0) {
       sh.nnodes = K;
       sh.nact = 0;
@@ -576,50 +591,50 @@ segment_kernel(Geom g, DevParams p, WsPtrs ws) {
     }
     __syncthreads();
     for (uint32_t k = tid; k < K; k += nthreads) {
-      const uint32_t x = node_pos[k];
+      const uint32_t x = m.node_pos[k];
       uint32_t slot = hash_pos(x);
-      while (atomicCAS(&hslot[slot], kNil, (uint16_t)k) != kNil)
+      while (atomicCAS(&m.hslot[slot], kNil, (uint16_t)k) != kNil)
         slot = (slot + 1) & (kHashSlots - 1);
-      if (x < q_rel) act[atomicAdd(&sh.nact, 1u)] = (uint16_t)k;
+      if (x < q_rel) m.act[atomicAdd(&sh.nact, 1u)] = (uint16_t)k;
     }
     __syncthreads();
-    uint16_t *cur_act = act, *nxt_act = act2;
+    uint16_t *cur_act = m.act, *nxt_act = m.act2;
     while (true) {
       const uint32_t nact = sh.nact;
       if (nact == 0 || sh.abnormal) break;
       for (uint32_t t = tid; t < nact; t += nthreads) {
         const uint16_t h = cur_act[t];
-        const uint32_t y = chunk_step(bits, p, node_pos[h], end_rel);
+        const uint32_t y = chunk_step(bits, p, m.node_pos[h], end_rel);
         uint32_t slot = hash_pos(y);
         uint16_t id = kNil;
         bool created = false;
         for (int probe = 0; probe < kHashSlots; ++probe) {
-          uint16_t cur = *((volatile uint16_t *)&hslot[slot]);
+          uint16_t cur = *((volatile uint16_t *)&m.hslot[slot]);
           if (cur == kNil) {
             const uint32_t nid = atomicAdd(&sh.nnodes, 1u);
             if (nid >= (uint32_t)kMaxNodes) {
               sh.abnormal = 1;
               break;
             }
-            node_pos[nid] = y;
-            node_next[nid] = kNil;
+            m.node_pos[nid] = y;
+            m.node_next[nid] = kNil;
             __threadfence_block();
-            const uint16_t prev = atomicCAS(&hslot[slot], kNil, (uint16_t)nid);
+            const uint16_t prev = atomicCAS(&m.hslot[slot], kNil, (uint16_t)nid);
             if (prev == kNil) {
               id = (uint16_t)nid;
               created = true;
               break;
             }
-            node_pos[nid] = kInvalidPos;  // lost the slot; the winner may match
+            m.node_pos[nid] = kInvalidPos;  // lost the slot; the winner may match
             cur = prev;
           }
-          if (*((volatile uint32_t *)&node_pos[cur]) == y) {
+          if (*((volatile uint32_t *)&m.node_pos[cur]) == y) {
             id = cur;
             break;
           }
           slot = (slot + 1) & (kHashSlots - 1);
         }
-        node_next[h] = id;
+        m.node_next[h] = id;
         if (created && y < q_rel) nxt_act[atomicAdd(&sh.nnew, 1u)] = id;
       }
       __syncthreads();
@@ -633,22 +648,22 @@ segment_kernel(Geom g, DevParams p, WsPtrs ws) {
       nxt_act = tmp;
       __syncthreads();
     }
-    __syncthreads();
   }
+  __syncthreads();
 
-  // ---- Phase 4: exits, entry -> exit table, publication.
-  const uint32_t item = sh.item;
+  // Exits (terminal nodes) and, by pointer jumping, each entry's exit and hop
+  // count.  Publish the exit set and, when it has several elements, the table.
   if (!sh.abnormal) {
     const uint32_t nn = min(sh.nnodes, (uint32_t)kMaxNodes);
-    uint16_t *jmp = hslot;                 // reuse the hash (kHashSlots >= 2*kMaxNodes)
-    uint16_t *cnt = hslot + kMaxNodes;
+    uint16_t *jmp = m.hslot;               // reuse the hash (kHashSlots >= 2*kMaxNodes)
+    uint16_t *cnt = m.hslot + kMaxNodes;
     for (uint32_t n = tid; n < nn; n += nthreads) {
-      const bool valid = node_pos[n] != kInvalidPos;
-      const uint16_t nx = node_next[n];
+      const bool valid = m.node_pos[n] != kInvalidPos;
+      const uint16_t nx = m.node_next[n];
       if (valid && nx == kNil) {
         const uint32_t idx = atomicAdd(&sh.nimg, 1u);
-        if (idx < (uint32_t)kMaxImage) img_local[idx] = (uint64_t)(B + (int64_t)node_pos[n]);
-        img_of_node[n] = (uint16_t)idx;
+        if (idx < (uint32_t)kMaxImage) m.img_local[idx] = (uint64_t)(B + (int64_t)m.node_pos[n]);
+        m.img_of_node[n] = (uint16_t)idx;
       }
       jmp[n] = (nx == kNil) ? (uint16_t)n : nx;
       cnt[n] = (nx == kNil) ? 0 : 1;
@@ -659,15 +674,13 @@ segment_kernel(Geom g, DevParams p, WsPtrs ws) {
     for (uint32_t r = 1; r < 2 * nn; r <<= 1) {
       for (uint32_t n = tid; n < nn; n += nthreads) {
         const uint16_t j = jmp[n];
-        const uint16_t jj = jmp[j];
-        const uint16_t c = cnt[n] + cnt[j];
-        act[n] = jj;   // stage (act / act2 are free now)
-        act2[n] = c;
+        m.act[n] = jmp[j];
+        m.act2[n] = cnt[n] + cnt[j];
       }
       __syncthreads();
       for (uint32_t n = tid; n < nn; n += nthreads) {
-        jmp[n] = act[n];
-        cnt[n] = act2[n];
+        jmp[n] = m.act[n];
+        cnt[n] = m.act2[n];
       }
       __syncthreads();
     }
@@ -675,13 +688,13 @@ segment_kernel(Geom g, DevParams p, WsPtrs ws) {
     const bool notable = nimg > (uint32_t)kMaxImage;
     if (!notable) {
       for (uint32_t k = tid; k < nimg; k += nthreads)
-        ws.img[(uint64_t)item * kMaxImage + k] = img_local[k];
+        ws.img[(uint64_t)item * kMaxImage + k] = m.img_local[k];
       if (nimg > 1) {
         for (uint32_t k = tid; k < sh.K; k += nthreads) {
           const uint16_t ex = jmp[k];
-          const uint64_t ent = (uint64_t)(node_pos[k] - ps_rel);
+          const uint64_t ent = (uint64_t)(m.node_pos[k] - ps_rel);
           ws.tab[(uint64_t)item * kMaxEntries + k] =
-              ent | ((uint64_t)img_of_node[ex] << 32) | ((uint64_t)cnt[k] << 40);
+              ent | ((uint64_t)m.img_of_node[ex] << 32) | ((uint64_t)cnt[k] << 40);
         }
       }
     }
@@ -697,97 +710,210 @@ segment_kernel(Geom g, DevParams p, WsPtrs ws) {
     __threadfence();
     atomicOr(&ws.state[item], F_ABNORMAL);
   }
+}
 
-  // ---- Phase 5: true entry by look-back (thread 0), then emission.
-  if (tid == 0) {
-    uint64_t x = p_s;  // file start for the first item
-    if (!first) {
-      const uint32_t first_item = item - sh.seg;
-      uint32_t stack[kLookBackDepth];
-      int depth = 0;
-      uint32_t k = item - 1;
-      bool ok = false;
-      while (true) {
-        uint32_t st = wait_any(&ws.state[k], F_TABLE | F_INCL | F_ABNORMAL, ws.hdr);
-        if (st == 0) break;
-        if (st & F_INCL) { x = __ldcg(&ws.incl[k]); ok = true; break; }
-        if (st & F_SINGLE) { x = __ldcg(&ws.img[(uint64_t)k * kMaxImage]); ok = true; break; }
-        if ((st & (F_ABNORMAL | F_NOTABLE)) || depth == kLookBackDepth || k == first_item) {
-          st = wait_any(&ws.state[k], F_INCL, ws.hdr);
-          if (st == 0) break;
-          x = __ldcg(&ws.incl[k]);
-          ok = true;
-          break;
-        }
-        stack[depth++] = k;
-        --k;
-      }
-      // Apply the tables of the items passed over, earliest first.
-      while (ok && depth > 0) {
-        k = stack[--depth];
-        const uint64_t pk = (uint64_t)(k - first_item) * g.L;
-        const uint64_t want = x - pk;
-        const uint64_t *tb = ws.tab + (uint64_t)k * kMaxEntries;
-        uint32_t lo2 = 0, hi2 = __ldcg(&ws.tab_n[k]);
-        bool found = false;
-        while (lo2 < hi2) {
-          const uint32_t mid = (lo2 + hi2) >> 1;
-          const uint64_t v = __ldcg(&tb[mid]);
-          const uint64_t ent = v & 0xffffffffull;
-          if (ent == want) {
-            x = __ldcg(&ws.img[(uint64_t)k * kMaxImage + ((v >> 32) & 0xff)]);
-            found = true;
-            break;
-          }
-          if (ent < want) lo2 = mid + 1; else hi2 = mid;
-        }
-        if (!found) {
-          const uint32_t st = wait_any(&ws.state[k], F_INCL, ws.hdr);
-          if (st == 0) { ok = false; break; }
-          x = __ldcg(&ws.incl[k]);
-        }
-      }
-      if (!ok) x = p_s;  // timed out: keep going, status already records it
+// Exit of item j for entry position x (file-relative), from j's table.
+// Returns false if x is not one of j's entries.
+__device__ bool table_lookup(const WsPtrs &ws, uint32_t j, uint64_t pj,
+                             uint64_t x, uint64_t *out) {
+  if (x < pj) return false;
+  const uint64_t want = x - pj;
+  const uint64_t *tb = ws.tab + (uint64_t)j * kMaxEntries;
+  uint32_t lo = 0, hi = __ldcg(&ws.tab_n[j]);
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi) >> 1;
+    const uint64_t v = __ldcg(&tb[mid]);
+    const uint64_t ent = v & 0xffffffffull;
+    if (ent == want) {
+      *out = __ldcg(&ws.img[(uint64_t)j * kMaxImage + ((v >> 32) & 0xff)]);
+      return true;
     }
+    if (ent < want) lo = mid + 1; else hi = mid;
+  }
+  return false;
+}
+
+// Speculative entry of a non-first item by look-back over the predecessors'
+// published exit sets and tables (warp 0).  The candidates for this item's
+// entry are the exits of item s-1 over its entries; when there are several,
+// the exits of s-2 are pushed through s-1's table, and so on, up to
+// kLookBackDepth items.  The result assumes each predecessor was entered at
+// one of its tabulated entries; the verify pass checks that afterwards.
+// Waits only for predecessors' tables, which depend on nothing else.
+__device__ void seg_lookback(SegShared &sh, const Geom &g, const WsPtrs &ws) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t item = sh.item;
+  const uint32_t first_item = sh.first_item;
+  bool ok = false;
+  uint64_t x = 0;
+  for (uint32_t depth = 1; depth <= (uint32_t)kLookBackDepth; ++depth) {
+    const uint32_t k = item - depth;  // k >= first_item (item 0 is single)
+    uint32_t st = 0;
+    if (lane == 0) st = wait_any(&ws.state[k], F_TABLE | F_ABNORMAL, ws.hdr);
+    st = __shfl_sync(0xffffffffu, st, 0);
+    if (st == 0) break;
+    st = ld_acquire(&ws.state[k]);  // every lane acquires before reading k's data
+    if (st & (F_ABNORMAL | F_NOTABLE)) break;
+    const uint32_t nimg = __ldcg(&ws.img_n[k]);
+    // Each lane pushes one of k's exits through the tables of k+1 .. item-1.
+    bool have = lane < (int)nimg;
+    bool fail = false;
+    uint64_t y = have ? __ldcg(&ws.img[(uint64_t)k * kMaxImage + lane]) : 0;
+    for (uint32_t j = k + 1; j < item && have; ++j) {
+      uint64_t z;
+      if (table_lookup(ws, j, (uint64_t)(j - first_item) * g.L, y, &z)) y = z;
+      else { fail = true; have = false; }
+    }
+    if (__any_sync(0xffffffffu, fail)) break;
+    const uint64_t y0 = __shfl_sync(0xffffffffu, y, 0);
+    const bool same = !(lane < (int)nimg) || y == y0;
+    if (__all_sync(0xffffffffu, same)) {
+      x = y0;
+      ok = true;
+      break;
+    }
+    if (k == first_item) break;
+  }
+  if (lane == 0) {
     sh.true_entry = x;
+    sh.resolved = ok ? 1u : 0u;
+  }
+}
+
+// Emission from entry x (file-relative): the cuts in (x, exit] into the
+// item's slot, by following the walked nodes when x is a tabulated entry,
+// else by stepping the chunker on the bitmaps.  Thread 0.
+__device__ void seg_emit(SegShared &sh, const DevParams &p, const SegSmem &m,
+                         const WsPtrs &ws, uint64_t x, bool use_nodes) {
+  const int64_t B = sh.B;
+  const Bits bits{m.E, m.O};
+  const uint32_t end_rel = (uint32_t)((int64_t)sh.n_f - B);
+  const uint32_t q_rel = (uint32_t)((int64_t)sh.q_s - B);
+  const uint32_t item = sh.item;
+  const uint32_t xr = (uint32_t)((int64_t)x - B);
+  uint64_t *out = ws.slot + (uint64_t)item * ws.slot_cap;
+  uint32_t nout = 0;
+  uint64_t exit_pos = x;
+  int node = -1;
+  if (use_nodes) {
+    uint32_t lo = 0, hi = sh.K;
+    while (lo < hi) {
+      const uint32_t mid = (lo + hi) >> 1;
+      const uint32_t v = m.node_pos[mid];
+      if (v == xr) { node = (int)mid; break; }
+      if (v < xr) lo = mid + 1; else hi = mid;
+    }
+  }
+  if (node >= 0) {
+    uint32_t n = (uint32_t)node;
+    while (m.node_next[n] != kNil && nout < ws.slot_cap) {
+      n = m.node_next[n];
+      out[nout++] = (uint64_t)(B + (int64_t)m.node_pos[n]);
+    }
+    exit_pos = (uint64_t)(B + (int64_t)m.node_pos[n]);
+  } else {
+    uint32_t c = xr;
+    while (c < q_rel && nout < ws.slot_cap) {
+      c = chunk_step(bits, p, c, end_rel);
+      out[nout++] = (uint64_t)(B + (int64_t)c);
+    }
+    exit_pos = (uint64_t)(B + (int64_t)c);
+  }
+  ws.count[item] = nout;
+  ws.incl[item] = exit_pos;
+  ws.entry[item] = x;
+  __threadfence();
+  atomicOr(&ws.state[item], F_RESOLVED);
+}
+
+__global__ void __launch_bounds__(512)
+segment_kernel(Geom g, DevParams p, WsPtrs ws) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ SegShared sh;
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    sh.item = atomicAdd(&ws.hdr->ticket, 1u);
+    sh.nitems = ws.hdr->nitems;
   }
   __syncthreads();
-
+  if (sh.item >= sh.nitems) return;
   if (tid == 0) {
-    const uint64_t x = sh.true_entry;
-    const uint32_t xr = (uint32_t)((int64_t)x - B);
-    uint64_t *out = ws.slot + (uint64_t)item * ws.slot_cap;
-    uint32_t nout = 0;
-    uint64_t exit_pos = x;
-    int node = -1;
-    if (!sh.abnormal) {
-      uint32_t lo2 = 0, hi2 = sh.K;
-      while (lo2 < hi2) {
-        const uint32_t mid = (lo2 + hi2) >> 1;
-        const uint32_t v = node_pos[mid];
-        if (v == xr) { node = (int)mid; break; }
-        if (v < xr) lo2 = mid + 1; else hi2 = mid;
-      }
+    const uint32_t item = sh.item;
+    const uint32_t f = find_file(ws.seg_base, g.nfiles, item);
+    seg_setup(sh, g, p, item, f, item - ws.seg_base[f], ws.seg_base[f]);
+  }
+  __syncthreads();
+  const SegSmem m = carve(smem_raw, sh.W);
+  seg_bitmaps(sh, g, p, m);
+  __syncthreads();
+  seg_walk_publish(sh, p, m, ws);
+  __syncthreads();
+  if (sh.seg == 0) {
+    if (tid == 0) {
+      sh.true_entry = 0;
+      sh.resolved = 1;
     }
-    if (node >= 0) {
-      uint32_t n = (uint32_t)node;
-      while (node_next[n] != kNil && nout < ws.slot_cap) {
-        n = node_next[n];
-        out[nout++] = (uint64_t)(B + (int64_t)node_pos[n]);
+  } else if (tid < 32) {
+    seg_lookback(sh, g, ws);
+  }
+  __syncthreads();
+  if (tid == 0) {
+    if (sh.resolved) seg_emit(sh, p, m, ws, sh.true_entry, !sh.abnormal);
+    else atomicOr(&ws.state[sh.item], F_UNRESOLVED);
+  }
+}
+
+// Verify: item s of a file is consistent when it was resolved and its entry
+// equals the exit its predecessor computed.  By induction from the file start
+// (always a true entry), a file whose items are all consistent is exact.  The
+// first inconsistent item of each file is recorded for the repair pass.
+__global__ void verify_kernel(Geom g, WsPtrs ws) {
+  const uint32_t nitems = ws.hdr->nitems;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nitems;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t f = find_file(ws.seg_base, g.nfiles, (uint32_t)i);
+    const uint32_t s = (uint32_t)i - ws.seg_base[f];
+    const uint32_t st = ws.state[i];
+    bool ok = (st & F_RESOLVED) != 0;
+    if (ok && s > 0) ok = ws.entry[i] == ws.incl[i - 1] && (ws.state[i - 1] & F_RESOLVED);
+    if (!ok) atomicMin(&ws.first_bad[f], s);
+  }
+}
+
+// Repair: one block per file with an inconsistent item.  From the first
+// inconsistent item on, items are re-chunked from the true exit of their
+// predecessor (bitmaps rebuilt from the input); an item whose recorded entry
+// already equals that exit is kept.
+__global__ void __launch_bounds__(512)
+repair_kernel(Geom g, DevParams p, WsPtrs ws) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ SegShared sh;
+  __shared__ uint32_t s_run;
+  const int tid = threadIdx.x;
+  for (uint64_t f = blockIdx.x; f < g.nfiles; f += gridDim.x) {
+    const uint32_t fb = ws.first_bad[f];
+    if (fb == 0xffffffffu) continue;
+    const uint32_t base = ws.seg_base[f];
+    const uint32_t nseg = ws.seg_base[f + 1] - base;
+    uint64_t cur = ws.incl[base + fb - 1];  // fb >= 1: item 0 is always exact
+    for (uint32_t s = fb; s < nseg; ++s) {
+      const uint32_t item = base + s;
+      if (tid == 0) {
+        const uint32_t st = ws.state[item];
+        s_run = !((st & F_RESOLVED) && ws.entry[item] == cur);
+        if (s_run) seg_setup(sh, g, p, item, (uint32_t)f, s, base);
       }
-      exit_pos = (uint64_t)(B + (int64_t)node_pos[n]);
-    } else {
-      uint32_t c = xr;
-      while (c < q_rel && nout < ws.slot_cap) {
-        c = chunk_step(bits, p, c, end_rel);
-        out[nout++] = (uint64_t)(B + (int64_t)c);
+      __syncthreads();
+      if (s_run) {
+        const SegSmem m = carve(smem_raw, sh.W);
+        seg_bitmaps(sh, g, p, m);
+        __syncthreads();
+        if (tid == 0) seg_emit(sh, p, m, ws, cur, false);
       }
-      exit_pos = (uint64_t)(B + (int64_t)c);
+      __syncthreads();
+      cur = *((volatile uint64_t *)&ws.incl[item]);
+      __syncthreads();
     }
-    ws.count[item] = nout;
-    ws.incl[item] = exit_pos;
-    __threadfence();
-    atomicOr(&ws.state[item], F_INCL);
   }
 }
 
@@ -925,6 +1051,8 @@ Layout make_layout(const seqcdc_params_t *p, uint64_t total, uint64_t nfiles,
   l.ftile = take(l.nftiles * 4);
   l.state = take(l.imax * 4);
   l.incl = take(l.imax * 8);
+  l.entry = take(l.imax * 8);
+  l.first_bad = take((nfiles + 1) * 4);
   l.count = take(l.imax * 4);
   l.img_n = take(l.imax * 4);
   l.img = take(l.imax * kMaxImage * 8);
@@ -944,6 +1072,8 @@ WsPtrs ws_ptrs(void *d_ws, const Layout &l) {
   w.ftile = reinterpret_cast<uint32_t *>(b + l.ftile);
   w.state = reinterpret_cast<uint32_t *>(b + l.state);
   w.incl = reinterpret_cast<uint64_t *>(b + l.incl);
+  w.entry = reinterpret_cast<uint64_t *>(b + l.entry);
+  w.first_bad = reinterpret_cast<uint32_t *>(b + l.first_bad);
   w.count = reinterpret_cast<uint32_t *>(b + l.count);
   w.img_n = reinterpret_cast<uint32_t *>(b + l.img_n);
   w.img = reinterpret_cast<uint64_t *>(b + l.img);
@@ -981,11 +1111,18 @@ int run(const seqcdc_params_t *p, const uint8_t *d_data, uint64_t total,
   if (smem > 48 * 1024 && smem > configured) {
     if (cudaFuncSetAttribute(segment_kernel,
                              cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess ||
+        cudaFuncSetAttribute(repair_kernel,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem) != cudaSuccess)
       return SEQCDC_ECUDA;
     configured = smem;
   }
   segment_kernel<<<(unsigned)l.imax, threads, smem, st>>>(g, dp, w);
+  const uint64_t vblocks = (l.imax + 255) / 256;
+  verify_kernel<<<(unsigned)(vblocks < 4096 ? vblocks : 4096), 256, 0, st>>>(g, w);
+  const uint64_t rblocks = nfiles ? nfiles : 1;
+  repair_kernel<<<(unsigned)(rblocks < 65535 ? rblocks : 65535), threads, smem, st>>>(g, dp, w);
   count_tiles_kernel<<<(unsigned)l.nitiles, kItemTile, 0, st>>>(w);
   emit_kernel<<<(unsigned)l.nitiles, kItemTile, 0, st>>>(g, w, d_cuts, cap,
                                                           d_cut_offsets, d_count);
