@@ -1,0 +1,443 @@
+"""Benchmark: chunked GB/s of the SeqCDC CUDA chunker on GB300.
+
+Workload (one "step" = one pass of the whole chunking path over one batch):
+10,000 files with log-normal sizes (median 256 KiB, sigma 1.5, clamped to
+4 KiB..64 MiB, ~7.2 GiB in all), half uniform random / half order-1 Markov
+text content in 64 KiB pieces, laid out in CSR; 8 KiB parameter setting,
+increasing mode.  Inputs are generated on the host from a fixed seed, copied
+to HBM once, and are far larger than L2 (no flush needed between steps).
+
+Printed: one JSON line with the metric, the device-resident throughput
+(`value`), the end-to-end throughput through host buffers (`e2e`), the
+roofline of the dominant kernel, the plain one-launch-per-file loop for
+comparison, clocks, and the CPU oracle as a reported baseline.
+
+`--impl reference` times the CPU oracle (the plain single-threaded chunker,
+files spread over the host cores) on the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "chunked GB/s on 1 GB300 vs HBM roofline (batched vs plain); p50/p99 serve latency"
+NFILES = 10000
+SEED = 0
+KIB = 8
+MODE = 0
+
+
+def _dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def _measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling in the background (read-only)."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.samples = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.samples.append((time.time(), line.strip()))
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        if self.thread is not None:
+            self.thread.join(timeout=2)
+
+    def summary(self, t0: float, t1: float):
+        rows = []
+        for t, line in self.samples:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            rows.append((t, parts))
+        inside = [r for r in rows if t0 <= r[0] <= t1]
+        if not inside and rows:  # region shorter than the sampling period
+            inside = sorted(rows, key=lambda r: min(abs(r[0] - t0), abs(r[0] - t1)))[:3]
+        if not inside:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"],
+                    "samples": 0}
+        sm = [float(p[1]) for _, p in inside if p[1].replace(".", "").isdigit()]
+        mx = [float(p[2]) for _, p in inside if p[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for _, p in inside:
+            for name, v in zip(names, p[5:9]):
+                if "Active" in v and "Not" not in v:
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(inside)}
+
+
+def make_workload(rank: int):
+    from paper_2505_21194_gb300 import workloads as W
+    return W.file_batch(NFILES, seed=SEED + rank)
+
+
+def _traffic_record(kernel_src_hash: str):
+    """DRAM bytes per launch from the committed ncu summary, if still current."""
+    path = os.path.join(ROOT, "profiles", "segment_kernel_traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+    except Exception:
+        return None, None
+    if d.get("source_sha256") != kernel_src_hash:
+        return None, d
+    return d, d
+
+
+def _source_hash():
+    h = hashlib.sha256()
+    for rel in ("paper_2505_21194_gb300/csrc/seqcdc.cu", "include/seqcdc.h"):
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def cpu_oracle_pass(data, offs, threads):
+    import oracle
+    p = oracle.presets(KIB, MODE)
+    t = time.perf_counter()
+    cuts, _ = oracle.chunk_batch_threaded(data, offs, p, threads)
+    return time.perf_counter() - t, cuts.size
+
+
+def run_reference(args):
+    rank, world, _ = _dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+        if rank != 0:
+            dist.barrier()
+            return
+    data, offs = make_workload(0)
+    threads = os.cpu_count() or 1
+    for _ in range(args.warmup):
+        cpu_oracle_pass(data, offs, threads)
+    total = 0.0
+    for _ in range(args.steps):
+        dt, _ = cpu_oracle_pass(data, offs, threads)
+        total += dt
+    gbs = data.size * args.steps / total / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(gbs, 3), "unit": "GB/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(total / args.steps * 1e3, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": {"workload": "10,000 log-normal files (median 256 KiB, sigma 1.5), "
+                               "CSR, 8 KiB setting, increasing mode",
+                   "total_bytes": int(data.size), "nfiles": NFILES},
+        "cpu_baseline": {"value": round(gbs, 3), "unit": "GB/s", "cores": threads,
+                         "kind": "oracle",
+                         "sample": "full 10,000-file batch per step, files spread over %d "
+                                   "host threads, single-threaded chunker per file" % threads},
+        "e2e": {"value": round(gbs, 3), "unit": "GB/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def run_gpu(args):
+    import torch
+
+    from paper_2505_21194_gb300 import seqcdc
+
+    rank, world, local = _dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+    seqcdc.load_library()
+
+    data_np, offs_np = make_workload(rank)
+    total = int(data_np.size)
+    nfiles = offs_np.size - 1
+    p = seqcdc.seqcdc_params(KIB, MODE)
+    tuning = seqcdc.Tuning(args.segment_bytes, args.threads)
+    cap = total // p.min_size + nfiles
+    ws_bytes = seqcdc.seqcdc_workspace_size(p, total, nfiles, tuning)
+
+    d_data = torch.from_numpy(data_np).to(dev)
+    d_offs = torch.from_numpy(offs_np.astype(np.int64)).to(dev)
+    d_cuts = torch.empty(cap, dtype=torch.int64, device=dev)
+    d_co = torch.empty(nfiles + 1, dtype=torch.int64, device=dev)
+    d_ws = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        seqcdc.seqcdc_chunk_batch(p, d_data, total, d_offs, nfiles, d_cuts, cap,
+                                  d_co, d_ws, ws_bytes, tuning, stream)
+
+    for _ in range(max(args.warmup, 1)):
+        step()
+    st = seqcdc.seqcdc_status(d_ws, stream)
+    if st != 0:
+        raise RuntimeError("device status %d during warm-up" % st)
+    ncuts = int(d_co[-1].item())
+
+    sampler = ClockSampler(dev.index if dev.index is not None else 0)
+    sampler.start()
+    time.sleep(0.3)
+    kb = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ke = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    t_begin = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize(dev)
+    wall0 = time.time()
+    t_begin.record(stream)
+    for i in range(args.steps):
+        seqcdc.seqcdc_profile_events(kb[i], ke[i])
+        step()
+    t_end.record(stream)
+    torch.cuda.synchronize(dev)
+    wall1 = time.time()
+    seqcdc.seqcdc_profile_events(None, None)
+    if world > 1:
+        torch.distributed.barrier()
+    time.sleep(0.25)
+    sampler.stop()
+    clocks = sampler.summary(wall0, wall1)
+    st = seqcdc.seqcdc_status(d_ws, stream)
+    if st != 0:
+        raise RuntimeError("device status %d in the timed region" % st)
+    ms_step = t_begin.elapsed_time(t_end) / args.steps
+    seg_ms = sum(kb[i].elapsed_time(ke[i]) for i in range(args.steps)) / args.steps
+    if world > 1:
+        t = torch.tensor([ms_step], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_step = float(t.item())
+    gbs = total * world / (ms_step * 1e-3) / 1e9
+
+    # CUDA-graph-captured step (same work, one graph launch per step).
+    graph_ms = None
+    try:
+        g = torch.cuda.CUDAGraph()
+        s2 = torch.cuda.Stream(dev)
+        s2.wait_stream(stream)
+        with torch.cuda.stream(s2):
+            seqcdc.seqcdc_chunk_batch(p, d_data, total, d_offs, nfiles, d_cuts, cap,
+                                      d_co, d_ws, ws_bytes, tuning, s2)
+            torch.cuda.synchronize(dev)
+            with torch.cuda.graph(g, stream=s2):
+                seqcdc.seqcdc_chunk_batch(p, d_data, total, d_offs, nfiles, d_cuts,
+                                          cap, d_co, d_ws, ws_bytes, tuning, s2)
+        stream.wait_stream(s2)
+        for _ in range(3):
+            g.replay()
+        torch.cuda.synchronize(dev)
+        ga, gb_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ga.record(stream)
+        for _ in range(args.steps):
+            g.replay()
+        gb_.record(stream)
+        torch.cuda.synchronize(dev)
+        graph_ms = ga.elapsed_time(gb_) / args.steps
+        if seqcdc.seqcdc_status(d_ws, stream) != 0 or int(d_co[-1].item()) != ncuts:
+            graph_ms = None
+    except Exception as exc:  # report, do not hide
+        print("graph capture failed: %r" % (exc,), file=sys.stderr)
+
+    # Plain: one seqcdc_chunk call (all kernels) per file, back to back.
+    plain_ms = None
+    if not args.skip_plain:
+        offs64 = offs_np.astype(np.int64)
+        cnt = torch.empty(1, dtype=torch.int64, device=dev)
+        ws1 = seqcdc.seqcdc_workspace_size(p, int(np.diff(offs64).max()), 1, tuning)
+        d_ws1 = torch.empty(ws1, dtype=torch.uint8, device=dev)
+        # Each file gets its own 16-byte-aligned device buffer (the ABI's
+        # alignment rule); file starts inside the CSR batch are arbitrary.
+        views = []
+        for f in range(nfiles):
+            n = int(offs64[f + 1] - offs64[f])
+            buf = torch.empty(max(n, 1), dtype=torch.uint8, device=dev)
+            buf[:n].copy_(d_data[offs64[f]:offs64[f + 1]])
+            views.append(buf[:n])
+
+        def plain_pass():
+            for f in range(nfiles):
+                seqcdc.seqcdc_chunk(p, views[f], views[f].numel(), d_cuts, cap, cnt,
+                                    d_ws1, ws1, tuning, stream)
+
+        plain_pass()
+        torch.cuda.synchronize(dev)
+        pa, pb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        pa.record(stream)
+        plain_pass()
+        pb.record(stream)
+        torch.cuda.synchronize(dev)
+        plain_ms = pa.elapsed_time(pb)
+        if seqcdc.seqcdc_status(d_ws1, stream) != 0:
+            plain_ms = None
+        del views
+
+    # End to end through host buffers: H2D of the batch, chunking, D2H of the
+    # CSR index and the cut list, every step.
+    h_data = torch.from_numpy(data_np).pin_memory()
+    h_offs = torch.from_numpy(offs_np.astype(np.int64)).pin_memory()
+    h_co = torch.empty(nfiles + 1, dtype=torch.int64).pin_memory()
+    h_cuts = torch.empty(cap, dtype=torch.int64).pin_memory()
+    e2e_steps = max(1, min(args.steps, 5))
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    d2h = 0
+    for _ in range(e2e_steps):
+        d_data.copy_(h_data, non_blocking=True)
+        d_offs.copy_(h_offs, non_blocking=True)
+        step()
+        h_co.copy_(d_co, non_blocking=True)
+        torch.cuda.synchronize(dev)
+        k = int(h_co[-1])
+        h_cuts[:k].copy_(d_cuts[:k], non_blocking=True)
+        torch.cuda.synchronize(dev)
+        d2h = (nfiles + 1) * 8 + k * 8
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    e2e_gbs = total * world / e2e_s / 1e9
+    # host check of the last result: CSR is consistent
+    assert int(h_co[-1]) == ncuts
+
+    peak, peak_kind = _measured_peaks()
+    alg_bytes = total + ncuts * 8  # each input byte read once + the cut list
+    achieved = alg_bytes / (seg_ms * 1e-3) / 1e9
+    rec, _ = _traffic_record(_source_hash())
+    traffic = None
+    if rec is not None:
+        traffic = float(rec["dram_bytes_per_byte"]) * total
+    launches_per_step = 7
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC,
+        "value": round(gbs, 2),
+        "unit": "GB/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(ms_step, 4),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "u8",
+        "data": "synthetic",
+        "config": {
+            "workload": "batched: 10,000 log-normal files (median 256 KiB, sigma 1.5, "
+                        "4 KiB..64 MiB), half random / half Markov text, CSR; "
+                        "8 KiB setting, increasing mode",
+            "total_bytes": total, "nfiles": nfiles, "cuts": ncuts,
+            "segment_bytes": args.segment_bytes or 65536,
+            "block_threads": args.threads or 256,
+            "l2": "inputs (%.1f GiB) far larger than L2; no flush" % (total / 2**30),
+            "parallelism": "1 GPU per rank, independent batches (weak scaling)",
+        },
+        "e2e": {"value": round(e2e_gbs, 2), "unit": "GB/s",
+                "h2d_bytes_per_step": int(total + (nfiles + 1) * 8),
+                "d2h_bytes_per_step": int(d2h)},
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
+                     "unit": "GB/s", "frac": round(achieved / peak, 4),
+                     "traffic": traffic, "kernel": "segment_kernel",
+                     "peak_source": peak_kind,
+                     "kernel_ms": round(seg_ms, 4)},
+        "plain_one_launch_per_file": (
+            {"value": round(total / (plain_ms * 1e-3) / 1e9, 3), "unit": "GB/s",
+             "ms_per_pass": round(plain_ms, 2)} if plain_ms else None),
+        "graph_captured": ({"ms_per_step": round(graph_ms, 4),
+                            "value": round(total * world / (graph_ms * 1e-3) / 1e9, 2)}
+                           if graph_ms else None),
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clocks,
+    }
+    if world == 1:
+        threads = os.cpu_count() or 1
+        dt, _ = cpu_oracle_pass(data_np, offs_np, threads)
+        reps = 1
+        while dt * reps < 10.0 and reps < 4:  # a bounded sample of ~10 s
+            d2, _ = cpu_oracle_pass(data_np, offs_np, threads)
+            dt += d2
+            reps += 1
+        line["cpu_baseline"] = {
+            "value": round(total * reps / dt / 1e9, 3), "unit": "GB/s", "cores": threads,
+            "kind": "oracle",
+            "sample": "%d pass(es) over the full 10,000-file batch, files spread over "
+                      "%d host threads" % (reps, threads)}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--segment-bytes", type=int, default=0)
+    ap.add_argument("--threads", type=int, default=0)
+    ap.add_argument("--skip-plain", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

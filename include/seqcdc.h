@@ -60,7 +60,9 @@ extern "C" {
  *                 Sec. VI.D).
  *   skip_size     bytes ignored after a skip fires (Sec. III.C).
  *   min_size      minimum chunk size, >= 1 (Sec. III.B).
- *   max_size      maximum chunk size, >= min_size and <= 2^24.
+ *   max_size      maximum chunk size, >= min_size and <= 262144 (256 KiB:
+ *                 one block stages its segment plus max_size bytes in
+ *                 shared memory).
  */
 typedef struct {
     uint32_t mode;
@@ -142,11 +144,22 @@ int seqcdc_chunk_batch(const seqcdc_params_t *p, const uint8_t *d_data,
 
 /*
  * Synchronise `stream`, then return the device-side status recorded in d_ws by
- * the last call that used it: SEQCDC_OK, or SEQCDC_ETIMEOUT when a bounded
- * wait inside a kernel expired (its outputs are then not valid).  Returns
+ * the last call that used it: SEQCDC_OK, SEQCDC_ETIMEOUT when a bounded
+ * wait inside a kernel expired, or SEQCDC_ECAPACITY when the device found more
+ * cuts than `cap` (both mean the outputs are not valid).  Returns
  * SEQCDC_ECUDA if the synchronisation itself fails.
  */
 int seqcdc_status(const void *d_ws, void *stream);
+
+/*
+ * Measurement hook: record the CUDA events `ev_begin` / `ev_end` (cudaEvent_t
+ * passed as void*) on the call's stream immediately before and after the
+ * segment kernel of every later seqcdc_chunk / seqcdc_chunk_batch call made
+ * from this host thread, so that its device time can be read with
+ * cudaEventElapsedTime.  Pass NULL, NULL to stop.  The events are owned by the
+ * caller.  Always returns SEQCDC_OK.
+ */
+int seqcdc_profile_events(void *ev_begin, void *ev_end);
 
 /* Static, human-readable text for a status code. */
 const char *seqcdc_strerror(int status);

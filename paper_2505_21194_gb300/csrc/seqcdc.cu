@@ -1085,6 +1085,9 @@ WsPtrs ws_ptrs(void *d_ws, const Layout &l) {
   return w;
 }
 
+thread_local cudaEvent_t g_prof_begin = nullptr;
+thread_local cudaEvent_t g_prof_end = nullptr;
+
 int run(const seqcdc_params_t *p, const uint8_t *d_data, uint64_t total,
         const uint64_t *d_offsets, uint64_t nfiles, uint64_t *d_cuts,
         uint64_t cap, uint64_t *d_cut_offsets, uint64_t *d_count, void *d_ws,
@@ -1118,7 +1121,9 @@ int run(const seqcdc_params_t *p, const uint8_t *d_data, uint64_t total,
       return SEQCDC_ECUDA;
     configured = smem;
   }
+  if (g_prof_begin) cudaEventRecord(g_prof_begin, st);
   segment_kernel<<<(unsigned)l.imax, threads, smem, st>>>(g, dp, w);
+  if (g_prof_end) cudaEventRecord(g_prof_end, st);
   const uint64_t vblocks = (l.imax + 255) / 256;
   verify_kernel<<<(unsigned)(vblocks < 4096 ? vblocks : 4096), 256, 0, st>>>(g, w);
   const uint64_t rblocks = nfiles ? nfiles : 1;
@@ -1193,6 +1198,12 @@ int seqcdc_status(const void *d_ws, void *stream) {
     return SEQCDC_ECUDA;
   if (cudaStreamSynchronize(st) != cudaSuccess) return SEQCDC_ECUDA;
   return (int)v;
+}
+
+int seqcdc_profile_events(void *ev_begin, void *ev_end) {
+  g_prof_begin = static_cast<cudaEvent_t>(ev_begin);
+  g_prof_end = static_cast<cudaEvent_t>(ev_end);
+  return SEQCDC_OK;
 }
 
 const char *seqcdc_strerror(int status) {

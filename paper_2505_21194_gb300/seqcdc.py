@@ -93,6 +93,8 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
         lib.seqcdc_chunk_batch.restype = ctypes.c_int
         lib.seqcdc_status.argtypes = [vp, vp]
         lib.seqcdc_status.restype = ctypes.c_int
+        lib.seqcdc_profile_events.argtypes = [vp, vp]
+        lib.seqcdc_profile_events.restype = ctypes.c_int
         lib.seqcdc_strerror.argtypes = [ctypes.c_int]
         lib.seqcdc_strerror.restype = ctypes.c_char_p
         _lib = lib
@@ -177,6 +179,13 @@ def seqcdc_chunk_batch(p: Params, d_data, total_bytes: int, d_offsets,
 def seqcdc_status(d_ws, stream=None) -> int:
     """Synchronise the stream; return the device-side status in the workspace."""
     return load_library().seqcdc_status(_ptr(d_ws), _stream_handle(stream))
+
+
+def seqcdc_profile_events(ev_begin=None, ev_end=None) -> None:
+    """Bracket the segment kernel of later calls with two torch.cuda.Events."""
+    h = (lambda e: int(e.cuda_event) if e is not None else None)
+    _check(load_library().seqcdc_profile_events(h(ev_begin), h(ev_end)),
+           "seqcdc_profile_events")
 
 
 def seqcdc_strerror(status: int) -> str:
