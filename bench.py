@@ -121,9 +121,9 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(inside)}
 
 
-def make_workload(rank: int):
+def make_workload(rank: int, nfiles: int = NFILES):
     from paper_2505_21194_gb300 import workloads as W
-    return W.file_batch(NFILES, seed=SEED + rank)
+    return W.file_batch(nfiles, seed=SEED + rank)
 
 
 def _traffic_record(kernel_src_hash: str):
@@ -163,7 +163,7 @@ def run_reference(args):
         if rank != 0:
             dist.barrier()
             return
-    data, offs = make_workload(0)
+    data, offs = make_workload(0, args.nfiles)
     threads = os.cpu_count() or 1
     for _ in range(args.warmup):
         cpu_oracle_pass(data, offs, threads)
@@ -207,7 +207,7 @@ def run_gpu(args):
     torch.cuda.set_device(dev)
     seqcdc.load_library()
 
-    data_np, offs_np = make_workload(rank)
+    data_np, offs_np = make_workload(rank, args.nfiles)
     total = int(data_np.size)
     nfiles = offs_np.size - 1
     p = seqcdc.seqcdc_params(KIB, MODE)
@@ -240,6 +240,8 @@ def run_gpu(args):
     ke = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     t_begin = torch.cuda.Event(enable_timing=True)
     t_end = torch.cuda.Event(enable_timing=True)
+    for e in kb + ke:  # torch creates the CUDA event on its first record
+        e.record(stream)
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize(dev)
@@ -379,9 +381,9 @@ def run_gpu(args):
         "dtype": "u8",
         "data": "synthetic",
         "config": {
-            "workload": "batched: 10,000 log-normal files (median 256 KiB, sigma 1.5, "
+            "workload": "batched: %d log-normal files (median 256 KiB, sigma 1.5, "
                         "4 KiB..64 MiB), half random / half Markov text, CSR; "
-                        "8 KiB setting, increasing mode",
+                        "8 KiB setting, increasing mode" % nfiles,
             "total_bytes": total, "nfiles": nfiles, "cuts": ncuts,
             "segment_bytes": args.segment_bytes or 65536,
             "block_threads": args.threads or 256,
@@ -405,7 +407,7 @@ def run_gpu(args):
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clocks,
     }
-    if world == 1:
+    if world == 1 and not args.no_cpu:
         threads = os.cpu_count() or 1
         dt, _ = cpu_oracle_pass(data_np, offs_np, threads)
         reps = 1
@@ -430,6 +432,10 @@ def main():
     ap.add_argument("--segment-bytes", type=int, default=0)
     ap.add_argument("--threads", type=int, default=0)
     ap.add_argument("--skip-plain", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true",
+                    help="skip the CPU-oracle baseline (profiling runs)")
+    ap.add_argument("--nfiles", type=int, default=NFILES,
+                    help="files in the batch (default: the 10,000-file workload)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
