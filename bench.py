@@ -232,6 +232,7 @@ def run_gpu(args):
     if st != 0:
         raise RuntimeError("device status %d during warm-up" % st)
     ncuts = int(d_co[-1].item())
+    path_stats = seqcdc.seqcdc_stats(d_ws, stream)
 
     sampler = ClockSampler(dev.index if dev.index is not None else 0)
     sampler.start()
@@ -405,6 +406,7 @@ def run_gpu(args):
                             "value": round(total * world / (graph_ms * 1e-3) / 1e9, 2)}
                            if graph_ms else None),
         "gpu_launches": launches_per_step * args.steps,
+        "path_stats": path_stats,
         "clocks": clocks,
     }
     if world == 1 and not args.no_cpu:

@@ -10,33 +10,36 @@
 //               region; when the count reaches SkipTrigger the next SkipSize
 //               bytes are ignored and both counters restart.
 //   Sec. IV/VI  a chunk is cut at max_size if no run completes first.
-// The scan region of Sec. III.D is evaluated here as bitmaps: T[j] marks a
-// target-order pair (b[j-1], b[j]), O[j] an opposing pair, and
+// The scan of Sec. III.D is evaluated on bitmaps: T[j] marks a target-order
+// pair (b[j-1], b[j]), O[j] an opposing pair, and
 // E[j] = T[j] & T[j-1] & ... & T[j-SeqLength+2] marks the last byte of a
-// boundary run -- the AND of SeqLength-1 shifted comparison masks of
-// Sec. III.D.  A region starting at byte i ends at the first E bit at or after
-// i + SeqLength - 1 (a cut after it) or at the SkipTrigger-th O bit after i
-// (a skip), whichever comes first.
+// boundary run (the AND of SeqLength-1 shifted comparison masks of
+// Sec. III.D).  A scan region starting at byte i ends at the first E bit at or
+// after i + SeqLength - 1 (cut right after it) or at the SkipTrigger-th O bit
+// after i (skip), whichever comes first -- the first-set-bit and n-th-set-bit
+// queries of Sec. III.D.
 //
-// Parallel structure (not in the paper, which scans sequentially):
-//   plan kernels   split every file into segments of L bytes (items).
-//   segment kernel one thread block per item.  It stages the item's bytes
-//                  plus max_size bytes of look-ahead, builds the E and O
-//                  bitmaps in shared memory (SWAR byte compares, 16 bytes per
-//                  thread per step), and then walks the chunk chain from EVERY
-//                  position a chunk of this file could start at inside the
-//                  item's first max_size bytes (each natural cut is E+1), with
-//                  chains that reach a common cut merged through a shared-memory
-//                  hash.  The result is a table entry -> exit (first cut at or
-//                  after the item end) and the set of distinct exits.  The
-//                  table is published; the block then finds its true entry by
-//                  a bounded look-back over its predecessors' tables (a
-//                  single-valued exit set settles it at once) and emits its
-//                  true cuts from shared memory.
-//   compact        exclusive scan of per-item cut counts, then a copy into the
-//                  caller's CSR output.
-// The output equals a sequential scan's exactly: every cut of an item is
-// produced by the same state machine from a proven true chunk start.
+// Parallel structure (the paper scans one stream sequentially):
+//   plan     split every file into segments ("items") of L bytes.
+//   segment  one thread block per item.  The block builds the E and O bitmaps
+//            of its L bytes plus max_size bytes of look-ahead in shared memory
+//            (SWAR byte compares, 16 bytes per thread step) with per-256-byte
+//            summaries, then walks the chunk chain from EVERY natural cut
+//            (E bit + 1) in the item's first max_size bytes, merging chains
+//            that meet at a common cut.  Each entry thus maps to an exit (the
+//            first cut at or after the item end).  The block publishes the set
+//            of distinct exits ("image", <= 32 values), then the map from its
+//            predecessor's image to its own exits (a <= 32-entry function),
+//            and finds its true entry by decoupled look-back: composing
+//            predecessors' maps until one that has published its true exit.
+//            It then emits its cuts from shared memory.
+//   verify   check entry[s] == exit[s-1] along every file (by induction from
+//            the file start the output is then exact); a repair pass
+//            re-chunks from the first inconsistent item (needed only when a
+//            forced cut at max_size entered an item away from its natural
+//            entries, e.g. inside long runs of equal bytes).
+//   compact  exclusive scan of per-item cut counts and copy into the
+//            caller's CSR output.
 
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -49,27 +52,25 @@ namespace {
 // ---------------------------------------------------------------------------
 // Limits and layout constants.
 // ---------------------------------------------------------------------------
-constexpr int kMaxEntries = 512;    // entry candidates tabulated per item
-constexpr int kMaxNodes = 1024;     // distinct cut positions per item walk
-constexpr int kHashSlots = 2048;    // open-addressing slots (power of two)
-constexpr int kMaxImage = 32;       // distinct exits published per item (one per lane)
-constexpr int kFileTile = 1024;     // files per plan block
-constexpr int kItemTile = 256;      // items per compaction block
+constexpr int kMaxEntries = 512;   // natural entries walked per item
+constexpr int kMaxNodes = 1024;    // distinct cut positions per item walk
+constexpr int kHashSlots = 2048;   // open-addressing slots (power of two)
+constexpr int kMaxImage = 32;      // distinct exits published per item (one per lane)
+constexpr int kFileTile = 1024;    // files per plan block
+constexpr int kItemTile = 256;     // items per compaction block
 constexpr uint32_t kMaxSeqLength = 16;
 constexpr uint64_t kMaxMaxSize = 262144;
-constexpr int64_t kLookBackDepth = 6;
 constexpr uint64_t kWaitNs = 2000000000ull;  // 2 s bound on any device wait
 
-// Item state bits.
-constexpr uint32_t F_TABLE = 1u;     // exit set (and maybe table) published
-constexpr uint32_t F_SINGLE = 2u;    // exit set has exactly one element
-constexpr uint32_t F_NOTABLE = 4u;   // no usable table (too many exits)
-constexpr uint32_t F_RESOLVED = 8u;  // entry chosen, cuts and exit published
-constexpr uint32_t F_ABNORMAL = 16u; // no walk from all entries was possible
-constexpr uint32_t F_UNRESOLVED = 32u;  // look-back could not choose an entry
+// Item state bits (set once, in this order of availability).
+constexpr uint32_t F_IMG = 1u;     // image (distinct exits) published
+constexpr uint32_t F_NOIMG = 2u;   // no image (more than kMaxImage exits)
+constexpr uint32_t F_AGG = 4u;     // map predecessor image -> exits published
+constexpr uint32_t F_NOAGG = 8u;   // no such map (predecessor had no image)
+constexpr uint32_t F_INCL = 16u;   // true exit, entry and cuts published
 
 constexpr uint16_t kNil = 0xFFFFu;
-constexpr uint32_t kInvalidPos = 0xFFFFFFFFu;
+constexpr uint32_t kNone = 0xFFFFFFFFu;
 
 struct DevParams {
   uint32_t mode;
@@ -85,12 +86,24 @@ struct WsHeader {
   uint32_t status;
   uint32_t ticket;
   uint32_t nitems;
-  uint32_t pad[61];
+  uint32_t stats[8];  // see seqcdc_stats()
+  uint32_t pad[53];
+};
+
+enum : uint32_t {
+  ST_ITEMS = 0,         // items processed
+  ST_ABNORMAL = 1,      // items whose natural entries could not all be walked
+  ST_NOIMG = 2,         // items with more distinct exits than published
+  ST_LB_WAITS = 3,      // look-backs that had to wait for a true exit
+  ST_INCONSISTENT = 4,  // items whose entry disagreed with the predecessor
+  ST_RECOMPUTED = 5,    // items re-chunked by the repair pass
+  ST_REPLAYED = 6,      // emissions by stepping (entry was not a natural cut)
+  ST_LB_STEPS = 7,      // total look-back depth
 };
 
 struct Layout {
   size_t hdr, seg_base, ftile, state, incl, entry, first_bad, count, img_n,
-      img, tab_n, tab, slot, itile, total;
+      img, agg, slot, itile, total;
   uint64_t imax;     // upper bound on items
   uint64_t nftiles;  // plan tiles
   uint64_t nitiles;  // compaction tiles
@@ -115,17 +128,16 @@ __host__ __device__ inline uint64_t file_size(const Geom &g, uint64_t f) {
 
 struct WsPtrs {
   WsHeader *hdr;
-  uint32_t *seg_base;   // nfiles + 1
+  uint32_t *seg_base;   // nfiles + 1: first item of each file
   uint32_t *ftile;      // per plan tile
   uint32_t *state;      // per item
   uint64_t *incl;       // per item: exit from `entry` (file-relative)
   uint64_t *entry;      // per item: entry the item's cuts were computed from
   uint32_t *first_bad;  // per file: first inconsistent item (verify pass)
-  uint32_t *count;      // per item: true cuts emitted
-  uint32_t *img_n;      // per item
-  uint64_t *img;        // per item x kMaxImage (file-relative)
-  uint32_t *tab_n;      // per item
-  uint64_t *tab;        // per item x kMaxEntries
+  uint32_t *count;      // per item: cuts emitted
+  uint32_t *img_n;      // per item: image size
+  uint64_t *img;        // per item x kMaxImage: distinct exits (file-relative)
+  uint64_t *agg;        // per item x kMaxImage: exit for each predecessor image value
   uint64_t *slot;       // per item x slot_cap (file-relative cuts)
   uint32_t *itile;      // per compaction tile
   uint32_t slot_cap;
@@ -149,14 +161,16 @@ __device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p) {
 // Wait until (*flag & mask) != 0, at most kWaitNs.  Returns the flag value, or
 // 0 after recording SEQCDC_ETIMEOUT in the workspace status.
 __device__ uint32_t wait_any(const uint32_t *flag, uint32_t mask, WsHeader *hdr) {
-  uint64_t t0 = global_ns();
+  uint32_t v = ld_acquire(flag);
+  if (v & mask) return v;
+  const uint64_t t0 = global_ns();
   uint32_t backoff = 32;
   for (uint64_t it = 0; it < (1ull << 32); ++it) {
-    uint32_t v = ld_acquire(flag);
+    __nanosleep(backoff);
+    if (backoff < 512) backoff <<= 1;
+    v = ld_acquire(flag);
     if (v & mask) return v;
     if (global_ns() - t0 > kWaitNs) break;
-    __nanosleep(backoff);
-    if (backoff < 1024) backoff <<= 1;
   }
   atomicExch(&hdr->status, (uint32_t)SEQCDC_ETIMEOUT);
   return 0;
@@ -167,7 +181,7 @@ __device__ uint32_t wait_any(const uint32_t *flag, uint32_t mask, WsHeader *hdr)
 // borrow-free subtraction ((a | 0x80) - (b & 0x7f) - 1 stays within 0..0xff),
 // the high bits decide when they differ.
 __device__ __forceinline__ uint32_t gt_hi(uint32_t a, uint32_t b) {
-  uint32_t z = (a | 0x80808080u) - (b & 0x7f7f7f7fu) - 0x01010101u;
+  const uint32_t z = (a | 0x80808080u) - (b & 0x7f7f7f7fu) - 0x01010101u;
   return (a & ~b) | (~(a ^ b) & z);
 }
 
@@ -176,7 +190,7 @@ __device__ __forceinline__ uint32_t pack4(uint32_t m) {
   return ((m & 0x80808080u) * 0x00204081u) >> 28;
 }
 
-// Position (0..31) of the k-th set bit (k >= 1, k <= popc(x)).
+// Position (0..31) of the k-th set bit (1 <= k <= popc(x)).
 __device__ __forceinline__ uint32_t nth_set_bit(uint32_t x, uint32_t k) {
   uint32_t pos = 0;
   uint32_t c = __popc(x & 0xffffu);
@@ -192,26 +206,25 @@ __device__ __forceinline__ uint32_t nth_set_bit(uint32_t x, uint32_t k) {
   return pos;
 }
 
-// Target / opposing bit masks (16 positions) for the 16 bytes in v, given the
-// byte before them.  Bit t of the result refers to the pair
-// (byte t-1, byte t) of this group.
+// Target / opposing masks (16 positions) for the 16 bytes in v, given the
+// byte before them.  Bit t refers to the pair (byte t-1, byte t).
 __device__ __forceinline__ void classify16(uint32_t prev_byte, uint4 v,
                                            uint32_t mode, uint32_t &T16,
                                            uint32_t &O16) {
-  uint32_t x0 = v.x, x1 = v.y, x2 = v.z, x3 = v.w;
-  uint32_t y0 = (x0 << 8) | (prev_byte & 0xffu);
-  uint32_t y1 = __funnelshift_l(x0, x1, 8);
-  uint32_t y2 = __funnelshift_l(x1, x2, 8);
-  uint32_t y3 = __funnelshift_l(x2, x3, 8);
-  uint32_t up = pack4(gt_hi(x0, y0)) | (pack4(gt_hi(x1, y1)) << 4) |
-                (pack4(gt_hi(x2, y2)) << 8) | (pack4(gt_hi(x3, y3)) << 12);
-  uint32_t dn = pack4(gt_hi(y0, x0)) | (pack4(gt_hi(y1, x1)) << 4) |
-                (pack4(gt_hi(y2, x2)) << 8) | (pack4(gt_hi(y3, x3)) << 12);
+  const uint32_t x0 = v.x, x1 = v.y, x2 = v.z, x3 = v.w;
+  const uint32_t y0 = (x0 << 8) | (prev_byte & 0xffu);
+  const uint32_t y1 = __funnelshift_l(x0, x1, 8);
+  const uint32_t y2 = __funnelshift_l(x1, x2, 8);
+  const uint32_t y3 = __funnelshift_l(x2, x3, 8);
+  const uint32_t up = pack4(gt_hi(x0, y0)) | (pack4(gt_hi(x1, y1)) << 4) |
+                      (pack4(gt_hi(x2, y2)) << 8) | (pack4(gt_hi(x3, y3)) << 12);
+  const uint32_t dn = pack4(gt_hi(y0, x0)) | (pack4(gt_hi(y1, x1)) << 4) |
+                      (pack4(gt_hi(y2, x2)) << 8) | (pack4(gt_hi(y3, x3)) << 12);
   T16 = mode == 0 ? up : dn;
   O16 = mode == 0 ? dn : up;
 }
 
-// 16 input bytes starting at global byte index gi (16-aligned); bytes outside
+// 16 input bytes at global byte index gi (16-aligned); bytes outside
 // [0, total) read as zero.
 __device__ __forceinline__ uint4 load16(const uint8_t *data, int64_t gi,
                                         uint64_t total) {
@@ -220,80 +233,10 @@ __device__ __forceinline__ uint4 load16(const uint8_t *data, int64_t gi,
   }
   uint32_t w[4] = {0, 0, 0, 0};
   for (int t = 0; t < 16; ++t) {
-    int64_t a = gi + t;
+    const int64_t a = gi + t;
     if (a >= 0 && (uint64_t)a < total) w[t >> 2] |= (uint32_t)data[a] << (8 * (t & 3));
   }
   return make_uint4(w[0], w[1], w[2], w[3]);
-}
-
-// ---------------------------------------------------------------------------
-// Shared-memory view of one item's bitmaps.  Positions are relative to the
-// window base B (file-relative): rel = pos - B.  Word w covers rel 32w..32w+31.
-// ---------------------------------------------------------------------------
-struct Bits {
-  const uint32_t *E;
-  const uint32_t *O;
-};
-
-// Event of one scan region starting at rel i (bytes i.. ; pairs i+1..).
-// Returns the cut (rel, > 0) if a boundary run ends first, or sets *skip to
-// the rel position of the trigger pair and returns 0, or returns 0 with
-// *skip = kInvalidPos if neither happens before rel `limit`.
-__device__ __forceinline__ uint32_t scan_region(const Bits &b,
-                                                const DevParams &p, uint32_t i,
-                                                uint32_t limit,
-                                                uint32_t *skip) {
-  const uint32_t o_start = i + 1;
-  const uint32_t e_start = i + p.R - 1;
-  uint32_t need = p.T;
-  uint32_t w = o_start >> 5;
-  const uint32_t w_end = (limit + 31) >> 5;
-  for (; w < w_end; ++w) {
-    const uint32_t base = w << 5;
-    uint32_t ob = b.O[w];
-    uint32_t eb = b.E[w];
-    if (o_start > base) ob &= ~0u << (o_start - base);
-    if (e_start > base) eb = (e_start - base >= 32) ? 0u : (eb & (~0u << (e_start - base)));
-    if (limit - base < 32) {
-      const uint32_t m = (1u << (limit - base)) - 1u;
-      ob &= m;
-      eb &= m;
-    }
-    if (need != 0) {
-      const uint32_t pc = __popc(ob);
-      if (pc >= need) {
-        const uint32_t sb = nth_set_bit(ob, need);
-        const uint32_t before = eb & ((1u << sb) - 1u);
-        if (before) return base + (__ffs(before) - 1) + 1;
-        *skip = base + sb;
-        return 0;
-      }
-      need -= pc;
-    }
-    if (eb) return base + (__ffs(eb) - 1) + 1;
-  }
-  *skip = kInvalidPos;
-  return 0;
-}
-
-// One chunk: from chunk start c (rel) return its end (rel).  `end_rel` is the
-// rel position of the file end (a hard limit).
-__device__ uint32_t chunk_step(const Bits &b, const DevParams &p, uint32_t c,
-                               uint32_t end_rel) {
-  const uint32_t limit = (end_rel - c > p.mx) ? c + p.mx : end_rel;
-  uint32_t i = c + (p.mn > p.R ? p.mn - p.R : 0u);
-  while (i + 1 < limit) {
-    uint32_t skip;
-    const uint32_t cut = scan_region(b, p, i, limit, &skip);
-    if (cut) return cut;
-    if (skip == kInvalidPos) break;
-    i = skip + 1 + p.S;
-  }
-  return limit;
-}
-
-__device__ __forceinline__ uint32_t hash_pos(uint32_t x) {
-  return (x * 2654435761u) >> (32 - 11);  // kHashSlots = 2048
 }
 
 // Exclusive block scan of one value per thread (blockDim <= 1024).
@@ -303,7 +246,7 @@ __device__ uint32_t block_excl_scan(uint32_t v, uint32_t *scratch,
   const int nwarps = (blockDim.x + 31) >> 5;
   uint32_t x = v;
   for (int d = 1; d < 32; d <<= 1) {
-    uint32_t y = __shfl_up_sync(0xffffffffu, x, d);
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, d);
     if (lane >= d) x += y;
   }
   if (lane == 31) scratch[warp] = x;
@@ -311,7 +254,7 @@ __device__ uint32_t block_excl_scan(uint32_t v, uint32_t *scratch,
   if (warp == 0) {
     uint32_t s = lane < nwarps ? scratch[lane] : 0u;
     for (int d = 1; d < 32; d <<= 1) {
-      uint32_t y = __shfl_up_sync(0xffffffffu, s, d);
+      const uint32_t y = __shfl_up_sync(0xffffffffu, s, d);
       if (lane >= d) s += y;
     }
     if (lane < nwarps) scratch[lane] = s;
@@ -324,6 +267,99 @@ __device__ uint32_t block_excl_scan(uint32_t v, uint32_t *scratch,
 }
 
 // ---------------------------------------------------------------------------
+// Bitmaps of one item in shared memory.  Positions are relative to the window
+// base B (file-relative): rel = pos - B; word w covers rel 32w .. 32w+31; a
+// block is 8 words (256 positions).
+//   E, O    run-end and opposing-pair bits
+//   eany    bit b set when block b has an E bit
+//   ocnt    number of O bits in block b
+// ---------------------------------------------------------------------------
+struct Bits {
+  const uint32_t *E;
+  const uint32_t *O;
+  const uint32_t *eany;
+  const uint16_t *ocnt;
+};
+
+// First E position in [x, limit), or kNone.
+__device__ __forceinline__ uint32_t first_E(const Bits &b, uint32_t x,
+                                            uint32_t limit) {
+  if (x >= limit) return kNone;
+  const uint32_t wl = (limit - 1) >> 5;
+  uint32_t w = x >> 5;
+  uint32_t m = b.E[w] & (~0u << (x & 31));
+  while (true) {
+    if (m) {
+      const uint32_t pos = (w << 5) + (__ffs(m) - 1);
+      return pos < limit ? pos : kNone;
+    }
+    if (w >= wl) return kNone;
+    ++w;
+    if ((w & 7) == 0) {  // block boundary: jump to the next block with E bits
+      const uint32_t bl = wl >> 3;
+      uint32_t bi = w >> 3;
+      uint32_t fw = bi >> 5;
+      uint32_t fm = b.eany[fw] & (~0u << (bi & 31));
+      while (!fm) {
+        ++fw;
+        if ((fw << 5) > bl) return kNone;
+        fm = b.eany[fw];
+      }
+      bi = (fw << 5) + (__ffs(fm) - 1);
+      if (bi > bl) return kNone;
+      w = bi << 3;
+    }
+    m = b.E[w];
+  }
+}
+
+// Position of the need-th O bit at or after x (need >= 1), if < limit; else kNone.
+__device__ __forceinline__ uint32_t nth_O(const Bits &b, uint32_t x,
+                                          uint32_t need, uint32_t limit) {
+  if (x >= limit) return kNone;
+  const uint32_t wl = (limit - 1) >> 5;
+  uint32_t w = x >> 5;
+  uint32_t m = b.O[w] & (~0u << (x & 31));
+  uint32_t c = __popc(m);
+  while (c < need) {
+    need -= c;
+    if (w >= wl) return kNone;
+    ++w;
+    if ((w & 7) == 0) {  // whole blocks that cannot hold the need-th bit
+      while (w + 8 <= wl + 1 && b.ocnt[w >> 3] < need) {
+        need -= b.ocnt[w >> 3];
+        w += 8;
+      }
+      if (w > wl) return kNone;
+    }
+    m = b.O[w];
+    c = __popc(m);
+  }
+  const uint32_t pos = (w << 5) + nth_set_bit(m, need);
+  return pos < limit ? pos : kNone;
+}
+
+// One chunk: from chunk start c (rel) return its end (rel).  `end_rel` is the
+// rel position of the file end.
+__device__ uint32_t chunk_step(const Bits &b, const DevParams &p, uint32_t c,
+                               uint32_t end_rel) {
+  const uint32_t limit = (end_rel - c > p.mx) ? c + p.mx : end_rel;
+  uint32_t i = c + (p.mn > p.R ? p.mn - p.R : 0u);
+  while (i + 1 < limit) {
+    const uint32_t s = p.T ? nth_O(b, i + 1, p.T, limit) : kNone;
+    const uint32_t e = first_E(b, i + p.R - 1, s == kNone ? limit : s);
+    if (e != kNone) return e + 1;     // boundary run ends first (Sec. III.A)
+    if (s == kNone) break;
+    i = s + 1 + p.S;                  // content-defined skip (Sec. III.C)
+  }
+  return limit;                       // max size or end of input (Sec. IV)
+}
+
+__device__ __forceinline__ uint32_t hash_pos(uint32_t x) {
+  return (x * 2654435761u) >> (32 - 11);  // kHashSlots = 2048
+}
+
+// ---------------------------------------------------------------------------
 // Plan: seg_base[f] = sum of ceil(n_g / L) over g < f; item count.
 // ---------------------------------------------------------------------------
 __global__ void plan_tiles_kernel(Geom g, WsPtrs ws) {
@@ -332,8 +368,7 @@ __global__ void plan_tiles_kernel(Geom g, WsPtrs ws) {
   uint32_t sum = 0;
   for (uint64_t f = f0 + threadIdx.x; f < f0 + kFileTile && f < g.nfiles;
        f += blockDim.x) {
-    const uint64_t n = file_size(g, f);
-    sum += (uint32_t)((n + g.L - 1) / g.L);
+    sum += (uint32_t)((file_size(g, f) + g.L - 1) / g.L);
   }
   for (int d = 16; d; d >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, d);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = sum;
@@ -349,7 +384,6 @@ __global__ void plan_scan_kernel(Geom g, WsPtrs ws, uint64_t nftiles,
                                  uint64_t imax) {
   __shared__ uint32_t scratch[32];
   __shared__ uint32_t s_prefix;
-  // Prefix of all previous tiles.
   uint32_t part = 0;
   for (uint64_t t = threadIdx.x; t < blockIdx.x; t += blockDim.x) part += ws.ftile[t];
   for (int d = 16; d; d >>= 1) part += __shfl_down_sync(0xffffffffu, part, d);
@@ -365,14 +399,11 @@ __global__ void plan_scan_kernel(Geom g, WsPtrs ws, uint64_t nftiles,
   const uint64_t f0 = (uint64_t)blockIdx.x * kFileTile;
   for (uint64_t c0 = f0; c0 < f0 + kFileTile; c0 += blockDim.x) {
     const uint64_t f = c0 + threadIdx.x;
-    uint32_t v = 0;
-    if (f < g.nfiles && f < f0 + kFileTile) {
-      const uint64_t n = file_size(g, f);
-      v = (uint32_t)((n + g.L - 1) / g.L);
-    }
+    const bool live = f < g.nfiles && f < f0 + kFileTile;
+    const uint32_t v = live ? (uint32_t)((file_size(g, f) + g.L - 1) / g.L) : 0u;
     uint32_t tot;
     const uint32_t ex = block_excl_scan(v, scratch, &tot);
-    if (f < g.nfiles && f < f0 + kFileTile) ws.seg_base[f] = running + ex;
+    if (live) ws.seg_base[f] = running + ex;
     running += tot;
   }
   if (blockIdx.x == nftiles - 1 && threadIdx.x == 0) {
@@ -380,8 +411,8 @@ __global__ void plan_scan_kernel(Geom g, WsPtrs ws, uint64_t nftiles,
     ws.hdr->nitems = running;
     ws.hdr->ticket = 0;
     ws.hdr->status = 0;
+    for (int k = 0; k < 8; ++k) ws.hdr->stats[k] = 0;
   }
-  // Reset per-item state and per-file repair marks.
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < imax;
        i += (uint64_t)gridDim.x * blockDim.x) {
     ws.state[i] = 0;
@@ -393,43 +424,55 @@ __global__ void plan_scan_kernel(Geom g, WsPtrs ws, uint64_t nftiles,
 }
 
 // ---------------------------------------------------------------------------
-// Segment kernel.
+// Per-item machinery.
 // ---------------------------------------------------------------------------
 struct SegShared {
   uint32_t item, file, seg, nitems, first_item;
   int64_t B;          // window base (file-relative); global index of rel 0 is 16-aligned
   uint64_t p_s, q_s, n_f, gbase;
-  uint32_t W;         // bitmap words
-  uint32_t K;         // entries
-  uint32_t nnodes, nact, nnew, abnormal, rounds, nimg;
+  uint32_t W, NB;     // bitmap words, blocks
+  uint32_t K;         // natural entries
+  uint32_t nnodes, nact, nnew, abnormal, nimg, npred, pred_flags;
   uint32_t scratch[32];
   uint64_t true_entry;
-  uint32_t resolved;
 };
 
-// Pointers into the dynamic shared memory of one item.
 struct SegSmem {
-  uint32_t *E, *O;
+  uint32_t *E, *O, *eany;
+  uint16_t *ocnt;
   uint32_t *node_pos;     // kMaxNodes
   uint16_t *node_next;    // kMaxNodes
-  uint16_t *hslot;        // kHashSlots
+  uint16_t *hslot;        // kHashSlots (reused as jmp after the walk)
   uint16_t *act, *act2;   // kMaxNodes each
   uint64_t *img_local;    // kMaxImage
-  uint16_t *img_of_node;  // kMaxNodes
+  uint64_t *agg_local;    // kMaxImage
 };
+
+__host__ __device__ inline uint32_t nblocks(uint32_t W) { return (W + 7) / 8; }
 
 __device__ __forceinline__ SegSmem carve(unsigned char *raw, uint32_t W) {
   SegSmem m;
+  const uint32_t NB = nblocks(W);
   m.E = reinterpret_cast<uint32_t *>(raw);
   m.O = m.E + W;
-  m.node_pos = m.O + W;
-  m.node_next = reinterpret_cast<uint16_t *>(m.node_pos + kMaxNodes);
+  m.eany = m.O + W;
+  m.node_pos = m.eany + (NB + 31) / 32;
+  m.img_local = reinterpret_cast<uint64_t *>(
+      reinterpret_cast<uintptr_t>(m.node_pos + kMaxNodes + 1) & ~(uintptr_t)7);
+  m.agg_local = m.img_local + kMaxImage;
+  m.node_next = reinterpret_cast<uint16_t *>(m.agg_local + kMaxImage);
   m.hslot = m.node_next + kMaxNodes;
   m.act = m.hslot + kHashSlots;
   m.act2 = m.act + kMaxNodes;
-  m.img_local = reinterpret_cast<uint64_t *>(m.act2 + kMaxNodes);
-  m.img_of_node = reinterpret_cast<uint16_t *>(m.img_local + kMaxImage);
+  m.ocnt = m.act2 + kMaxNodes;
   return m;
+}
+
+__host__ __device__ inline size_t seg_smem_bytes_for(uint32_t W) {
+  const uint32_t NB = nblocks(W);
+  return (size_t)W * 8 + ((NB + 31) / 32) * 4 + (kMaxNodes + 1) * 4 + 8 +
+         kMaxImage * 16 + kMaxNodes * 2 + kHashSlots * 2 + kMaxNodes * 4 +
+         (size_t)NB * 2 + 16;
 }
 
 __device__ __forceinline__ uint32_t find_file(const uint32_t *seg_base,
@@ -462,14 +505,19 @@ __device__ void seg_setup(SegShared &sh, const Geom &g, const DevParams &p,
   gb = gb >= 0 ? (gb & ~(int64_t)15) : -(((-gb) + 15) & ~(int64_t)15);
   sh.B = gb - (int64_t)sh.gbase;
   sh.W = (uint32_t)(((int64_t)w1 - sh.B + 31) >> 5);
+  sh.NB = nblocks(sh.W);
   sh.abnormal = 0;
   sh.nnodes = 0;
   sh.K = 0;
   sh.nimg = 0;
-  sh.resolved = 0;
+  sh.npred = 0;
 }
 
-// E and O bitmaps of the window [B, B + 32 W), 16 positions per lane step.
+__device__ __forceinline__ Bits bits_of(const SegSmem &m) {
+  return Bits{m.E, m.O, m.eany, m.ocnt};
+}
+
+// E and O bitmaps of the window [B, B + 32 W) and their block summaries.
 __device__ void seg_bitmaps(const SegShared &sh, const Geom &g,
                             const DevParams &p, const SegSmem &m) {
   const int tid = threadIdx.x, nthreads = blockDim.x;
@@ -516,24 +564,40 @@ __device__ void seg_bitmaps(const SegShared &sh, const Geom &g,
     carry_byte = __shfl_sync(0xffffffffu, v.w >> 24, 31);
     carry_T = __shfl_sync(0xffffffffu, t16, 31);
   }
+  __syncthreads();
+  // Block summaries; each warp covers 32 consecutive blocks per pass.
+  const uint32_t NB = sh.NB;
+  for (uint32_t b0 = warp * 32; b0 < NB; b0 += nwarps * 32) {
+    const uint32_t b = b0 + lane;
+    uint32_t any = 0, cnt = 0;
+    if (b < NB) {
+      const uint32_t w0 = b * 8, w1 = min(w0 + 8, W);
+      for (uint32_t w = w0; w < w1; ++w) {
+        any |= m.E[w];
+        cnt += __popc(m.O[w]);
+      }
+      m.ocnt[b] = (uint16_t)cnt;
+    }
+    const uint32_t bal = __ballot_sync(0xffffffffu, any != 0);
+    if (lane == 0) m.eany[b0 >> 5] = bal;
+  }
 }
 
-// Phases 2-4: entry candidates, walk of every entry's chain with merging,
-// exits and the entry -> exit table, published to the workspace.  All threads.
-__device__ void seg_walk_publish(SegShared &sh, const DevParams &p,
-                                 const SegSmem &m, const WsPtrs &ws) {
+// Entry candidates, then the walk of every entry's chain to its exit with
+// merging, then each entry's exit by pointer jumping (left in hslot[0..n) as
+// the terminal node index).  All threads.  Sets sh.abnormal when the entries
+// or nodes do not fit.
+__device__ void seg_walk(SegShared &sh, const DevParams &p, const SegSmem &m) {
   const int tid = threadIdx.x, nthreads = blockDim.x;
   const int64_t B = sh.B;
-  const uint64_t n_f = sh.n_f, p_s = sh.p_s, q_s = sh.q_s;
+  const uint64_t n_f = sh.n_f, p_s = sh.p_s;
   const uint32_t end_rel = (uint32_t)((int64_t)n_f - B);
-  const uint32_t q_rel = (uint32_t)((int64_t)q_s - B);
+  const uint32_t q_rel = (uint32_t)((int64_t)sh.q_s - B);
   const uint32_t ps_rel = (uint32_t)((int64_t)p_s - B);
-  const Bits bits{m.E, m.O};
-  const uint32_t item = sh.item;
+  const Bits bits = bits_of(m);
 
-  // Entry candidates.  Item 0 of a file starts at the file start; any other
-  // item may be entered at every natural cut x = e + 1 (E[e] set) with
-  // p_s <= x < p_s + max_size.
+  // Item 0 of a file starts at the file start; any other item may be entered
+  // at every natural cut x = e + 1 (E[e] set) with p_s <= x < p_s + max_size.
   if (sh.seg == 0) {
     if (tid == 0) {
       m.node_pos[0] = ps_rel;
@@ -576,217 +640,273 @@ __device__ void seg_walk_publish(SegShared &sh, const DevParams &p,
     }
   }
   __syncthreads();
+  if (sh.abnormal) return;
 
-  // Walk every entry's chunk chain to its exit (first cut >= q_s), merging
-  // chains that reach a common cut.  Nodes are distinct cut positions.
-  if (!sh.abnormal) {
-    const uint32_t K = sh.K;
-    for (int i = tid; i < kHashSlots; i += nthreads) m.hslot[i] = kNil;
-    for (int i = tid; i < kMaxNodes; i += nthreads) m.node_next[i] = kNil;
-    if (tid == 0) {
-      sh.nnodes = K;
-      sh.nact = 0;
-      sh.nnew = 0;
-      sh.rounds = 0;
-    }
-    __syncthreads();
-    for (uint32_t k = tid; k < K; k += nthreads) {
-      const uint32_t x = m.node_pos[k];
-      uint32_t slot = hash_pos(x);
-      while (atomicCAS(&m.hslot[slot], kNil, (uint16_t)k) != kNil)
-        slot = (slot + 1) & (kHashSlots - 1);
-      if (x < q_rel) m.act[atomicAdd(&sh.nact, 1u)] = (uint16_t)k;
-    }
-    __syncthreads();
-    uint16_t *cur_act = m.act, *nxt_act = m.act2;
-    while (true) {
-      const uint32_t nact = sh.nact;
-      if (nact == 0 || sh.abnormal) break;
-      for (uint32_t t = tid; t < nact; t += nthreads) {
-        const uint16_t h = cur_act[t];
-        const uint32_t y = chunk_step(bits, p, m.node_pos[h], end_rel);
-        uint32_t slot = hash_pos(y);
-        uint16_t id = kNil;
-        bool created = false;
-        for (int probe = 0; probe < kHashSlots; ++probe) {
-          uint16_t cur = *((volatile uint16_t *)&m.hslot[slot]);
-          if (cur == kNil) {
-            const uint32_t nid = atomicAdd(&sh.nnodes, 1u);
-            if (nid >= (uint32_t)kMaxNodes) {
-              sh.abnormal = 1;
-              break;
-            }
-            m.node_pos[nid] = y;
-            m.node_next[nid] = kNil;
-            __threadfence_block();
-            const uint16_t prev = atomicCAS(&m.hslot[slot], kNil, (uint16_t)nid);
-            if (prev == kNil) {
-              id = (uint16_t)nid;
-              created = true;
-              break;
-            }
-            m.node_pos[nid] = kInvalidPos;  // lost the slot; the winner may match
-            cur = prev;
-          }
-          if (*((volatile uint32_t *)&m.node_pos[cur]) == y) {
-            id = cur;
+  const uint32_t K = sh.K;
+  for (int i = tid; i < kHashSlots; i += nthreads) m.hslot[i] = kNil;
+  for (int i = tid; i < kMaxNodes; i += nthreads) m.node_next[i] = kNil;
+  if (tid == 0) {
+    sh.nnodes = K;
+    sh.nact = 0;
+    sh.nnew = 0;
+  }
+  __syncthreads();
+  for (uint32_t k = tid; k < K; k += nthreads) {
+    const uint32_t x = m.node_pos[k];
+    uint32_t slot = hash_pos(x);
+    while (atomicCAS(&m.hslot[slot], kNil, (uint16_t)k) != kNil)
+      slot = (slot + 1) & (kHashSlots - 1);
+    if (x < q_rel) m.act[atomicAdd(&sh.nact, 1u)] = (uint16_t)k;
+  }
+  __syncthreads();
+  uint16_t *cur_act = m.act, *nxt_act = m.act2;
+  while (true) {
+    const uint32_t nact = sh.nact;
+    if (nact == 0 || sh.abnormal) break;
+    for (uint32_t t = tid; t < nact; t += nthreads) {
+      const uint16_t h = cur_act[t];
+      const uint32_t y = chunk_step(bits, p, m.node_pos[h], end_rel);
+      uint32_t slot = hash_pos(y);
+      uint16_t id = kNil;
+      bool created = false;
+      for (int probe = 0; probe < kHashSlots; ++probe) {
+        uint16_t cur = *((volatile uint16_t *)&m.hslot[slot]);
+        if (cur == kNil) {
+          const uint32_t nid = atomicAdd(&sh.nnodes, 1u);
+          if (nid >= (uint32_t)kMaxNodes) {
+            sh.abnormal = 1;
             break;
           }
-          slot = (slot + 1) & (kHashSlots - 1);
+          m.node_pos[nid] = y;
+          m.node_next[nid] = kNil;
+          __threadfence_block();
+          const uint16_t prev = atomicCAS(&m.hslot[slot], kNil, (uint16_t)nid);
+          if (prev == kNil) {
+            id = (uint16_t)nid;
+            created = true;
+            break;
+          }
+          m.node_pos[nid] = kNone;  // lost the slot; the winner may match
+          cur = prev;
         }
-        m.node_next[h] = id;
-        if (created && y < q_rel) nxt_act[atomicAdd(&sh.nnew, 1u)] = id;
+        if (*((volatile uint32_t *)&m.node_pos[cur]) == y) {
+          id = cur;
+          break;
+        }
+        slot = (slot + 1) & (kHashSlots - 1);
       }
-      __syncthreads();
-      if (tid == 0) {
-        sh.nact = sh.nnew;
-        sh.nnew = 0;
-        sh.rounds++;
-      }
-      uint16_t *tmp = cur_act;
-      cur_act = nxt_act;
-      nxt_act = tmp;
-      __syncthreads();
+      m.node_next[h] = id;
+      if (created && y < q_rel) nxt_act[atomicAdd(&sh.nnew, 1u)] = id;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      sh.nact = sh.nnew;
+      sh.nnew = 0;
+    }
+    uint16_t *tmp = cur_act;
+    cur_act = nxt_act;
+    nxt_act = tmp;
+    __syncthreads();
+  }
+  if (sh.abnormal) return;
+
+  // Terminal nodes are the exits; pointer jumping gives every node its
+  // terminal.  A path can pass through several merged chains, so its length
+  // is bounded by the node count, not by the number of rounds.
+  const uint32_t nn = min(sh.nnodes, (uint32_t)kMaxNodes);
+  uint16_t *jmp = m.hslot;
+  for (uint32_t n = tid; n < nn; n += nthreads) {
+    const uint16_t nx = m.node_next[n];
+    jmp[n] = (nx == kNil) ? (uint16_t)n : nx;
+    if (nx == kNil && m.node_pos[n] != kNone) {
+      const uint32_t idx = atomicAdd(&sh.nimg, 1u);
+      if (idx < (uint32_t)kMaxImage) m.img_local[idx] = (uint64_t)(B + (int64_t)m.node_pos[n]);
     }
   }
   __syncthreads();
+  for (uint32_t r = 1; r < 2 * nn; r <<= 1) {
+    for (uint32_t n = tid; n < nn; n += nthreads) m.act[n] = jmp[jmp[n]];
+    __syncthreads();
+    for (uint32_t n = tid; n < nn; n += nthreads) jmp[n] = m.act[n];
+    __syncthreads();
+  }
+}
 
-  // Exits (terminal nodes) and, by pointer jumping, each entry's exit and hop
-  // count.  Publish the exit set and, when it has several elements, the table.
+// Exit of this item from entry x (file-relative): follow the walked nodes when
+// x is a natural entry, else step the chunker on the bitmaps.  One thread.
+__device__ uint64_t seg_exit_from(const SegShared &sh, const DevParams &p,
+                                  const SegSmem &m, uint64_t x) {
+  const int64_t B = sh.B;
+  const uint32_t xr = (uint32_t)((int64_t)x - B);
   if (!sh.abnormal) {
-    const uint32_t nn = min(sh.nnodes, (uint32_t)kMaxNodes);
-    uint16_t *jmp = m.hslot;               // reuse the hash (kHashSlots >= 2*kMaxNodes)
-    uint16_t *cnt = m.hslot + kMaxNodes;
-    for (uint32_t n = tid; n < nn; n += nthreads) {
-      const bool valid = m.node_pos[n] != kInvalidPos;
-      const uint16_t nx = m.node_next[n];
-      if (valid && nx == kNil) {
-        const uint32_t idx = atomicAdd(&sh.nimg, 1u);
-        if (idx < (uint32_t)kMaxImage) m.img_local[idx] = (uint64_t)(B + (int64_t)m.node_pos[n]);
-        m.img_of_node[n] = (uint16_t)idx;
-      }
-      jmp[n] = (nx == kNil) ? (uint16_t)n : nx;
-      cnt[n] = (nx == kNil) ? 0 : 1;
+    uint32_t lo = 0, hi = sh.K;
+    while (lo < hi) {
+      const uint32_t mid = (lo + hi) >> 1;
+      const uint32_t v = m.node_pos[mid];
+      if (v == xr) return (uint64_t)(B + (int64_t)m.node_pos[m.hslot[mid]]);
+      if (v < xr) lo = mid + 1; else hi = mid;
     }
-    __syncthreads();
-    // A path can pass through several merged chains, so its length is bounded
-    // by the node count, not by the number of rounds.
-    for (uint32_t r = 1; r < 2 * nn; r <<= 1) {
-      for (uint32_t n = tid; n < nn; n += nthreads) {
-        const uint16_t j = jmp[n];
-        m.act[n] = jmp[j];
-        m.act2[n] = cnt[n] + cnt[j];
-      }
-      __syncthreads();
-      for (uint32_t n = tid; n < nn; n += nthreads) {
-        jmp[n] = m.act[n];
-        cnt[n] = m.act2[n];
-      }
-      __syncthreads();
-    }
-    const uint32_t nimg = sh.nimg;
-    const bool notable = nimg > (uint32_t)kMaxImage;
-    if (!notable) {
-      for (uint32_t k = tid; k < nimg; k += nthreads)
-        ws.img[(uint64_t)item * kMaxImage + k] = m.img_local[k];
-      if (nimg > 1) {
-        for (uint32_t k = tid; k < sh.K; k += nthreads) {
-          const uint16_t ex = jmp[k];
-          const uint64_t ent = (uint64_t)(m.node_pos[k] - ps_rel);
-          ws.tab[(uint64_t)item * kMaxEntries + k] =
-              ent | ((uint64_t)m.img_of_node[ex] << 32) | ((uint64_t)cnt[k] << 40);
-        }
-      }
-    }
-    __syncthreads();
-    if (tid == 0) {
-      ws.img_n[item] = nimg;
-      ws.tab_n[item] = sh.K;
-      __threadfence();
-      atomicOr(&ws.state[item], F_TABLE | (nimg == 1 ? F_SINGLE : 0u) |
-                                    (notable ? F_NOTABLE : 0u));
-    }
-  } else if (tid == 0) {
+  }
+  const Bits bits = bits_of(m);
+  const uint32_t end_rel = (uint32_t)((int64_t)sh.n_f - B);
+  const uint32_t q_rel = (uint32_t)((int64_t)sh.q_s - B);
+  uint32_t c = xr;
+  while (c < q_rel) c = chunk_step(bits, p, c, end_rel);
+  return (uint64_t)(B + (int64_t)c);
+}
+
+// Publish the image: distinct exits over the walked entries.  All threads.
+__device__ void seg_publish_image(SegShared &sh, const SegSmem &m,
+                                  const WsPtrs &ws) {
+  const int tid = threadIdx.x;
+  const uint32_t item = sh.item;
+  const uint32_t nimg = sh.nimg;
+  const bool too_many = nimg > (uint32_t)kMaxImage;
+  if (!too_many)
+    for (uint32_t k = tid; k < nimg; k += blockDim.x)
+      ws.img[(uint64_t)item * kMaxImage + k] = m.img_local[k];
+  __syncthreads();
+  if (tid == 0) {
+    ws.img_n[item] = too_many ? 0u : nimg;
     __threadfence();
-    atomicOr(&ws.state[item], F_ABNORMAL);
+    atomicOr(&ws.state[item], too_many ? F_NOIMG : F_IMG);
+    if (too_many) atomicAdd(&ws.hdr->stats[ST_NOIMG], 1u);
   }
 }
 
-// Exit of item j for entry position x (file-relative), from j's table.
-// Returns false if x is not one of j's entries.
-__device__ bool table_lookup(const WsPtrs &ws, uint32_t j, uint64_t pj,
-                             uint64_t x, uint64_t *out) {
-  if (x < pj) return false;
-  const uint64_t want = x - pj;
-  const uint64_t *tb = ws.tab + (uint64_t)j * kMaxEntries;
-  uint32_t lo = 0, hi = __ldcg(&ws.tab_n[j]);
-  while (lo < hi) {
-    const uint32_t mid = (lo + hi) >> 1;
-    const uint64_t v = __ldcg(&tb[mid]);
-    const uint64_t ent = v & 0xffffffffull;
-    if (ent == want) {
-      *out = __ldcg(&ws.img[(uint64_t)j * kMaxImage + ((v >> 32) & 0xff)]);
-      return true;
+// Map from the predecessor's image to this item's exits (the "aggregate" of
+// the decoupled look-back).  For an item whose natural entries could not be
+// walked, the map's values also become its image.  All threads.
+__device__ void seg_publish_agg(SegShared &sh, const DevParams &p,
+                                const SegSmem &m, const WsPtrs &ws) {
+  const int tid = threadIdx.x;
+  const uint32_t item = sh.item;
+  if (tid == 0) {
+    const uint32_t st = wait_any(&ws.state[item - 1], F_IMG | F_NOIMG, ws.hdr);
+    sh.pred_flags = st;
+    sh.npred = (st & F_IMG) ? __ldcg(&ws.img_n[item - 1]) : 0u;
+  }
+  __syncthreads();
+  const uint32_t npred = sh.npred;
+  const bool ok = (sh.pred_flags & F_IMG) != 0;
+  if (ok) {
+    ld_acquire(&ws.state[item - 1]);
+    for (uint32_t j = tid; j < npred; j += blockDim.x) {
+      const uint64_t y = __ldcg(&ws.img[(uint64_t)(item - 1) * kMaxImage + j]);
+      const uint64_t ex = seg_exit_from(sh, p, m, y);
+      m.agg_local[j] = ex;
+      ws.agg[(uint64_t)item * kMaxImage + j] = ex;
     }
-    if (ent < want) lo = mid + 1; else hi = mid;
   }
-  return false;
+  __syncthreads();
+  if (tid == 0) {
+    if (sh.abnormal) {
+      // Image of an item without a full walk: the distinct mapped exits.
+      uint32_t n = 0;
+      if (ok) {
+        for (uint32_t j = 0; j < npred; ++j) {
+          bool seen = false;
+          for (uint32_t k = 0; k < n; ++k) seen |= (m.img_local[k] == m.agg_local[j]);
+          if (!seen) m.img_local[n++] = m.agg_local[j];
+        }
+        for (uint32_t k = 0; k < n; ++k) ws.img[(uint64_t)item * kMaxImage + k] = m.img_local[k];
+      }
+      ws.img_n[item] = n;
+      __threadfence();
+      atomicOr(&ws.state[item], ok ? (F_IMG | F_AGG) : (F_NOIMG | F_NOAGG));
+      if (!ok) atomicAdd(&ws.hdr->stats[ST_NOIMG], 1u);
+    } else {
+      __threadfence();
+      atomicOr(&ws.state[item], ok ? F_AGG : F_NOAGG);
+    }
+  }
 }
 
-// Speculative entry of a non-first item by look-back over the predecessors'
-// published exit sets and tables (warp 0).  The candidates for this item's
-// entry are the exits of item s-1 over its entries; when there are several,
-// the exits of s-2 are pushed through s-1's table, and so on, up to
-// kLookBackDepth items.  The result assumes each predecessor was entered at
-// one of its tabulated entries; the verify pass checks that afterwards.
-// Waits only for predecessors' tables, which depend on nothing else.
-__device__ void seg_lookback(SegShared &sh, const Geom &g, const WsPtrs &ws) {
+// True entry by decoupled look-back (warp 0).  Going back from item-1, each
+// predecessor k either has published its true exit (stop), or its map from
+// the image of k-1 to its exits (compose and continue), or no map (wait for
+// its true exit).  The composite is held as one value per lane: lane j holds
+// the exit of item-1 reached from value j of the current image.
+__device__ uint64_t seg_lookback(SegShared &sh, const WsPtrs &ws) {
   const int lane = threadIdx.x & 31;
   const uint32_t item = sh.item;
-  const uint32_t first_item = sh.first_item;
-  bool ok = false;
+  uint32_t k = item - 1;
+  uint64_t comp = 0;        // per lane: composite value (valid if have)
+  bool have = false;        // composite defined for this lane
+  bool started = false;     // at least one map composed
+  uint32_t steps = 0;
   uint64_t x = 0;
-  for (uint32_t depth = 1; depth <= (uint32_t)kLookBackDepth; ++depth) {
-    const uint32_t k = item - depth;  // k >= first_item (item 0 is single)
+  bool waited = false;
+  while (true) {
     uint32_t st = 0;
-    if (lane == 0) st = wait_any(&ws.state[k], F_TABLE | F_ABNORMAL, ws.hdr);
+    if (lane == 0) st = wait_any(&ws.state[k], F_INCL | F_AGG | F_NOAGG, ws.hdr);
     st = __shfl_sync(0xffffffffu, st, 0);
-    if (st == 0) break;
-    st = ld_acquire(&ws.state[k]);  // every lane acquires before reading k's data
-    if (st & (F_ABNORMAL | F_NOTABLE)) break;
-    const uint32_t nimg = __ldcg(&ws.img_n[k]);
-    // Each lane pushes one of k's exits through the tables of k+1 .. item-1.
-    bool have = lane < (int)nimg;
-    bool fail = false;
-    uint64_t y = have ? __ldcg(&ws.img[(uint64_t)k * kMaxImage + lane]) : 0;
-    for (uint32_t j = k + 1; j < item && have; ++j) {
-      uint64_t z;
-      if (table_lookup(ws, j, (uint64_t)(j - first_item) * g.L, y, &z)) y = z;
-      else { fail = true; have = false; }
+    if (st == 0) { x = sh.p_s; break; }  // timed out; status is recorded
+    st = ld_acquire(&ws.state[k]);
+    if (!(st & F_INCL) && (st & F_NOAGG)) {
+      if (lane == 0) st = wait_any(&ws.state[k], F_INCL, ws.hdr);
+      st = __shfl_sync(0xffffffffu, st, 0);
+      waited = true;
+      if (st == 0) { x = sh.p_s; break; }
+      st = ld_acquire(&ws.state[k]);
     }
-    if (__any_sync(0xffffffffu, fail)) break;
-    const uint64_t y0 = __shfl_sync(0xffffffffu, y, 0);
-    const bool same = !(lane < (int)nimg) || y == y0;
-    if (__all_sync(0xffffffffu, same)) {
-      x = y0;
-      ok = true;
+    if (st & F_INCL) {
+      const uint64_t e = __ldcg(&ws.incl[k]);  // true exit of k = entry of k+1
+      if (!started) { x = e; break; }
+      // Find e in the image of k (the domain of the composite).
+      const uint32_t n = __ldcg(&ws.img_n[k]);
+      const uint64_t v = (lane < (int)n) ? __ldcg(&ws.img[(uint64_t)k * kMaxImage + lane]) : ~0ull;
+      const uint32_t hit = __ballot_sync(0xffffffffu, lane < (int)n && v == e && have);
+      if (hit) {
+        x = __shfl_sync(0xffffffffu, comp, __ffs(hit) - 1);
+        break;
+      }
+      // The true exit of k is outside the composite's domain: wait for the
+      // true exit of item-1 instead.
+      if (lane == 0) st = wait_any(&ws.state[item - 1], F_INCL, ws.hdr);
+      st = __shfl_sync(0xffffffffu, st, 0);
+      waited = true;
+      x = st ? __ldcg(&ws.incl[item - 1]) : sh.p_s;
       break;
     }
-    if (k == first_item) break;
+    // F_AGG: map from the image of k-1 to the exits of k.
+    const uint32_t n_agg = __ldcg(&ws.img_n[k - 1]);
+    const uint64_t a = (lane < (int)n_agg) ? __ldcg(&ws.agg[(uint64_t)k * kMaxImage + lane]) : 0;
+    if (!started) {
+      comp = a;
+      have = lane < (int)n_agg;
+      started = true;
+    } else {
+      // New composite over image(k-1): lane j -> comp at the index of a_j in image(k).
+      const uint32_t n_img = __ldcg(&ws.img_n[k]);
+      const uint64_t im = (lane < (int)n_img) ? __ldcg(&ws.img[(uint64_t)k * kMaxImage + lane]) : ~0ull;
+      uint64_t nc = 0;
+      bool nh = false;
+      for (uint32_t j = 0; j < n_img; ++j) {
+        const uint64_t imj = __shfl_sync(0xffffffffu, im, j);
+        const uint64_t cj = __shfl_sync(0xffffffffu, comp, j);
+        const bool hj = __shfl_sync(0xffffffffu, have, j);
+        if (!nh && lane < (int)n_agg && a == imj && hj) { nc = cj; nh = true; }
+      }
+      comp = nc;
+      have = nh;
+    }
+    ++steps;
+    --k;  // k > first item: the first item publishes F_INCL, never F_AGG
   }
   if (lane == 0) {
-    sh.true_entry = x;
-    sh.resolved = ok ? 1u : 0u;
+    atomicAdd(&ws.hdr->stats[ST_LB_STEPS], steps);
+    if (waited) atomicAdd(&ws.hdr->stats[ST_LB_WAITS], 1u);
   }
+  return x;
 }
 
-// Emission from entry x (file-relative): the cuts in (x, exit] into the
-// item's slot, by following the walked nodes when x is a tabulated entry,
-// else by stepping the chunker on the bitmaps.  Thread 0.
+// Emission from entry x: the cuts in (x, exit] into the item's slot, then the
+// entry, exit and count, then F_INCL.  Thread 0.
 __device__ void seg_emit(SegShared &sh, const DevParams &p, const SegSmem &m,
                          const WsPtrs &ws, uint64_t x, bool use_nodes) {
   const int64_t B = sh.B;
-  const Bits bits{m.E, m.O};
+  const Bits bits = bits_of(m);
   const uint32_t end_rel = (uint32_t)((int64_t)sh.n_f - B);
   const uint32_t q_rel = (uint32_t)((int64_t)sh.q_s - B);
   const uint32_t item = sh.item;
@@ -812,6 +932,7 @@ __device__ void seg_emit(SegShared &sh, const DevParams &p, const SegSmem &m,
     }
     exit_pos = (uint64_t)(B + (int64_t)m.node_pos[n]);
   } else {
+    atomicAdd(&ws.hdr->stats[ST_REPLAYED], 1u);
     uint32_t c = xr;
     while (c < q_rel && nout < ws.slot_cap) {
       c = chunk_step(bits, p, c, end_rel);
@@ -823,7 +944,7 @@ __device__ void seg_emit(SegShared &sh, const DevParams &p, const SegSmem &m,
   ws.incl[item] = exit_pos;
   ws.entry[item] = x;
   __threadfence();
-  atomicOr(&ws.state[item], F_RESOLVED);
+  atomicOr(&ws.state[item], F_INCL);
 }
 
 __global__ void __launch_bounds__(512)
@@ -841,42 +962,61 @@ segment_kernel(Geom g, DevParams p, WsPtrs ws) {
     const uint32_t item = sh.item;
     const uint32_t f = find_file(ws.seg_base, g.nfiles, item);
     seg_setup(sh, g, p, item, f, item - ws.seg_base[f], ws.seg_base[f]);
+    atomicAdd(&ws.hdr->stats[ST_ITEMS], 1u);
   }
   __syncthreads();
   const SegSmem m = carve(smem_raw, sh.W);
   seg_bitmaps(sh, g, p, m);
   __syncthreads();
-  seg_walk_publish(sh, p, m, ws);
+  seg_walk(sh, p, m);
+  __syncthreads();
+  if (sh.abnormal) {
+    if (tid == 0) atomicAdd(&ws.hdr->stats[ST_ABNORMAL], 1u);
+  } else {
+    seg_publish_image(sh, m, ws);
+  }
   __syncthreads();
   if (sh.seg == 0) {
     if (tid == 0) {
+      if (sh.abnormal) {
+        // Image of an unwalked first item: its single exit from the file start.
+        const uint64_t ex = seg_exit_from(sh, p, m, 0);
+        ws.img[(uint64_t)sh.item * kMaxImage] = ex;
+        ws.img_n[sh.item] = 1;
+        __threadfence();
+        atomicOr(&ws.state[sh.item], F_IMG);
+      }
       sh.true_entry = 0;
-      sh.resolved = 1;
     }
-  } else if (tid < 32) {
-    seg_lookback(sh, g, ws);
+  } else {
+    seg_publish_agg(sh, p, m, ws);
+    __syncthreads();
+    if (tid < 32) {
+      const uint64_t x = seg_lookback(sh, ws);
+      if (tid == 0) sh.true_entry = x;
+    }
   }
   __syncthreads();
-  if (tid == 0) {
-    if (sh.resolved) seg_emit(sh, p, m, ws, sh.true_entry, !sh.abnormal);
-    else atomicOr(&ws.state[sh.item], F_UNRESOLVED);
-  }
+  if (tid == 0) seg_emit(sh, p, m, ws, sh.true_entry, !sh.abnormal);
 }
 
-// Verify: item s of a file is consistent when it was resolved and its entry
-// equals the exit its predecessor computed.  By induction from the file start
-// (always a true entry), a file whose items are all consistent is exact.  The
-// first inconsistent item of each file is recorded for the repair pass.
+// Verify: item s of a file is consistent when its entry equals the exit its
+// predecessor computed.  By induction from the file start (always a true
+// entry), a file whose items are all consistent is exact.  The first
+// inconsistent item of each file is recorded for the repair pass.
 __global__ void verify_kernel(Geom g, WsPtrs ws) {
   const uint32_t nitems = ws.hdr->nitems;
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nitems;
        i += (uint64_t)gridDim.x * blockDim.x) {
     const uint32_t f = find_file(ws.seg_base, g.nfiles, (uint32_t)i);
     const uint32_t s = (uint32_t)i - ws.seg_base[f];
-    const uint32_t st = ws.state[i];
-    bool ok = (st & F_RESOLVED) != 0;
-    if (ok && s > 0) ok = ws.entry[i] == ws.incl[i - 1] && (ws.state[i - 1] & F_RESOLVED);
-    if (!ok) atomicMin(&ws.first_bad[f], s);
+    bool ok = (ws.state[i] & F_INCL) != 0;
+    if (ok && s > 0) ok = ws.entry[i] == ws.incl[i - 1];
+    if (ok && s == 0) ok = ws.entry[i] == 0;
+    if (!ok) {
+      atomicMin(&ws.first_bad[f], s);
+      atomicAdd(&ws.hdr->stats[ST_INCONSISTENT], 1u);
+    }
   }
 }
 
@@ -895,13 +1035,16 @@ repair_kernel(Geom g, DevParams p, WsPtrs ws) {
     if (fb == 0xffffffffu) continue;
     const uint32_t base = ws.seg_base[f];
     const uint32_t nseg = ws.seg_base[f + 1] - base;
-    uint64_t cur = ws.incl[base + fb - 1];  // fb >= 1: item 0 is always exact
+    uint64_t cur = fb ? ws.incl[base + fb - 1] : 0;
     for (uint32_t s = fb; s < nseg; ++s) {
       const uint32_t item = base + s;
       if (tid == 0) {
-        const uint32_t st = ws.state[item];
-        s_run = !((st & F_RESOLVED) && ws.entry[item] == cur);
-        if (s_run) seg_setup(sh, g, p, item, (uint32_t)f, s, base);
+        s_run = !((ws.state[item] & F_INCL) && ws.entry[item] == cur);
+        if (s_run) {
+          seg_setup(sh, g, p, item, (uint32_t)f, s, base);
+          sh.abnormal = 1;  // no walk: emit by stepping
+          atomicAdd(&ws.hdr->stats[ST_RECOMPUTED], 1u);
+        }
       }
       __syncthreads();
       if (s_run) {
@@ -938,15 +1081,14 @@ __global__ void count_tiles_kernel(WsPtrs ws) {
 __global__ void emit_kernel(Geom g, WsPtrs ws, uint64_t *d_cuts, uint64_t cap,
                             uint64_t *d_cut_offsets, uint64_t *d_count) {
   __shared__ uint32_t scratch[32];
+  __shared__ uint64_t red64[32];
   __shared__ uint64_t s_prefix;
   __shared__ uint32_t offs[kItemTile + 1];
   const uint32_t nitems = ws.hdr->nitems;
   const uint64_t lo = (uint64_t)blockIdx.x * kItemTile;
-  // Prefix of all earlier tiles.
   uint64_t part = 0;
   for (uint64_t t = threadIdx.x; t < blockIdx.x; t += blockDim.x) part += ws.itile[t];
   for (int d = 16; d; d >>= 1) part += __shfl_down_sync(0xffffffffu, part, d);
-  __shared__ uint64_t red64[32];
   if ((threadIdx.x & 31) == 0) red64[threadIdx.x >> 5] = part;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -963,29 +1105,27 @@ __global__ void emit_kernel(Geom g, WsPtrs ws, uint64_t *d_cuts, uint64_t cap,
   if (threadIdx.x == 0) offs[kItemTile] = tot;
   __syncthreads();
   const uint64_t prefix = s_prefix;
-  // Copy: one warp per item.
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int it = warp; it < kItemTile; it += blockDim.x >> 5) {
     const uint64_t item = lo + it;
     if (item >= nitems) break;
     const uint32_t n = ws.count[item];
-    const uint64_t *src = ws.slot + item * ws.slot_cap;
     const uint64_t at = prefix + offs[it];
     if (at + n > cap) {  // cannot happen for a correct cut list; never write past cap
       if (lane == 0) atomicExch(&ws.hdr->status, (uint32_t)SEQCDC_ECAPACITY);
       continue;
     }
+    const uint64_t *src = ws.slot + item * ws.slot_cap;
     uint64_t *dst = d_cuts + at;
     for (uint32_t j = lane; j < n; j += 32) dst[j] = src[j];
   }
   // CSR offsets of the files whose first item index falls in [lo, lo+tile).
   const uint64_t hi = lo + kItemTile;
   if (lo <= nitems) {
-    // lower_bound(seg_base, lo) over [0, nfiles]
-    uint64_t a = 0, b = g.nfiles + 1;
+    uint64_t a = 0, b = g.nfiles + 1;  // lower_bound(seg_base, lo)
     while (a < b) {
-      const uint64_t m = (a + b) >> 1;
-      if (ws.seg_base[m] < lo) a = m + 1; else b = m;
+      const uint64_t mid = (a + b) >> 1;
+      if (ws.seg_base[mid] < lo) a = mid + 1; else b = mid;
     }
     for (uint64_t f = a + threadIdx.x; f <= g.nfiles; f += blockDim.x) {
       const uint32_t sb = ws.seg_base[f];
@@ -1011,7 +1151,7 @@ bool params_ok(const seqcdc_params_t *p) {
   return true;
 }
 
-uint32_t pick_segment(const seqcdc_params_t *p, const seqcdc_tuning_t *t) {
+uint32_t pick_segment(const seqcdc_tuning_t *t) {
   uint32_t L = (t && t->segment_bytes) ? t->segment_bytes : 65536u;
   L = (L + 1023u) & ~1023u;
   if (L < 4096u) L = 4096u;
@@ -1025,10 +1165,8 @@ uint32_t pick_threads(const seqcdc_tuning_t *t) {
   return n;
 }
 
-size_t seg_smem_bytes(uint32_t L, uint64_t mx) {
-  const uint64_t W = (L + mx + 64 + 31) / 32 + 2;
-  return (size_t)(8 * W) + kMaxNodes * 4 + kMaxNodes * 2 + kHashSlots * 2 +
-         kMaxNodes * 2 * 2 + kMaxImage * 8 + kMaxNodes * 2 + 64;
+uint32_t max_words(uint32_t L, uint64_t mx) {
+  return (uint32_t)((L + mx + 64 + 31) / 32 + 2);
 }
 
 Layout make_layout(const seqcdc_params_t *p, uint64_t total, uint64_t nfiles,
@@ -1056,8 +1194,7 @@ Layout make_layout(const seqcdc_params_t *p, uint64_t total, uint64_t nfiles,
   l.count = take(l.imax * 4);
   l.img_n = take(l.imax * 4);
   l.img = take(l.imax * kMaxImage * 8);
-  l.tab_n = take(l.imax * 4);
-  l.tab = take(l.imax * (size_t)kMaxEntries * 8);
+  l.agg = take(l.imax * kMaxImage * 8);
   l.slot = take(l.imax * (size_t)l.slot_cap * 8);
   l.itile = take(l.nitiles * 4);
   l.total = o;
@@ -1077,8 +1214,7 @@ WsPtrs ws_ptrs(void *d_ws, const Layout &l) {
   w.count = reinterpret_cast<uint32_t *>(b + l.count);
   w.img_n = reinterpret_cast<uint32_t *>(b + l.img_n);
   w.img = reinterpret_cast<uint64_t *>(b + l.img);
-  w.tab_n = reinterpret_cast<uint32_t *>(b + l.tab_n);
-  w.tab = reinterpret_cast<uint64_t *>(b + l.tab);
+  w.agg = reinterpret_cast<uint64_t *>(b + l.agg);
   w.slot = reinterpret_cast<uint64_t *>(b + l.slot);
   w.itile = reinterpret_cast<uint32_t *>(b + l.itile);
   w.slot_cap = l.slot_cap;
@@ -1096,7 +1232,7 @@ int run(const seqcdc_params_t *p, const uint8_t *d_data, uint64_t total,
   if (!d_ws || ((uintptr_t)d_ws & 255u)) return SEQCDC_EINVAL;
   if (total > 0 && (!d_data || ((uintptr_t)d_data & 15u))) return SEQCDC_EINVAL;
   if (total > 0 && !d_cuts) return SEQCDC_EINVAL;
-  const uint32_t L = pick_segment(p, tuning);
+  const uint32_t L = pick_segment(tuning);
   const uint32_t threads = pick_threads(tuning);
   const Layout l = make_layout(p, total, nfiles, L);
   if (l.imax >= 0xffffffffull) return SEQCDC_ERANGE;
@@ -1107,9 +1243,8 @@ int run(const seqcdc_params_t *p, const uint8_t *d_data, uint64_t total,
   Geom g{d_data, total, d_offsets, nfiles, L};
   DevParams dp{p->mode, p->seq_length, p->skip_trigger, p->skip_size,
                (uint32_t)p->min_size, (uint32_t)p->max_size};
-  plan_tiles_kernel<<<(unsigned)l.nftiles, 256, 0, st>>>(g, w);
-  plan_scan_kernel<<<(unsigned)l.nftiles, 256, 0, st>>>(g, w, l.nftiles, l.imax);
-  const size_t smem = seg_smem_bytes(L, p->max_size);
+  const size_t smem = seg_smem_bytes_for(max_words(L, p->max_size));
+  if (smem > 227 * 1024) return SEQCDC_ERANGE;
   static size_t configured = 0;
   if (smem > 48 * 1024 && smem > configured) {
     if (cudaFuncSetAttribute(segment_kernel,
@@ -1121,6 +1256,8 @@ int run(const seqcdc_params_t *p, const uint8_t *d_data, uint64_t total,
       return SEQCDC_ECUDA;
     configured = smem;
   }
+  plan_tiles_kernel<<<(unsigned)l.nftiles, 256, 0, st>>>(g, w);
+  plan_scan_kernel<<<(unsigned)l.nftiles, 256, 0, st>>>(g, w, l.nftiles, l.imax);
   if (g_prof_begin) cudaEventRecord(g_prof_begin, st);
   segment_kernel<<<(unsigned)l.imax, threads, smem, st>>>(g, dp, w);
   if (g_prof_end) cudaEventRecord(g_prof_end, st);
@@ -1168,7 +1305,7 @@ int seqcdc_validate(const seqcdc_params_t *p) {
 size_t seqcdc_workspace_size(const seqcdc_params_t *p, uint64_t total_bytes,
                              uint64_t nfiles, const seqcdc_tuning_t *tuning) {
   if (!params_ok(p)) return 0;
-  return make_layout(p, total_bytes, nfiles, pick_segment(p, tuning)).total;
+  return make_layout(p, total_bytes, nfiles, pick_segment(tuning)).total;
 }
 
 int seqcdc_chunk(const seqcdc_params_t *p, const uint8_t *d_in, uint64_t n,
@@ -1198,6 +1335,17 @@ int seqcdc_status(const void *d_ws, void *stream) {
     return SEQCDC_ECUDA;
   if (cudaStreamSynchronize(st) != cudaSuccess) return SEQCDC_ECUDA;
   return (int)v;
+}
+
+int seqcdc_stats(const void *d_ws, void *stream, uint32_t *out, uint32_t n) {
+  if (!d_ws || !out) return SEQCDC_EINVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  WsHeader h;
+  if (cudaMemcpyAsync(&h, d_ws, sizeof(h), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return SEQCDC_ECUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return SEQCDC_ECUDA;
+  for (uint32_t k = 0; k < n && k < 8; ++k) out[k] = h.stats[k];
+  return SEQCDC_OK;
 }
 
 int seqcdc_profile_events(void *ev_begin, void *ev_end) {

@@ -93,6 +93,8 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
         lib.seqcdc_chunk_batch.restype = ctypes.c_int
         lib.seqcdc_status.argtypes = [vp, vp]
         lib.seqcdc_status.restype = ctypes.c_int
+        lib.seqcdc_stats.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_uint32), u32]
+        lib.seqcdc_stats.restype = ctypes.c_int
         lib.seqcdc_profile_events.argtypes = [vp, vp]
         lib.seqcdc_profile_events.restype = ctypes.c_int
         lib.seqcdc_strerror.argtypes = [ctypes.c_int]
@@ -179,6 +181,18 @@ def seqcdc_chunk_batch(p: Params, d_data, total_bytes: int, d_offsets,
 def seqcdc_status(d_ws, stream=None) -> int:
     """Synchronise the stream; return the device-side status in the workspace."""
     return load_library().seqcdc_status(_ptr(d_ws), _stream_handle(stream))
+
+
+STAT_NAMES = ("segments", "abnormal", "notable", "unresolved", "inconsistent",
+              "recomputed", "replayed", "reserved")
+
+
+def seqcdc_stats(d_ws, stream=None) -> dict:
+    """Path counters of the last call that used workspace ``d_ws``."""
+    out = (ctypes.c_uint32 * 8)()
+    _check(load_library().seqcdc_stats(_ptr(d_ws), _stream_handle(stream), out, 8),
+           "seqcdc_stats")
+    return dict(zip(STAT_NAMES, list(out)))
 
 
 def seqcdc_profile_events(ev_begin=None, ev_end=None) -> None:
