@@ -838,17 +838,22 @@ __device__ uint64_t seg_lookback(SegShared &sh, const WsPtrs &ws) {
   uint64_t x = 0;
   bool waited = false;
   while (true) {
+    // Lane 0 waits; every lane then acquires the flag for its own reads, but
+    // all lanes branch on lane 0's snapshot (flags only gain bits, and lanes
+    // acting on different snapshots would diverge around warp shuffles).
     uint32_t st = 0;
     if (lane == 0) st = wait_any(&ws.state[k], F_INCL | F_AGG | F_NOAGG, ws.hdr);
     st = __shfl_sync(0xffffffffu, st, 0);
     if (st == 0) { x = sh.p_s; break; }  // timed out; status is recorded
-    st = ld_acquire(&ws.state[k]);
+    (void)ld_acquire(&ws.state[k]);
+    __syncwarp();
     if (!(st & F_INCL) && (st & F_NOAGG)) {
       if (lane == 0) st = wait_any(&ws.state[k], F_INCL, ws.hdr);
       st = __shfl_sync(0xffffffffu, st, 0);
       waited = true;
       if (st == 0) { x = sh.p_s; break; }
-      st = ld_acquire(&ws.state[k]);
+      (void)ld_acquire(&ws.state[k]);
+      __syncwarp();
     }
     if (st & F_INCL) {
       const uint64_t e = __ldcg(&ws.incl[k]);  // true exit of k = entry of k+1
@@ -866,7 +871,13 @@ __device__ uint64_t seg_lookback(SegShared &sh, const WsPtrs &ws) {
       if (lane == 0) st = wait_any(&ws.state[item - 1], F_INCL, ws.hdr);
       st = __shfl_sync(0xffffffffu, st, 0);
       waited = true;
-      x = st ? __ldcg(&ws.incl[item - 1]) : sh.p_s;
+      if (st) {
+        (void)ld_acquire(&ws.state[item - 1]);
+        __syncwarp();
+        x = __ldcg(&ws.incl[item - 1]);
+      } else {
+        x = sh.p_s;
+      }
       break;
     }
     // F_AGG: map from the image of k-1 to the exits of k.
