@@ -154,12 +154,12 @@ int seqcdc_status(const void *d_ws, void *stream);
 /*
  * Synchronise `stream` and copy up to `n` (<= 8) path counters of the last
  * call that used d_ws into out[]: [0] segments processed, [1] segments whose
- * walk could not tabulate every entry, [2] segments with more distinct exits
- * than the library publishes, [3] segments whose look-back could not choose
- * an entry, [4] segments found inconsistent by the verify pass, [5] segments
- * re-chunked by the repair pass, [6] segments emitted by stepping from an
- * entry that was not tabulated.  The counters describe which code paths ran;
- * the output is exact either way.
+ * natural entries could not all be walked, [2] segments with more distinct
+ * exits than the library publishes, [3] look-backs that had to wait for a
+ * predecessor's true exit, [4] segments found inconsistent by the verify
+ * pass, [5] segments re-chunked by the repair pass, [6] emissions that stepped
+ * from an entry that was not a natural cut, [7] total look-back depth.  The
+ * counters describe which code paths ran; the output is exact either way.
  */
 int seqcdc_stats(const void *d_ws, void *stream, uint32_t *out, uint32_t n);
 

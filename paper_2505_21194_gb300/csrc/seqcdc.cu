@@ -903,6 +903,29 @@ __device__ uint64_t seg_lookback(SegShared &sh, const WsPtrs &ws) {
       have = nh;
     }
     ++steps;
+    // A constant composite settles the entry whichever image value was true
+    // (under the same tabulated-entry assumption the verify pass checks).
+    {
+      const uint32_t hv = __ballot_sync(0xffffffffu, have);
+      if (hv == 0) {  // nothing composes any more: wait for item-1's true exit
+        if (lane == 0) st = wait_any(&ws.state[item - 1], F_INCL, ws.hdr);
+        st = __shfl_sync(0xffffffffu, st, 0);
+        waited = true;
+        if (st) {
+          (void)ld_acquire(&ws.state[item - 1]);
+          __syncwarp();
+          x = __ldcg(&ws.incl[item - 1]);
+        } else {
+          x = sh.p_s;
+        }
+        break;
+      }
+      const uint64_t c0 = __shfl_sync(0xffffffffu, comp, __ffs(hv) - 1);
+      if (__all_sync(0xffffffffu, !have || comp == c0)) {
+        x = c0;
+        break;
+      }
+    }
     --k;  // k > first item: the first item publishes F_INCL, never F_AGG
   }
   if (lane == 0) {

@@ -183,8 +183,8 @@ def seqcdc_status(d_ws, stream=None) -> int:
     return load_library().seqcdc_status(_ptr(d_ws), _stream_handle(stream))
 
 
-STAT_NAMES = ("segments", "abnormal", "notable", "unresolved", "inconsistent",
-              "recomputed", "replayed", "reserved")
+STAT_NAMES = ("segments", "abnormal", "no_image", "lookback_waits", "inconsistent",
+              "recomputed", "replayed", "lookback_steps")
 
 
 def seqcdc_stats(d_ws, stream=None) -> dict:
