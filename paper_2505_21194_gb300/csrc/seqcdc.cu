@@ -52,9 +52,8 @@ namespace {
 // ---------------------------------------------------------------------------
 // Limits and layout constants.
 // ---------------------------------------------------------------------------
-constexpr int kMaxEntries = 512;   // natural entries walked per item
-constexpr int kMaxNodes = 1024;    // distinct cut positions per item walk
-constexpr int kHashSlots = 2048;   // open-addressing slots (power of two)
+constexpr int kMaxCand = 1024;     // natural cuts tabulated per item
+constexpr int kImgHash = 128;      // distinct-exit hash slots (power of two)
 constexpr int kMaxImage = 32;      // distinct exits published per item (one per lane)
 constexpr int kFileTile = 1024;    // files per plan block
 constexpr int kItemTile = 256;     // items per compaction block
@@ -69,8 +68,11 @@ constexpr uint32_t F_AGG = 4u;     // map predecessor image -> exits published
 constexpr uint32_t F_NOAGG = 8u;   // no such map (predecessor had no image)
 constexpr uint32_t F_INCL = 16u;   // true exit, entry and cuts published
 
-constexpr uint16_t kNil = 0xFFFFu;
 constexpr uint32_t kNone = 0xFFFFFFFFu;
+constexpr uint32_t kTerminal = 0x80000000u;  // candidate next: first cut >= item end
+constexpr uint32_t kEscape = 0xFFFFFFFFu;    // candidate next: forced cut inside item
+constexpr uint32_t kAbnormal = 0xFFFFFFFFu;  // cand_n: too many natural cuts
+constexpr uint64_t kBad = ~0ull;             // unknown exit / entry
 
 struct DevParams {
   uint32_t mode;
@@ -91,19 +93,19 @@ struct WsHeader {
 };
 
 enum : uint32_t {
-  ST_ITEMS = 0,         // items processed
-  ST_ABNORMAL = 1,      // items whose natural entries could not all be walked
-  ST_NOIMG = 2,         // items with more distinct exits than published
+  ST_ITEMS = 0,         // items resolved
+  ST_ABNORMAL = 1,      // items with more natural cuts than tabulated
+  ST_NOIMG = 2,         // items without a published exit set
   ST_LB_WAITS = 3,      // look-backs that had to wait for a true exit
   ST_INCONSISTENT = 4,  // items whose entry disagreed with the predecessor
   ST_RECOMPUTED = 5,    // items re-chunked by the repair pass
-  ST_REPLAYED = 6,      // emissions by stepping (entry was not a natural cut)
+  ST_REPLAYED = 6,      // items left to the repair pass by the resolve kernel
   ST_LB_STEPS = 7,      // total look-back depth
 };
 
 struct Layout {
   size_t hdr, seg_base, ftile, state, incl, entry, first_bad, count, img_n,
-      img, agg, slot, itile, total;
+      img, agg, cand_n, ent_n, cand_pos, cand_nxt, ent_term, slot, itile, total;
   uint64_t imax;     // upper bound on items
   uint64_t nftiles;  // plan tiles
   uint64_t nitiles;  // compaction tiles
@@ -138,6 +140,11 @@ struct WsPtrs {
   uint32_t *img_n;      // per item: image size
   uint64_t *img;        // per item x kMaxImage: distinct exits (file-relative)
   uint64_t *agg;        // per item x kMaxImage: exit for each predecessor image value
+  uint32_t *cand_n;     // per item: natural cuts tabulated (kAbnormal: too many)
+  uint32_t *ent_n;      // per item: how many of them are entries (< p_s + max)
+  uint32_t *cand_pos;   // per item x kMaxCand: positions (relative to the item start)
+  uint32_t *cand_nxt;   // per item x kMaxCand: next candidate / terminal / escape
+  uint32_t *ent_term;   // per item x kMaxCand: exit of each entry (relative) or escape
   uint64_t *slot;       // per item x slot_cap (file-relative cuts)
   uint32_t *itile;      // per compaction tile
   uint32_t slot_cap;
@@ -355,9 +362,6 @@ __device__ uint32_t chunk_step(const Bits &b, const DevParams &p, uint32_t c,
   return limit;                       // max size or end of input (Sec. IV)
 }
 
-__device__ __forceinline__ uint32_t hash_pos(uint32_t x) {
-  return (x * 2654435761u) >> (32 - 11);  // kHashSlots = 2048
-}
 
 // ---------------------------------------------------------------------------
 // Plan: seg_base[f] = sum of ceil(n_g / L) over g < f; item count.
@@ -427,52 +431,47 @@ __global__ void plan_scan_kernel(Geom g, WsPtrs ws, uint64_t nftiles,
 // Per-item machinery.
 // ---------------------------------------------------------------------------
 struct SegShared {
-  uint32_t item, file, seg, nitems, first_item;
+  uint32_t item, file, seg, first_item;
   int64_t B;          // window base (file-relative); global index of rel 0 is 16-aligned
   uint64_t p_s, q_s, n_f, gbase;
   uint32_t W, NB;     // bitmap words, blocks
-  uint32_t K;         // natural entries
-  uint32_t nnodes, nact, nnew, abnormal, nimg, npred, pred_flags;
+  uint32_t nc, nent, ninvalid, nimg;
   uint32_t scratch[32];
-  uint64_t true_entry;
 };
 
-struct SegSmem {
+// Shared memory of the map kernel (bitmaps, summaries, candidate graph).
+struct MapSmem {
   uint32_t *E, *O, *eany;
   uint16_t *ocnt;
-  uint32_t *node_pos;     // kMaxNodes
-  uint16_t *node_next;    // kMaxNodes
-  uint16_t *hslot;        // kHashSlots (reused as jmp after the walk)
-  uint16_t *act, *act2;   // kMaxNodes each
-  uint64_t *img_local;    // kMaxImage
-  uint64_t *agg_local;    // kMaxImage
+  uint16_t *erank;   // candidate run ends in words before w (from the first candidate word)
+  uint32_t *cpos;    // kMaxCand: candidate positions (rel)
+  uint32_t *cnxt;    // kMaxCand: next candidate index or terminal code
+  uint16_t *jmp, *jtmp;  // kMaxCand: pointer doubling
+  uint32_t *ihash;   // kImgHash: distinct exits
 };
 
 __host__ __device__ inline uint32_t nblocks(uint32_t W) { return (W + 7) / 8; }
 
-__device__ __forceinline__ SegSmem carve(unsigned char *raw, uint32_t W) {
-  SegSmem m;
+__device__ __forceinline__ MapSmem carve(unsigned char *raw, uint32_t W, uint32_t L) {
+  MapSmem m;
   const uint32_t NB = nblocks(W);
   m.E = reinterpret_cast<uint32_t *>(raw);
   m.O = m.E + W;
   m.eany = m.O + W;
-  m.node_pos = m.eany + (NB + 31) / 32;
-  m.img_local = reinterpret_cast<uint64_t *>(
-      reinterpret_cast<uintptr_t>(m.node_pos + kMaxNodes + 1) & ~(uintptr_t)7);
-  m.agg_local = m.img_local + kMaxImage;
-  m.node_next = reinterpret_cast<uint16_t *>(m.agg_local + kMaxImage);
-  m.hslot = m.node_next + kMaxNodes;
-  m.act = m.hslot + kHashSlots;
-  m.act2 = m.act + kMaxNodes;
-  m.ocnt = m.act2 + kMaxNodes;
+  m.cpos = m.eany + (NB + 31) / 32;
+  m.cnxt = m.cpos + kMaxCand;
+  m.ihash = m.cnxt + kMaxCand;
+  m.ocnt = reinterpret_cast<uint16_t *>(m.ihash + kImgHash);
+  m.erank = m.ocnt + NB;
+  m.jmp = m.erank + (L / 32 + 4);
+  m.jtmp = m.jmp + kMaxCand;
   return m;
 }
 
-__host__ __device__ inline size_t seg_smem_bytes_for(uint32_t W) {
+__host__ __device__ inline size_t map_smem_bytes(uint32_t W, uint32_t L) {
   const uint32_t NB = nblocks(W);
-  return (size_t)W * 8 + ((NB + 31) / 32) * 4 + (kMaxNodes + 1) * 4 + 8 +
-         kMaxImage * 16 + kMaxNodes * 2 + kHashSlots * 2 + kMaxNodes * 4 +
-         (size_t)NB * 2 + 16;
+  return (size_t)W * 8 + ((NB + 31) / 32) * 4 + (size_t)kMaxCand * 8 +
+         kImgHash * 4 + (size_t)NB * 2 + (L / 32 + 4) * 2 + kMaxCand * 4 + 16;
 }
 
 __device__ __forceinline__ uint32_t find_file(const uint32_t *seg_base,
@@ -486,7 +485,7 @@ __device__ __forceinline__ uint32_t find_file(const uint32_t *seg_base,
   return (uint32_t)lo;
 }
 
-// Geometry of item (file, seg); thread 0 only.
+// Geometry of item (file, seg); one thread.
 __device__ void seg_setup(SegShared &sh, const Geom &g, const DevParams &p,
                           uint32_t item, uint32_t file, uint32_t seg,
                           uint32_t first_item) {
@@ -506,29 +505,57 @@ __device__ void seg_setup(SegShared &sh, const Geom &g, const DevParams &p,
   sh.B = gb - (int64_t)sh.gbase;
   sh.W = (uint32_t)(((int64_t)w1 - sh.B + 31) >> 5);
   sh.NB = nblocks(sh.W);
-  sh.abnormal = 0;
-  sh.nnodes = 0;
-  sh.K = 0;
+  sh.nc = 0;
+  sh.nent = 0;
+  sh.ninvalid = 0;
   sh.nimg = 0;
-  sh.npred = 0;
 }
 
-__device__ __forceinline__ Bits bits_of(const SegSmem &m) {
+__device__ __forceinline__ Bits bits_of(const MapSmem &m) {
   return Bits{m.E, m.O, m.eany, m.ocnt};
 }
 
+// Classify one 16-byte group (lane-parallel), chaining the previous byte and
+// the previous group's T bits through the warp; stores E and O halves.
+__device__ __forceinline__ void bitmap_step(const uint4 v, bool live, uint32_t h,
+                                            uint32_t mode, uint32_t R,
+                                            uint32_t &carry_byte,
+                                            uint32_t &carry_T, uint16_t *E16,
+                                            uint16_t *O16) {
+  const int lane = threadIdx.x & 31;
+  uint32_t pb = __shfl_up_sync(0xffffffffu, v.w >> 24, 1);
+  if (lane == 0) pb = carry_byte;
+  uint32_t t16, o16;
+  classify16(pb, v, mode, t16, o16);
+  uint32_t pt = __shfl_up_sync(0xffffffffu, t16, 1);
+  if (lane == 0) pt = carry_T;
+  // E at group position t needs T at t, t-1, ..., t-(R-2): the previous
+  // group's T bits sit below this group's in a 32-bit window.
+  const uint32_t tw = (t16 << 16) | (pt & 0xffffu);
+  uint32_t ew = tw;
+  for (uint32_t k = 1; k + 1 < R; ++k) ew &= tw << k;
+  if (live) {
+    E16[h] = (uint16_t)(ew >> 16);
+    O16[h] = (uint16_t)o16;
+  }
+  carry_byte = __shfl_sync(0xffffffffu, v.w >> 24, 31);
+  carry_T = __shfl_sync(0xffffffffu, t16, 31);
+}
+
 // E and O bitmaps of the window [B, B + 32 W) and their block summaries.
+// Each lane keeps two 16-byte loads in flight.
 __device__ void seg_bitmaps(const SegShared &sh, const Geom &g,
-                            const DevParams &p, const SegSmem &m) {
+                            const DevParams &p, uint32_t *E, uint32_t *O,
+                            uint32_t *eany, uint16_t *ocnt) {
   const int tid = threadIdx.x, nthreads = blockDim.x;
   const uint32_t W = sh.W;
   const int64_t gwin = (int64_t)sh.gbase + sh.B;  // global byte index of rel 0
-  uint16_t *E16 = reinterpret_cast<uint16_t *>(m.E);
-  uint16_t *O16 = reinterpret_cast<uint16_t *>(m.O);
+  uint16_t *E16 = reinterpret_cast<uint16_t *>(E);
+  uint16_t *O16 = reinterpret_cast<uint16_t *>(O);
   const uint32_t H = 2 * W;  // 16-byte groups
   const int lane = tid & 31, warp = tid >> 5, nwarps = nthreads >> 5;
   uint32_t per = (H + nwarps - 1) / nwarps;
-  per = (per + 31) & ~31u;
+  per = (per + 63) & ~63u;
   const uint32_t h0 = warp * per;
   const uint32_t h1 = min(h0 + per, H);
   uint32_t carry_byte = 0, carry_T = 0;
@@ -541,28 +568,13 @@ __device__ void seg_bitmaps(const SegShared &sh, const Geom &g,
     carry_T = t16;
     carry_byte = pv.w >> 24;
   }
-  for (uint32_t hb = h0; hb < h1; hb += 32) {
-    const uint32_t h = hb + lane;
-    const bool live = h < h1;
-    const uint4 v = live ? load16(g.data, gwin + 16 * (int64_t)h, g.total)
-                         : make_uint4(0, 0, 0, 0);
-    uint32_t pb = __shfl_up_sync(0xffffffffu, v.w >> 24, 1);
-    if (lane == 0) pb = carry_byte;
-    uint32_t t16, o16;
-    classify16(pb, v, p.mode, t16, o16);
-    uint32_t pt = __shfl_up_sync(0xffffffffu, t16, 1);
-    if (lane == 0) pt = carry_T;
-    // E at group position t needs T at t, t-1, ..., t-(R-2): the previous
-    // group's T bits sit below this group's in a 32-bit window.
-    const uint32_t tw = (t16 << 16) | (pt & 0xffffu);
-    uint32_t ew = tw;
-    for (uint32_t k = 1; k + 1 < p.R; ++k) ew &= tw << k;
-    if (live) {
-      E16[h] = (uint16_t)(ew >> 16);
-      O16[h] = (uint16_t)o16;
-    }
-    carry_byte = __shfl_sync(0xffffffffu, v.w >> 24, 31);
-    carry_T = __shfl_sync(0xffffffffu, t16, 31);
+  for (uint32_t hb = h0; hb < h1; hb += 64) {
+    const uint32_t ha = hb + lane, hc = hb + 32 + lane;
+    const bool la = ha < h1, lc = hc < h1;
+    const uint4 va = la ? load16(g.data, gwin + 16 * (int64_t)ha, g.total) : make_uint4(0, 0, 0, 0);
+    const uint4 vc = lc ? load16(g.data, gwin + 16 * (int64_t)hc, g.total) : make_uint4(0, 0, 0, 0);
+    bitmap_step(va, la, ha, p.mode, p.R, carry_byte, carry_T, E16, O16);
+    bitmap_step(vc, lc, hc, p.mode, p.R, carry_byte, carry_T, E16, O16);
   }
   __syncthreads();
   // Block summaries; each warp covers 32 consecutive blocks per pass.
@@ -573,301 +585,258 @@ __device__ void seg_bitmaps(const SegShared &sh, const Geom &g,
     if (b < NB) {
       const uint32_t w0 = b * 8, w1 = min(w0 + 8, W);
       for (uint32_t w = w0; w < w1; ++w) {
-        any |= m.E[w];
-        cnt += __popc(m.O[w]);
+        any |= E[w];
+        cnt += __popc(O[w]);
       }
-      m.ocnt[b] = (uint16_t)cnt;
+      ocnt[b] = (uint16_t)cnt;
     }
     const uint32_t bal = __ballot_sync(0xffffffffu, any != 0);
-    if (lane == 0) m.eany[b0 >> 5] = bal;
+    if (lane == 0) eany[b0 >> 5] = bal;
   }
 }
 
-// Entry candidates, then the walk of every entry's chain to its exit with
-// merging, then each entry's exit by pointer jumping (left in hslot[0..n) as
-// the terminal node index).  All threads.  Sets sh.abnormal when the entries
-// or nodes do not fit.
-__device__ void seg_walk(SegShared &sh, const DevParams &p, const SegSmem &m) {
+// ---------------------------------------------------------------------------
+// Map kernel: one block per item, no inter-block waits.
+//   candidates  every natural cut x = e + 1 (E[e] set) with p_s <= x < q_s,
+//               plus the file start for the first item of a file;
+//   next        the chunker's next cut from each candidate, as the index of
+//               that candidate, or a terminal code (first cut >= q_s) or an
+//               escape code (a forced cut inside the item: not a candidate);
+//   exits       by pointer doubling, the terminal of every entry candidate
+//               (those below p_s + max_size), and their distinct values.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(512)
+map_kernel(Geom g, DevParams p, WsPtrs ws) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ SegShared sh;
   const int tid = threadIdx.x, nthreads = blockDim.x;
+  const uint32_t item = blockIdx.x;
+  const uint32_t nitems = ws.hdr->nitems;
+  if (item >= nitems) return;
+  if (tid == 0) {
+    const uint32_t f = find_file(ws.seg_base, g.nfiles, item);
+    seg_setup(sh, g, p, item, f, item - ws.seg_base[f], ws.seg_base[f]);
+  }
+  __syncthreads();
+  const MapSmem m = carve(smem_raw, sh.W, g.L);
+  seg_bitmaps(sh, g, p, m.E, m.O, m.eany, m.ocnt);
+  __syncthreads();
+
   const int64_t B = sh.B;
-  const uint64_t n_f = sh.n_f, p_s = sh.p_s;
+  const uint64_t p_s = sh.p_s, n_f = sh.n_f;
   const uint32_t end_rel = (uint32_t)((int64_t)n_f - B);
   const uint32_t q_rel = (uint32_t)((int64_t)sh.q_s - B);
   const uint32_t ps_rel = (uint32_t)((int64_t)p_s - B);
-  const Bits bits = bits_of(m);
-
-  // Item 0 of a file starts at the file start; any other item may be entered
-  // at every natural cut x = e + 1 (E[e] set) with p_s <= x < p_s + max_size.
-  if (sh.seg == 0) {
-    if (tid == 0) {
-      m.node_pos[0] = ps_rel;
-      sh.K = 1;
-    }
-  } else {
-    const uint64_t xe = min(p_s + (uint64_t)p.mx, n_f);  // entries x < xe
-    const uint32_t lo = ps_rel - 1;                      // e >= lo
-    const uint32_t hi = (uint32_t)((int64_t)xe - B) - 1; // e < hi
-    const uint32_t wlo = lo >> 5, whi = (hi + 31) >> 5;
-    const uint32_t nw = whi - wlo;
-    const uint32_t per = (nw + nthreads - 1) / nthreads;
-    const uint32_t a = wlo + tid * per, z = min(a + per, whi);
-    uint32_t cnt = 0;
+  const uint32_t first = sh.seg == 0 ? 1u : 0u;
+  // Candidate run ends e in [lo, hi): x = e + 1 in [p_s, q_s).  In a file's
+  // first item, run ends before byte SeqLength-1 would need bytes before the
+  // file start, so they are not candidates.
+  const uint32_t lo = first ? ps_rel + p.R - 1 : ps_rel - 1;
+  const uint32_t hi = max(q_rel - 1, lo);
+  const uint32_t ent_end = (uint32_t)((int64_t)min(p_s + (uint64_t)p.mx, n_f) - B);
+  const uint32_t wlo = lo >> 5, whi = (hi + 31) >> 5;
+  const uint32_t nw = whi - wlo;
+  const uint32_t per = (nw + nthreads - 1) / nthreads;
+  const uint32_t a = wlo + tid * per, z = min(a + per, whi);
+  uint32_t cnt = 0, cent = 0;
+  for (uint32_t w = a; w < z; ++w) {
+    uint32_t v = m.E[w];
+    const uint32_t base = w << 5;
+    if (lo > base) v &= ~0u << (lo - base);
+    if (hi - base < 32) v &= (1u << (hi - base)) - 1u;
+    cnt += __popc(v);
+    // entries: e + 1 < ent_end
+    const uint32_t eh = ent_end - 1;  // e < eh
+    uint32_t ve = v;
+    if (eh <= base) ve = 0;
+    else if (eh - base < 32) ve &= (1u << (eh - base)) - 1u;
+    cent += __popc(ve);
+  }
+  uint32_t nc_nat;
+  const uint32_t off = block_excl_scan(cnt, sh.scratch, &nc_nat);
+  uint32_t nent_nat;
+  (void)block_excl_scan(cent, sh.scratch, &nent_nat);
+  const uint32_t nc = nc_nat + first;
+  const bool abnormal = nc > (uint32_t)kMaxCand;
+  if (!abnormal) {
+    uint32_t o = off + first;
     for (uint32_t w = a; w < z; ++w) {
       uint32_t v = m.E[w];
       const uint32_t base = w << 5;
       if (lo > base) v &= ~0u << (lo - base);
       if (hi - base < 32) v &= (1u << (hi - base)) - 1u;
-      cnt += __popc(v);
-    }
-    uint32_t K;
-    const uint32_t off = block_excl_scan(cnt, sh.scratch, &K);
-    if (K == 0 || K > (uint32_t)kMaxEntries) {
-      if (tid == 0) sh.abnormal = 1;
-    } else {
-      uint32_t o = off;
-      for (uint32_t w = a; w < z; ++w) {
-        uint32_t v = m.E[w];
-        const uint32_t base = w << 5;
-        if (lo > base) v &= ~0u << (lo - base);
-        if (hi - base < 32) v &= (1u << (hi - base)) - 1u;
-        while (v) {
-          const uint32_t bpos = __ffs(v) - 1;
-          v &= v - 1;
-          m.node_pos[o++] = base + bpos + 1;
-        }
+      m.erank[w - wlo] = (uint16_t)(o - first);
+      while (v) {
+        const uint32_t bpos = __ffs(v) - 1;
+        v &= v - 1;
+        m.cpos[o++] = base + bpos + 1;
       }
-      if (tid == 0) sh.K = K;
     }
-  }
-  __syncthreads();
-  if (sh.abnormal) return;
-
-  const uint32_t K = sh.K;
-  for (int i = tid; i < kHashSlots; i += nthreads) m.hslot[i] = kNil;
-  for (int i = tid; i < kMaxNodes; i += nthreads) m.node_next[i] = kNil;
-  if (tid == 0) {
-    sh.nnodes = K;
-    sh.nact = 0;
-    sh.nnew = 0;
-  }
-  __syncthreads();
-  for (uint32_t k = tid; k < K; k += nthreads) {
-    const uint32_t x = m.node_pos[k];
-    uint32_t slot = hash_pos(x);
-    while (atomicCAS(&m.hslot[slot], kNil, (uint16_t)k) != kNil)
-      slot = (slot + 1) & (kHashSlots - 1);
-    if (x < q_rel) m.act[atomicAdd(&sh.nact, 1u)] = (uint16_t)k;
-  }
-  __syncthreads();
-  uint16_t *cur_act = m.act, *nxt_act = m.act2;
-  while (true) {
-    const uint32_t nact = sh.nact;
-    if (nact == 0 || sh.abnormal) break;
-    for (uint32_t t = tid; t < nact; t += nthreads) {
-      const uint16_t h = cur_act[t];
-      const uint32_t y = chunk_step(bits, p, m.node_pos[h], end_rel);
-      uint32_t slot = hash_pos(y);
-      uint16_t id = kNil;
-      bool created = false;
-      for (int probe = 0; probe < kHashSlots; ++probe) {
-        uint16_t cur = *((volatile uint16_t *)&m.hslot[slot]);
-        if (cur == kNil) {
-          const uint32_t nid = atomicAdd(&sh.nnodes, 1u);
-          if (nid >= (uint32_t)kMaxNodes) {
-            sh.abnormal = 1;
-            break;
-          }
-          m.node_pos[nid] = y;
-          m.node_next[nid] = kNil;
-          __threadfence_block();
-          const uint16_t prev = atomicCAS(&m.hslot[slot], kNil, (uint16_t)nid);
-          if (prev == kNil) {
-            id = (uint16_t)nid;
-            created = true;
-            break;
-          }
-          m.node_pos[nid] = kNone;  // lost the slot; the winner may match
-          cur = prev;
-        }
-        if (*((volatile uint32_t *)&m.node_pos[cur]) == y) {
-          id = cur;
-          break;
-        }
-        slot = (slot + 1) & (kHashSlots - 1);
-      }
-      m.node_next[h] = id;
-      if (created && y < q_rel) nxt_act[atomicAdd(&sh.nnew, 1u)] = id;
-    }
-    __syncthreads();
     if (tid == 0) {
-      sh.nact = sh.nnew;
-      sh.nnew = 0;
-    }
-    uint16_t *tmp = cur_act;
-    cur_act = nxt_act;
-    nxt_act = tmp;
-    __syncthreads();
-  }
-  if (sh.abnormal) return;
-
-  // Terminal nodes are the exits; pointer jumping gives every node its
-  // terminal.  A path can pass through several merged chains, so its length
-  // is bounded by the node count, not by the number of rounds.
-  const uint32_t nn = min(sh.nnodes, (uint32_t)kMaxNodes);
-  uint16_t *jmp = m.hslot;
-  for (uint32_t n = tid; n < nn; n += nthreads) {
-    const uint16_t nx = m.node_next[n];
-    jmp[n] = (nx == kNil) ? (uint16_t)n : nx;
-    if (nx == kNil && m.node_pos[n] != kNone) {
-      const uint32_t idx = atomicAdd(&sh.nimg, 1u);
-      if (idx < (uint32_t)kMaxImage) m.img_local[idx] = (uint64_t)(B + (int64_t)m.node_pos[n]);
+      if (first) m.cpos[0] = ps_rel;
+      sh.nc = nc;
+      sh.nent = first ? 1u : nent_nat;
     }
   }
   __syncthreads();
-  for (uint32_t r = 1; r < 2 * nn; r <<= 1) {
-    for (uint32_t n = tid; n < nn; n += nthreads) m.act[n] = jmp[jmp[n]];
-    __syncthreads();
-    for (uint32_t n = tid; n < nn; n += nthreads) jmp[n] = m.act[n];
-    __syncthreads();
-  }
-}
-
-// Exit of this item from entry x (file-relative): follow the walked nodes when
-// x is a natural entry, else step the chunker on the bitmaps.  One thread.
-__device__ uint64_t seg_exit_from(const SegShared &sh, const DevParams &p,
-                                  const SegSmem &m, uint64_t x) {
-  const int64_t B = sh.B;
-  const uint32_t xr = (uint32_t)((int64_t)x - B);
-  if (!sh.abnormal) {
-    uint32_t lo = 0, hi = sh.K;
-    while (lo < hi) {
-      const uint32_t mid = (lo + hi) >> 1;
-      const uint32_t v = m.node_pos[mid];
-      if (v == xr) return (uint64_t)(B + (int64_t)m.node_pos[m.hslot[mid]]);
-      if (v < xr) lo = mid + 1; else hi = mid;
+  if (abnormal) {
+    if (tid == 0) {
+      ws.cand_n[item] = kAbnormal;
+      ws.img_n[item] = 0;
+      ws.state[item] = F_NOIMG;
+      atomicAdd(&ws.hdr->stats[ST_ABNORMAL], 1u);
     }
+    return;
   }
+
+  // Next cut of every candidate, as a candidate index or a terminal code.
   const Bits bits = bits_of(m);
-  const uint32_t end_rel = (uint32_t)((int64_t)sh.n_f - B);
-  const uint32_t q_rel = (uint32_t)((int64_t)sh.q_s - B);
-  uint32_t c = xr;
-  while (c < q_rel) c = chunk_step(bits, p, c, end_rel);
-  return (uint64_t)(B + (int64_t)c);
-}
-
-// Publish the image: distinct exits over the walked entries.  All threads.
-__device__ void seg_publish_image(SegShared &sh, const SegSmem &m,
-                                  const WsPtrs &ws) {
-  const int tid = threadIdx.x;
-  const uint32_t item = sh.item;
-  const uint32_t nimg = sh.nimg;
-  const bool too_many = nimg > (uint32_t)kMaxImage;
-  if (!too_many)
-    for (uint32_t k = tid; k < nimg; k += blockDim.x)
-      ws.img[(uint64_t)item * kMaxImage + k] = m.img_local[k];
-  __syncthreads();
-  if (tid == 0) {
-    ws.img_n[item] = too_many ? 0u : nimg;
-    __threadfence();
-    atomicOr(&ws.state[item], too_many ? F_NOIMG : F_IMG);
-    if (too_many) atomicAdd(&ws.hdr->stats[ST_NOIMG], 1u);
-  }
-}
-
-// Map from the predecessor's image to this item's exits (the "aggregate" of
-// the decoupled look-back).  For an item whose natural entries could not be
-// walked, the map's values also become its image.  All threads.
-__device__ void seg_publish_agg(SegShared &sh, const DevParams &p,
-                                const SegSmem &m, const WsPtrs &ws) {
-  const int tid = threadIdx.x;
-  const uint32_t item = sh.item;
-  if (tid == 0) {
-    const uint32_t st = wait_any(&ws.state[item - 1], F_IMG | F_NOIMG, ws.hdr);
-    sh.pred_flags = st;
-    sh.npred = (st & F_IMG) ? __ldcg(&ws.img_n[item - 1]) : 0u;
-  }
-  __syncthreads();
-  const uint32_t npred = sh.npred;
-  const bool ok = (sh.pred_flags & F_IMG) != 0;
-  if (ok) {
-    ld_acquire(&ws.state[item - 1]);
-    for (uint32_t j = tid; j < npred; j += blockDim.x) {
-      const uint64_t y = __ldcg(&ws.img[(uint64_t)(item - 1) * kMaxImage + j]);
-      const uint64_t ex = seg_exit_from(sh, p, m, y);
-      m.agg_local[j] = ex;
-      ws.agg[(uint64_t)item * kMaxImage + j] = ex;
-    }
-  }
-  __syncthreads();
-  if (tid == 0) {
-    if (sh.abnormal) {
-      // Image of an item without a full walk: the distinct mapped exits.
-      uint32_t n = 0;
-      if (ok) {
-        for (uint32_t j = 0; j < npred; ++j) {
-          bool seen = false;
-          for (uint32_t k = 0; k < n; ++k) seen |= (m.img_local[k] == m.agg_local[j]);
-          if (!seen) m.img_local[n++] = m.agg_local[j];
-        }
-        for (uint32_t k = 0; k < n; ++k) ws.img[(uint64_t)item * kMaxImage + k] = m.img_local[k];
-      }
-      ws.img_n[item] = n;
-      __threadfence();
-      atomicOr(&ws.state[item], ok ? (F_IMG | F_AGG) : (F_NOIMG | F_NOAGG));
-      if (!ok) atomicAdd(&ws.hdr->stats[ST_NOIMG], 1u);
+  const uint32_t tmask_lo = ~((1u << (lo & 31)) - 1u);
+  for (uint32_t k = tid; k < nc; k += nthreads) {
+    const uint32_t y = chunk_step(bits, p, m.cpos[k], end_rel);
+    uint32_t code;
+    if (y >= q_rel) {
+      code = kTerminal | (y - ps_rel);
     } else {
-      __threadfence();
-      atomicOr(&ws.state[item], ok ? F_AGG : F_NOAGG);
+      const uint32_t e = y - 1;
+      const uint32_t w = e >> 5;
+      const uint32_t bit = 1u << (e & 31);
+      if (m.E[w] & bit) {
+        uint32_t below = m.E[w] & (bit - 1u);
+        if (w == wlo) below &= tmask_lo;
+        code = first + m.erank[w - wlo] + __popc(below);
+      } else {
+        code = kEscape;  // a forced cut inside the item: not a candidate
+      }
     }
+    m.cnxt[k] = code;
+    m.jmp[k] = (code & kTerminal) ? (uint16_t)k : (uint16_t)code;
+  }
+  for (int i = tid; i < kImgHash; i += nthreads) m.ihash[i] = kEscape;
+  __syncthreads();
+  // Pointer doubling: jmp[k] -> last candidate of k's chain.
+  for (uint32_t r = 1; r < 2 * nc; r <<= 1) {
+    for (uint32_t k = tid; k < nc; k += nthreads) m.jtmp[k] = m.jmp[m.jmp[k]];
+    __syncthreads();
+    for (uint32_t k = tid; k < nc; k += nthreads) m.jmp[k] = m.jtmp[k];
+    __syncthreads();
+  }
+  // Publish the candidate graph and every entry's exit; collect distinct exits.
+  const uint32_t nent = sh.nent;
+  uint32_t *gpos = ws.cand_pos + (uint64_t)item * kMaxCand;
+  uint32_t *gnxt = ws.cand_nxt + (uint64_t)item * kMaxCand;
+  uint32_t *gterm = ws.ent_term + (uint64_t)item * kMaxCand;
+  for (uint32_t k = tid; k < nc; k += nthreads) {
+    gpos[k] = m.cpos[k] - ps_rel;
+    gnxt[k] = m.cnxt[k];
+    if (k < nent) {
+      const uint32_t t = m.cnxt[m.jmp[k]];
+      const uint32_t ex = (t == kEscape) ? kEscape : (t & ~kTerminal);
+      gterm[k] = ex;
+      if (ex == kEscape) {
+        atomicAdd(&sh.ninvalid, 1u);
+      } else {
+        uint32_t slot = (ex * 2654435761u) >> (32 - 7);  // kImgHash = 128
+        for (int probe = 0; probe < kImgHash; ++probe) {
+          const uint32_t prev = atomicCAS(&m.ihash[slot], kEscape, ex);
+          if (prev == kEscape) { atomicAdd(&sh.nimg, 1u); break; }
+          if (prev == ex) break;
+          slot = (slot + 1) & (kImgHash - 1);
+        }
+      }
+    }
+  }
+  __syncthreads();
+  const bool img_ok = sh.ninvalid == 0 && sh.nimg <= (uint32_t)kMaxImage;
+  if (tid == 0) sh.nimg = 0;
+  __syncthreads();
+  if (img_ok) {
+    for (int i = tid; i < kImgHash; i += nthreads) {
+      const uint32_t ex = m.ihash[i];
+      if (ex != kEscape) {
+        const uint32_t at = atomicAdd(&sh.nimg, 1u);
+        ws.img[(uint64_t)item * kMaxImage + at] = p_s + ex;
+      }
+    }
+  }
+  __syncthreads();
+  if (tid == 0) {
+    ws.cand_n[item] = nc;
+    ws.ent_n[item] = nent;
+    ws.img_n[item] = img_ok ? sh.nimg : 0u;
+    ws.state[item] = img_ok ? F_IMG : F_NOIMG;
+    if (!img_ok) atomicAdd(&ws.hdr->stats[ST_NOIMG], 1u);
   }
 }
 
-// True entry by decoupled look-back (warp 0).  Going back from item-1, each
+// ---------------------------------------------------------------------------
+// Resolve kernel: one warp per item, items taken in ticket order so that
+// every item's predecessors are running or done.
+// ---------------------------------------------------------------------------
+struct ResShared {
+  uint32_t item, file, seg, first_item, nc, nent;
+  uint64_t p_s, q_s;
+};
+
+// Exit of `item` from entry position y (file-relative), from its table; kBad
+// when y is not a tabulated entry or its chain escapes.  One lane.
+__device__ uint64_t exit_of(const WsPtrs &ws, const ResShared &r, uint64_t y) {
+  if (y >= r.q_s) return y;
+  if (r.nc == kAbnormal || y < r.p_s) return kBad;
+  const uint32_t want = (uint32_t)(y - r.p_s);
+  const uint32_t *gpos = ws.cand_pos + (uint64_t)r.item * kMaxCand;
+  uint32_t lo = 0, hi = r.nent;
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi) >> 1;
+    const uint32_t v = gpos[mid];
+    if (v == want) {
+      const uint32_t t = ws.ent_term[(uint64_t)r.item * kMaxCand + mid];
+      return t == kEscape ? kBad : r.p_s + t;
+    }
+    if (v < want) lo = mid + 1; else hi = mid;
+  }
+  return kBad;
+}
+
+// True entry by decoupled look-back (one warp).  Going back from item-1, each
 // predecessor k either has published its true exit (stop), or its map from
 // the image of k-1 to its exits (compose and continue), or no map (wait for
-// its true exit).  The composite is held as one value per lane: lane j holds
-// the exit of item-1 reached from value j of the current image.
-__device__ uint64_t seg_lookback(SegShared &sh, const WsPtrs &ws) {
+// its true exit).  The composite is one value per lane: lane j holds the exit
+// of item-1 reached from value j of the current image.  A composite that is
+// the same for every value settles the entry at once.
+__device__ uint64_t lookback(const ResShared &r, const WsPtrs &ws) {
   const int lane = threadIdx.x & 31;
-  const uint32_t item = sh.item;
+  const uint32_t item = r.item;
   uint32_t k = item - 1;
-  uint64_t comp = 0;        // per lane: composite value (valid if have)
-  bool have = false;        // composite defined for this lane
-  bool started = false;     // at least one map composed
+  uint64_t comp = 0;
+  bool have = false, started = false, waited = false;
   uint32_t steps = 0;
-  uint64_t x = 0;
-  bool waited = false;
+  uint64_t x = kBad;
   while (true) {
-    // Lane 0 waits; every lane then acquires the flag for its own reads, but
-    // all lanes branch on lane 0's snapshot (flags only gain bits, and lanes
-    // acting on different snapshots would diverge around warp shuffles).
+    // Lane 0 waits; every lane acquires for its own reads but all branch on
+    // lane 0's snapshot (flags only gain bits).
     uint32_t st = 0;
     if (lane == 0) st = wait_any(&ws.state[k], F_INCL | F_AGG | F_NOAGG, ws.hdr);
     st = __shfl_sync(0xffffffffu, st, 0);
-    if (st == 0) { x = sh.p_s; break; }  // timed out; status is recorded
+    if (st == 0) break;  // timed out; status is recorded
     (void)ld_acquire(&ws.state[k]);
     __syncwarp();
     if (!(st & F_INCL) && (st & F_NOAGG)) {
       if (lane == 0) st = wait_any(&ws.state[k], F_INCL, ws.hdr);
       st = __shfl_sync(0xffffffffu, st, 0);
       waited = true;
-      if (st == 0) { x = sh.p_s; break; }
+      if (st == 0) break;
       (void)ld_acquire(&ws.state[k]);
       __syncwarp();
     }
     if (st & F_INCL) {
       const uint64_t e = __ldcg(&ws.incl[k]);  // true exit of k = entry of k+1
-      if (!started) { x = e; break; }
-      // Find e in the image of k (the domain of the composite).
+      if (!started || e == kBad) { x = e; break; }
       const uint32_t n = __ldcg(&ws.img_n[k]);
-      const uint64_t v = (lane < (int)n) ? __ldcg(&ws.img[(uint64_t)k * kMaxImage + lane]) : ~0ull;
+      const uint64_t v = (lane < (int)n) ? __ldcg(&ws.img[(uint64_t)k * kMaxImage + lane]) : kBad;
       const uint32_t hit = __ballot_sync(0xffffffffu, lane < (int)n && v == e && have);
-      if (hit) {
-        x = __shfl_sync(0xffffffffu, comp, __ffs(hit) - 1);
-        break;
-      }
-      // The true exit of k is outside the composite's domain: wait for the
-      // true exit of item-1 instead.
+      if (hit) { x = __shfl_sync(0xffffffffu, comp, __ffs(hit) - 1); break; }
+      // Outside the composite's domain: wait for item-1's own true exit.
       if (lane == 0) st = wait_any(&ws.state[item - 1], F_INCL, ws.hdr);
       st = __shfl_sync(0xffffffffu, st, 0);
       waited = true;
@@ -875,57 +844,45 @@ __device__ uint64_t seg_lookback(SegShared &sh, const WsPtrs &ws) {
         (void)ld_acquire(&ws.state[item - 1]);
         __syncwarp();
         x = __ldcg(&ws.incl[item - 1]);
-      } else {
-        x = sh.p_s;
       }
       break;
     }
     // F_AGG: map from the image of k-1 to the exits of k.
     const uint32_t n_agg = __ldcg(&ws.img_n[k - 1]);
-    const uint64_t a = (lane < (int)n_agg) ? __ldcg(&ws.agg[(uint64_t)k * kMaxImage + lane]) : 0;
+    const uint64_t av = (lane < (int)n_agg) ? __ldcg(&ws.agg[(uint64_t)k * kMaxImage + lane]) : kBad;
     if (!started) {
-      comp = a;
-      have = lane < (int)n_agg;
+      comp = av;
+      have = lane < (int)n_agg && av != kBad;
       started = true;
     } else {
-      // New composite over image(k-1): lane j -> comp at the index of a_j in image(k).
       const uint32_t n_img = __ldcg(&ws.img_n[k]);
-      const uint64_t im = (lane < (int)n_img) ? __ldcg(&ws.img[(uint64_t)k * kMaxImage + lane]) : ~0ull;
+      const uint64_t im = (lane < (int)n_img) ? __ldcg(&ws.img[(uint64_t)k * kMaxImage + lane]) : kBad;
       uint64_t nc = 0;
       bool nh = false;
       for (uint32_t j = 0; j < n_img; ++j) {
         const uint64_t imj = __shfl_sync(0xffffffffu, im, j);
         const uint64_t cj = __shfl_sync(0xffffffffu, comp, j);
         const bool hj = __shfl_sync(0xffffffffu, have, j);
-        if (!nh && lane < (int)n_agg && a == imj && hj) { nc = cj; nh = true; }
+        if (!nh && lane < (int)n_agg && av != kBad && av == imj && hj) { nc = cj; nh = true; }
       }
       comp = nc;
       have = nh;
     }
     ++steps;
-    // A constant composite settles the entry whichever image value was true
-    // (under the same tabulated-entry assumption the verify pass checks).
-    {
-      const uint32_t hv = __ballot_sync(0xffffffffu, have);
-      if (hv == 0) {  // nothing composes any more: wait for item-1's true exit
-        if (lane == 0) st = wait_any(&ws.state[item - 1], F_INCL, ws.hdr);
-        st = __shfl_sync(0xffffffffu, st, 0);
-        waited = true;
-        if (st) {
-          (void)ld_acquire(&ws.state[item - 1]);
-          __syncwarp();
-          x = __ldcg(&ws.incl[item - 1]);
-        } else {
-          x = sh.p_s;
-        }
-        break;
+    const uint32_t hv = __ballot_sync(0xffffffffu, have);
+    if (hv == 0) {  // nothing composes any more: wait for item-1's true exit
+      if (lane == 0) st = wait_any(&ws.state[item - 1], F_INCL, ws.hdr);
+      st = __shfl_sync(0xffffffffu, st, 0);
+      waited = true;
+      if (st) {
+        (void)ld_acquire(&ws.state[item - 1]);
+        __syncwarp();
+        x = __ldcg(&ws.incl[item - 1]);
       }
-      const uint64_t c0 = __shfl_sync(0xffffffffu, comp, __ffs(hv) - 1);
-      if (__all_sync(0xffffffffu, !have || comp == c0)) {
-        x = c0;
-        break;
-      }
+      break;
     }
+    const uint64_t c0 = __shfl_sync(0xffffffffu, comp, __ffs(hv) - 1);
+    if (__all_sync(0xffffffffu, !have || comp == c0)) { x = c0; break; }
     --k;  // k > first item: the first item publishes F_INCL, never F_AGG
   }
   if (lane == 0) {
@@ -935,118 +892,104 @@ __device__ uint64_t seg_lookback(SegShared &sh, const WsPtrs &ws) {
   return x;
 }
 
-// Emission from entry x: the cuts in (x, exit] into the item's slot, then the
-// entry, exit and count, then F_INCL.  Thread 0.
-__device__ void seg_emit(SegShared &sh, const DevParams &p, const SegSmem &m,
-                         const WsPtrs &ws, uint64_t x, bool use_nodes) {
-  const int64_t B = sh.B;
-  const Bits bits = bits_of(m);
-  const uint32_t end_rel = (uint32_t)((int64_t)sh.n_f - B);
-  const uint32_t q_rel = (uint32_t)((int64_t)sh.q_s - B);
-  const uint32_t item = sh.item;
-  const uint32_t xr = (uint32_t)((int64_t)x - B);
-  uint64_t *out = ws.slot + (uint64_t)item * ws.slot_cap;
-  uint32_t nout = 0;
-  uint64_t exit_pos = x;
-  int node = -1;
-  if (use_nodes) {
-    uint32_t lo = 0, hi = sh.K;
-    while (lo < hi) {
-      const uint32_t mid = (lo + hi) >> 1;
-      const uint32_t v = m.node_pos[mid];
-      if (v == xr) { node = (int)mid; break; }
-      if (v < xr) lo = mid + 1; else hi = mid;
+__global__ void __launch_bounds__(32)
+resolve_kernel(Geom g, WsPtrs ws) {
+  __shared__ ResShared r;
+  const int lane = threadIdx.x;
+  if (lane == 0) {
+    const uint32_t item = atomicAdd(&ws.hdr->ticket, 1u);
+    r.item = item;
+    if (item < ws.hdr->nitems) {
+      const uint32_t f = find_file(ws.seg_base, g.nfiles, item);
+      r.file = f;
+      r.first_item = ws.seg_base[f];
+      r.seg = item - r.first_item;
+      r.p_s = (uint64_t)r.seg * g.L;
+      r.q_s = min(r.p_s + g.L, file_size(g, f));
+      r.nc = ws.cand_n[item];
+      r.nent = ws.ent_n[item];
     }
   }
-  if (node >= 0) {
-    uint32_t n = (uint32_t)node;
-    while (m.node_next[n] != kNil && nout < ws.slot_cap) {
-      n = m.node_next[n];
-      out[nout++] = (uint64_t)(B + (int64_t)m.node_pos[n]);
+  __syncwarp();
+  const uint32_t item = r.item;
+  if (item >= ws.hdr->nitems) return;
+  uint64_t x = 0;
+  if (r.seg > 0) {
+    // The map from the predecessor's image to this item's exits.
+    const uint32_t pst = ws.state[item - 1];  // written by the map kernel
+    const bool ok = (pst & F_IMG) != 0;
+    const uint32_t n = ok ? ws.img_n[item - 1] : 0u;
+    if (lane < (int)n) {
+      const uint64_t y = ws.img[(uint64_t)(item - 1) * kMaxImage + lane];
+      ws.agg[(uint64_t)item * kMaxImage + lane] = exit_of(ws, r, y);
     }
-    exit_pos = (uint64_t)(B + (int64_t)m.node_pos[n]);
-  } else {
-    atomicAdd(&ws.hdr->stats[ST_REPLAYED], 1u);
-    uint32_t c = xr;
-    while (c < q_rel && nout < ws.slot_cap) {
-      c = chunk_step(bits, p, c, end_rel);
-      out[nout++] = (uint64_t)(B + (int64_t)c);
+    __syncwarp();
+    if (lane == 0) {
+      __threadfence();
+      atomicOr(&ws.state[item], ok ? F_AGG : F_NOAGG);
     }
-    exit_pos = (uint64_t)(B + (int64_t)c);
+    x = lookback(r, ws);
   }
-  ws.count[item] = nout;
-  ws.incl[item] = exit_pos;
-  ws.entry[item] = x;
-  __threadfence();
-  atomicOr(&ws.state[item], F_INCL);
-}
-
-__global__ void __launch_bounds__(512)
-segment_kernel(Geom g, DevParams p, WsPtrs ws) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ SegShared sh;
-  const int tid = threadIdx.x;
-  if (tid == 0) {
-    sh.item = atomicAdd(&ws.hdr->ticket, 1u);
-    sh.nitems = ws.hdr->nitems;
-  }
-  __syncthreads();
-  if (sh.item >= sh.nitems) return;
-  if (tid == 0) {
-    const uint32_t item = sh.item;
-    const uint32_t f = find_file(ws.seg_base, g.nfiles, item);
-    seg_setup(sh, g, p, item, f, item - ws.seg_base[f], ws.seg_base[f]);
+  // Emission from x along the candidate links (lane 0).
+  if (lane == 0) {
+    uint64_t *out = ws.slot + (uint64_t)item * ws.slot_cap;
+    uint32_t nout = 0;
+    uint64_t exit_pos = x;
+    bool bad = (x == kBad);
+    if (!bad && x < r.q_s) {
+      bad = true;
+      if (r.nc != kAbnormal && x >= r.p_s) {
+        const uint32_t want = (uint32_t)(x - r.p_s);
+        const uint32_t *gpos = ws.cand_pos + (uint64_t)item * kMaxCand;
+        const uint32_t *gnxt = ws.cand_nxt + (uint64_t)item * kMaxCand;
+        uint32_t lo = 0, hi = r.nent;
+        int k = -1;
+        while (lo < hi) {
+          const uint32_t mid = (lo + hi) >> 1;
+          const uint32_t v = gpos[mid];
+          if (v == want) { k = (int)mid; break; }
+          if (v < want) lo = mid + 1; else hi = mid;
+        }
+        if (k >= 0) {
+          uint32_t code = gnxt[k];
+          while (!(code & kTerminal) && nout < ws.slot_cap) {
+            out[nout++] = r.p_s + gpos[code];
+            code = gnxt[code];
+          }
+          if (code != kEscape && nout < ws.slot_cap) {
+            exit_pos = r.p_s + (code & ~kTerminal);
+            out[nout++] = exit_pos;
+            bad = false;
+          }
+        }
+      }
+    }
+    if (bad) {
+      nout = 0;
+      exit_pos = kBad;
+      atomicAdd(&ws.hdr->stats[ST_REPLAYED], 1u);
+    }
+    ws.count[item] = nout;
+    ws.incl[item] = exit_pos;
+    ws.entry[item] = x;
+    __threadfence();
+    atomicOr(&ws.state[item], F_INCL);
     atomicAdd(&ws.hdr->stats[ST_ITEMS], 1u);
   }
-  __syncthreads();
-  const SegSmem m = carve(smem_raw, sh.W);
-  seg_bitmaps(sh, g, p, m);
-  __syncthreads();
-  seg_walk(sh, p, m);
-  __syncthreads();
-  if (sh.abnormal) {
-    if (tid == 0) atomicAdd(&ws.hdr->stats[ST_ABNORMAL], 1u);
-  } else {
-    seg_publish_image(sh, m, ws);
-  }
-  __syncthreads();
-  if (sh.seg == 0) {
-    if (tid == 0) {
-      if (sh.abnormal) {
-        // Image of an unwalked first item: its single exit from the file start.
-        const uint64_t ex = seg_exit_from(sh, p, m, 0);
-        ws.img[(uint64_t)sh.item * kMaxImage] = ex;
-        ws.img_n[sh.item] = 1;
-        __threadfence();
-        atomicOr(&ws.state[sh.item], F_IMG);
-      }
-      sh.true_entry = 0;
-    }
-  } else {
-    seg_publish_agg(sh, p, m, ws);
-    __syncthreads();
-    if (tid < 32) {
-      const uint64_t x = seg_lookback(sh, ws);
-      if (tid == 0) sh.true_entry = x;
-    }
-  }
-  __syncthreads();
-  if (tid == 0) seg_emit(sh, p, m, ws, sh.true_entry, !sh.abnormal);
 }
 
-// Verify: item s of a file is consistent when its entry equals the exit its
-// predecessor computed.  By induction from the file start (always a true
-// entry), a file whose items are all consistent is exact.  The first
-// inconsistent item of each file is recorded for the repair pass.
+// Verify: item s of a file is consistent when it was emitted and its entry
+// equals the exit its predecessor computed.  By induction from the file start
+// (always a true entry), a file whose items are all consistent is exact.  The
+// first inconsistent item of each file is recorded for the repair pass.
 __global__ void verify_kernel(Geom g, WsPtrs ws) {
   const uint32_t nitems = ws.hdr->nitems;
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nitems;
        i += (uint64_t)gridDim.x * blockDim.x) {
     const uint32_t f = find_file(ws.seg_base, g.nfiles, (uint32_t)i);
     const uint32_t s = (uint32_t)i - ws.seg_base[f];
-    bool ok = (ws.state[i] & F_INCL) != 0;
-    if (ok && s > 0) ok = ws.entry[i] == ws.incl[i - 1];
-    if (ok && s == 0) ok = ws.entry[i] == 0;
+    bool ok = (ws.state[i] & F_INCL) && ws.incl[i] != kBad && ws.entry[i] != kBad;
+    if (ok) ok = ws.entry[i] == (s > 0 ? ws.incl[i - 1] : 0ull);
     if (!ok) {
       atomicMin(&ws.first_bad[f], s);
       atomicAdd(&ws.hdr->stats[ST_INCONSISTENT], 1u);
@@ -1056,8 +999,8 @@ __global__ void verify_kernel(Geom g, WsPtrs ws) {
 
 // Repair: one block per file with an inconsistent item.  From the first
 // inconsistent item on, items are re-chunked from the true exit of their
-// predecessor (bitmaps rebuilt from the input); an item whose recorded entry
-// already equals that exit is kept.
+// predecessor (bitmaps rebuilt from the input, chunker stepped sequentially);
+// an item whose recorded entry already equals that exit is kept.
 __global__ void __launch_bounds__(512)
 repair_kernel(Geom g, DevParams p, WsPtrs ws) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1073,19 +1016,35 @@ repair_kernel(Geom g, DevParams p, WsPtrs ws) {
     for (uint32_t s = fb; s < nseg; ++s) {
       const uint32_t item = base + s;
       if (tid == 0) {
-        s_run = !((ws.state[item] & F_INCL) && ws.entry[item] == cur);
+        s_run = !((ws.state[item] & F_INCL) && ws.incl[item] != kBad &&
+                  ws.entry[item] == cur);
         if (s_run) {
           seg_setup(sh, g, p, item, (uint32_t)f, s, base);
-          sh.abnormal = 1;  // no walk: emit by stepping
           atomicAdd(&ws.hdr->stats[ST_RECOMPUTED], 1u);
         }
       }
       __syncthreads();
       if (s_run) {
-        const SegSmem m = carve(smem_raw, sh.W);
-        seg_bitmaps(sh, g, p, m);
+        const MapSmem m = carve(smem_raw, sh.W, g.L);
+        seg_bitmaps(sh, g, p, m.E, m.O, m.eany, m.ocnt);
         __syncthreads();
-        if (tid == 0) seg_emit(sh, p, m, ws, cur, false);
+        if (tid == 0) {
+          const Bits bits = bits_of(m);
+          const int64_t B = sh.B;
+          const uint32_t end_rel = (uint32_t)((int64_t)sh.n_f - B);
+          const uint32_t q_rel = (uint32_t)((int64_t)sh.q_s - B);
+          uint64_t *out = ws.slot + (uint64_t)item * ws.slot_cap;
+          uint32_t nout = 0;
+          uint32_t c = (uint32_t)((int64_t)cur - B);
+          while (c < q_rel && nout < ws.slot_cap) {
+            c = chunk_step(bits, p, c, end_rel);
+            out[nout++] = (uint64_t)(B + (int64_t)c);
+          }
+          ws.count[item] = nout;
+          ws.entry[item] = cur;
+          ws.incl[item] = nout ? (uint64_t)(B + (int64_t)c) : cur;
+          ws.state[item] |= F_INCL;
+        }
       }
       __syncthreads();
       cur = *((volatile uint64_t *)&ws.incl[item]);
@@ -1185,8 +1144,11 @@ bool params_ok(const seqcdc_params_t *p) {
   return true;
 }
 
-uint32_t pick_segment(const seqcdc_tuning_t *t) {
+uint32_t pick_segment(const seqcdc_params_t *p, const seqcdc_tuning_t *t) {
   uint32_t L = (t && t->segment_bytes) ? t->segment_bytes : 65536u;
+  // An item must be at least max_size long so that its entries (natural cuts
+  // below p_s + max_size) all lie inside it.
+  if (p && L < p->max_size) L = (uint32_t)p->max_size;
   L = (L + 1023u) & ~1023u;
   if (L < 4096u) L = 4096u;
   if (L > (1u << 20)) L = 1u << 20;
@@ -1229,6 +1191,11 @@ Layout make_layout(const seqcdc_params_t *p, uint64_t total, uint64_t nfiles,
   l.img_n = take(l.imax * 4);
   l.img = take(l.imax * kMaxImage * 8);
   l.agg = take(l.imax * kMaxImage * 8);
+  l.cand_n = take(l.imax * 4);
+  l.ent_n = take(l.imax * 4);
+  l.cand_pos = take(l.imax * (size_t)kMaxCand * 4);
+  l.cand_nxt = take(l.imax * (size_t)kMaxCand * 4);
+  l.ent_term = take(l.imax * (size_t)kMaxCand * 4);
   l.slot = take(l.imax * (size_t)l.slot_cap * 8);
   l.itile = take(l.nitiles * 4);
   l.total = o;
@@ -1249,6 +1216,11 @@ WsPtrs ws_ptrs(void *d_ws, const Layout &l) {
   w.img_n = reinterpret_cast<uint32_t *>(b + l.img_n);
   w.img = reinterpret_cast<uint64_t *>(b + l.img);
   w.agg = reinterpret_cast<uint64_t *>(b + l.agg);
+  w.cand_n = reinterpret_cast<uint32_t *>(b + l.cand_n);
+  w.ent_n = reinterpret_cast<uint32_t *>(b + l.ent_n);
+  w.cand_pos = reinterpret_cast<uint32_t *>(b + l.cand_pos);
+  w.cand_nxt = reinterpret_cast<uint32_t *>(b + l.cand_nxt);
+  w.ent_term = reinterpret_cast<uint32_t *>(b + l.ent_term);
   w.slot = reinterpret_cast<uint64_t *>(b + l.slot);
   w.itile = reinterpret_cast<uint32_t *>(b + l.itile);
   w.slot_cap = l.slot_cap;
@@ -1266,7 +1238,7 @@ int run(const seqcdc_params_t *p, const uint8_t *d_data, uint64_t total,
   if (!d_ws || ((uintptr_t)d_ws & 255u)) return SEQCDC_EINVAL;
   if (total > 0 && (!d_data || ((uintptr_t)d_data & 15u))) return SEQCDC_EINVAL;
   if (total > 0 && !d_cuts) return SEQCDC_EINVAL;
-  const uint32_t L = pick_segment(tuning);
+  const uint32_t L = pick_segment(p, tuning);
   const uint32_t threads = pick_threads(tuning);
   const Layout l = make_layout(p, total, nfiles, L);
   if (l.imax >= 0xffffffffull) return SEQCDC_ERANGE;
@@ -1277,11 +1249,11 @@ int run(const seqcdc_params_t *p, const uint8_t *d_data, uint64_t total,
   Geom g{d_data, total, d_offsets, nfiles, L};
   DevParams dp{p->mode, p->seq_length, p->skip_trigger, p->skip_size,
                (uint32_t)p->min_size, (uint32_t)p->max_size};
-  const size_t smem = seg_smem_bytes_for(max_words(L, p->max_size));
+  const size_t smem = map_smem_bytes(max_words(L, p->max_size), L);
   if (smem > 227 * 1024) return SEQCDC_ERANGE;
   static size_t configured = 0;
   if (smem > 48 * 1024 && smem > configured) {
-    if (cudaFuncSetAttribute(segment_kernel,
+    if (cudaFuncSetAttribute(map_kernel,
                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem) != cudaSuccess ||
         cudaFuncSetAttribute(repair_kernel,
@@ -1293,8 +1265,9 @@ int run(const seqcdc_params_t *p, const uint8_t *d_data, uint64_t total,
   plan_tiles_kernel<<<(unsigned)l.nftiles, 256, 0, st>>>(g, w);
   plan_scan_kernel<<<(unsigned)l.nftiles, 256, 0, st>>>(g, w, l.nftiles, l.imax);
   if (g_prof_begin) cudaEventRecord(g_prof_begin, st);
-  segment_kernel<<<(unsigned)l.imax, threads, smem, st>>>(g, dp, w);
+  map_kernel<<<(unsigned)l.imax, threads, smem, st>>>(g, dp, w);
   if (g_prof_end) cudaEventRecord(g_prof_end, st);
+  resolve_kernel<<<(unsigned)l.imax, 32, 0, st>>>(g, w);
   const uint64_t vblocks = (l.imax + 255) / 256;
   verify_kernel<<<(unsigned)(vblocks < 4096 ? vblocks : 4096), 256, 0, st>>>(g, w);
   const uint64_t rblocks = nfiles ? nfiles : 1;
@@ -1339,7 +1312,7 @@ int seqcdc_validate(const seqcdc_params_t *p) {
 size_t seqcdc_workspace_size(const seqcdc_params_t *p, uint64_t total_bytes,
                              uint64_t nfiles, const seqcdc_tuning_t *tuning) {
   if (!params_ok(p)) return 0;
-  return make_layout(p, total_bytes, nfiles, pick_segment(tuning)).total;
+  return make_layout(p, total_bytes, nfiles, pick_segment(p, tuning)).total;
 }
 
 int seqcdc_chunk(const seqcdc_params_t *p, const uint8_t *d_in, uint64_t n,
