@@ -52,7 +52,6 @@ namespace {
 // ---------------------------------------------------------------------------
 // Limits and layout constants.
 // ---------------------------------------------------------------------------
-constexpr int kMaxCand = 1024;     // natural cuts tabulated per item
 constexpr int kImgHash = 128;      // distinct-exit hash slots (power of two)
 constexpr int kMaxImage = 32;      // distinct exits published per item (one per lane)
 constexpr int kFileTile = 1024;    // files per plan block
@@ -119,7 +118,12 @@ struct Geom {
   const uint64_t *offsets;  // nullptr: single stream of `total` bytes
   uint64_t nfiles;
   uint32_t L;
+  uint32_t cap;             // natural cuts tabulated per item (L / 64)
 };
+
+// Natural cuts tabulated per item: one per 64 bytes, twice the density of
+// uniform random or text input (about one per 126 bytes at SeqLength 5).
+__host__ __device__ inline uint32_t cand_cap(uint32_t L) { return L / 64 < 256 ? 256 : L / 64; }
 
 __host__ __device__ inline uint64_t file_start(const Geom &g, uint64_t f) {
   return g.offsets ? g.offsets[f] : 0;
@@ -453,6 +457,7 @@ struct MapSmem {
 __host__ __device__ inline uint32_t nblocks(uint32_t W) { return (W + 7) / 8; }
 
 __device__ __forceinline__ MapSmem carve(unsigned char *raw, uint32_t W, uint32_t L) {
+  const uint32_t kMaxCand = cand_cap(L);
   MapSmem m;
   const uint32_t NB = nblocks(W);
   m.E = reinterpret_cast<uint32_t *>(raw);
@@ -470,6 +475,7 @@ __device__ __forceinline__ MapSmem carve(unsigned char *raw, uint32_t W, uint32_
 
 __host__ __device__ inline size_t map_smem_bytes(uint32_t W, uint32_t L) {
   const uint32_t NB = nblocks(W);
+  const uint32_t kMaxCand = cand_cap(L);
   return (size_t)W * 8 + ((NB + 31) / 32) * 4 + (size_t)kMaxCand * 8 +
          kImgHash * 4 + (size_t)NB * 2 + (L / 32 + 4) * 2 + kMaxCand * 4 + 16;
 }
@@ -608,6 +614,7 @@ __device__ void seg_bitmaps(const SegShared &sh, const Geom &g,
 __global__ void __launch_bounds__(512)
 map_kernel(Geom g, DevParams p, WsPtrs ws) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  const uint32_t kMaxCand = g.cap;
   __shared__ SegShared sh;
   const int tid = threadIdx.x, nthreads = blockDim.x;
   const uint32_t item = blockIdx.x;
@@ -780,7 +787,8 @@ struct ResShared {
 
 // Exit of `item` from entry position y (file-relative), from its table; kBad
 // when y is not a tabulated entry or its chain escapes.  One lane.
-__device__ uint64_t exit_of(const WsPtrs &ws, const ResShared &r, uint64_t y) {
+__device__ uint64_t exit_of(const WsPtrs &ws, const ResShared &r, uint64_t y,
+                           uint32_t kMaxCand) {
   if (y >= r.q_s) return y;
   if (r.nc == kAbnormal || y < r.p_s) return kBad;
   const uint32_t want = (uint32_t)(y - r.p_s);
@@ -895,6 +903,7 @@ __device__ uint64_t lookback(const ResShared &r, const WsPtrs &ws) {
 __global__ void __launch_bounds__(32)
 resolve_kernel(Geom g, WsPtrs ws) {
   __shared__ ResShared r;
+  const uint32_t kMaxCand = g.cap;
   const int lane = threadIdx.x;
   if (lane == 0) {
     const uint32_t item = atomicAdd(&ws.hdr->ticket, 1u);
@@ -921,7 +930,7 @@ resolve_kernel(Geom g, WsPtrs ws) {
     const uint32_t n = ok ? ws.img_n[item - 1] : 0u;
     if (lane < (int)n) {
       const uint64_t y = ws.img[(uint64_t)(item - 1) * kMaxImage + lane];
-      ws.agg[(uint64_t)item * kMaxImage + lane] = exit_of(ws, r, y);
+      ws.agg[(uint64_t)item * kMaxImage + lane] = exit_of(ws, r, y, g.cap);
     }
     __syncwarp();
     if (lane == 0) {
@@ -1193,9 +1202,9 @@ Layout make_layout(const seqcdc_params_t *p, uint64_t total, uint64_t nfiles,
   l.agg = take(l.imax * kMaxImage * 8);
   l.cand_n = take(l.imax * 4);
   l.ent_n = take(l.imax * 4);
-  l.cand_pos = take(l.imax * (size_t)kMaxCand * 4);
-  l.cand_nxt = take(l.imax * (size_t)kMaxCand * 4);
-  l.ent_term = take(l.imax * (size_t)kMaxCand * 4);
+  l.cand_pos = take(l.imax * (size_t)cand_cap(L) * 4);
+  l.cand_nxt = take(l.imax * (size_t)cand_cap(L) * 4);
+  l.ent_term = take(l.imax * (size_t)cand_cap(L) * 4);
   l.slot = take(l.imax * (size_t)l.slot_cap * 8);
   l.itile = take(l.nitiles * 4);
   l.total = o;
@@ -1246,7 +1255,7 @@ int run(const seqcdc_params_t *p, const uint8_t *d_data, uint64_t total,
   if (cap < total / p->min_size + nfiles) return SEQCDC_ECAPACITY;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const WsPtrs w = ws_ptrs(d_ws, l);
-  Geom g{d_data, total, d_offsets, nfiles, L};
+  Geom g{d_data, total, d_offsets, nfiles, L, cand_cap(L)};
   DevParams dp{p->mode, p->seq_length, p->skip_trigger, p->skip_size,
                (uint32_t)p->min_size, (uint32_t)p->max_size};
   const size_t smem = map_smem_bytes(max_words(L, p->max_size), L);
