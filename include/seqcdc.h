@@ -143,6 +143,38 @@ int seqcdc_chunk_batch(const seqcdc_params_t *p, const uint8_t *d_data,
                        const seqcdc_tuning_t *tuning, void *stream);
 
 /*
+ * Chunking without any device allocation, for callers that must not allocate:
+ * code embedded in a host process whose device memory is owned by another
+ * allocator or pool (a storage engine, a framework plugin), and latency-bound
+ * paths that cannot afford cudaMalloc / cudaFree, which can synchronise the
+ * device and take driver-wide locks.  This entry point has no counterpart in
+ * the paper; it is seqcdc_chunk() with its workspace taken from a fixed
+ * device array inside this library instead of a caller buffer.
+ *
+ *   SEQCDC_NOALLOC_SCRATCH_BYTES  size of that array.  It is part of the
+ *             library image: every GPU that loads the library holds these
+ *             bytes until the process exits.  The input may be at most as
+ *             large as fits: seqcdc_workspace_size(p, n, 1, tuning) must not
+ *             exceed it (about 64 MiB of input for the paper's parameter
+ *             sets), else SEQCDC_ERANGE is returned before anything runs.
+ *   d_in, n, d_cuts, cap, d_count, tuning, stream  as for seqcdc_chunk().
+ *   d_status  optional (may be NULL): one uint32 on the device that receives
+ *             the call's device-side status (SEQCDC_OK, SEQCDC_ETIMEOUT or
+ *             SEQCDC_ECAPACITY), written on `stream` after the chunking.
+ * It calls no cudaMalloc, cudaFree or other allocating routine.  The first
+ * call on a device looks up the array's device address (once per device,
+ * with that device current); make that first call before any stream capture.
+ * All calls share the one array and it keeps the last call's contents (the
+ * kernels reset what they need): calls that overlap on the GPU -- from two
+ * streams or two host threads without ordering -- race and give wrong results.
+ */
+#define SEQCDC_NOALLOC_SCRATCH_BYTES (16u << 20)
+int seqcdc_chunk_noalloc(const seqcdc_params_t *p, const uint8_t *d_in,
+                         uint64_t n, uint64_t *d_cuts, uint64_t cap,
+                         uint64_t *d_count, uint32_t *d_status,
+                         const seqcdc_tuning_t *tuning, void *stream);
+
+/*
  * Synchronise `stream`, then return the device-side status recorded in d_ws by
  * the last call that used it: SEQCDC_OK, SEQCDC_ETIMEOUT when a bounded
  * wait inside a kernel expired, or SEQCDC_ECAPACITY when the device found more

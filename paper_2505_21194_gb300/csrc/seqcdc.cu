@@ -45,6 +45,8 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <mutex>
+
 #include "seqcdc.h"
 
 namespace {
@@ -1287,6 +1289,36 @@ int run(const seqcdc_params_t *p, const uint8_t *d_data, uint64_t total,
   return cudaGetLastError() == cudaSuccess ? SEQCDC_OK : SEQCDC_ECUDA;
 }
 
+// ---------------------------------------------------------------------------
+// Fixed device scratch for seqcdc_chunk_noalloc().  A file-scope device array
+// of SEQCDC_NOALLOC_SCRATCH_BYTES: every GPU that loads this library holds it
+// until the process exits.  In host code its name is only a host-side handle;
+// the device address is looked up once per device and cached.
+// ---------------------------------------------------------------------------
+static __device__ __align__(256) unsigned char g_noalloc_scratch[SEQCDC_NOALLOC_SCRATCH_BYTES];
+
+__global__ void copy_status_kernel(const WsHeader *hdr, uint32_t *out) {
+  *out = hdr->status;
+}
+
+constexpr int kMaxDevices = 64;
+
+// Device address of g_noalloc_scratch on the current device (set-up on first
+// use per device, with that device current).  nullptr on failure.
+void *noalloc_scratch_address() {
+  static std::mutex mu;
+  static void *addr[kMaxDevices] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return nullptr;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!addr[dev]) {
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess) return nullptr;
+    addr[dev] = p;
+  }
+  return addr[dev];
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -1341,6 +1373,23 @@ int seqcdc_chunk_batch(const seqcdc_params_t *p, const uint8_t *d_data,
   if (!d_offsets || !d_cut_offsets) return SEQCDC_EINVAL;
   return run(p, d_data, total_bytes, d_offsets, nfiles, d_cuts, cap,
              d_cut_offsets, nullptr, d_ws, ws_bytes, tuning, stream);
+}
+
+int seqcdc_chunk_noalloc(const seqcdc_params_t *p, const uint8_t *d_in,
+                         uint64_t n, uint64_t *d_cuts, uint64_t cap,
+                         uint64_t *d_count, uint32_t *d_status,
+                         const seqcdc_tuning_t *tuning, void *stream) {
+  if (!d_count || !params_ok(p)) return SEQCDC_EINVAL;
+  const size_t need = make_layout(p, n, 1, pick_segment(p, tuning)).total;
+  if (need > (size_t)SEQCDC_NOALLOC_SCRATCH_BYTES) return SEQCDC_ERANGE;
+  void *ws = noalloc_scratch_address();
+  if (!ws) return SEQCDC_ECUDA;
+  const int rc = run(p, d_in, n, nullptr, 1, d_cuts, cap, nullptr, d_count, ws,
+                     (size_t)SEQCDC_NOALLOC_SCRATCH_BYTES, tuning, stream);
+  if (rc != SEQCDC_OK || !d_status) return rc;
+  copy_status_kernel<<<1, 1, 0, static_cast<cudaStream_t>(stream)>>>(
+      static_cast<const WsHeader *>(ws), d_status);
+  return cudaGetLastError() == cudaSuccess ? SEQCDC_OK : SEQCDC_ECUDA;
 }
 
 int seqcdc_status(const void *d_ws, void *stream) {

@@ -91,6 +91,8 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
         lib.seqcdc_chunk_batch.argtypes = [P, vp, u64, vp, u64, vp, u64, vp, vp,
                                            ctypes.c_size_t, T, vp]
         lib.seqcdc_chunk_batch.restype = ctypes.c_int
+        lib.seqcdc_chunk_noalloc.argtypes = [P, vp, u64, vp, u64, vp, vp, T, vp]
+        lib.seqcdc_chunk_noalloc.restype = ctypes.c_int
         lib.seqcdc_status.argtypes = [vp, vp]
         lib.seqcdc_status.restype = ctypes.c_int
         lib.seqcdc_stats.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_uint32), u32]
@@ -176,6 +178,21 @@ def seqcdc_chunk_batch(p: Params, d_data, total_bytes: int, d_offsets,
         ctypes.byref(p), _ptr(d_data), total_bytes, _ptr(d_offsets), nfiles,
         _ptr(d_cuts), cap, _ptr(d_cut_offsets), _ptr(d_ws), ws_bytes,
         _tuning(tuning), _stream_handle(stream)), "seqcdc_chunk_batch")
+
+
+SEQCDC_NOALLOC_SCRATCH_BYTES = 16 << 20
+
+
+def seqcdc_chunk_noalloc(p: Params, d_in, n: int, d_cuts, cap: int, d_count,
+                         d_status=None, tuning=None, stream=None) -> None:
+    """Raw entry point that allocates nothing (fixed scratch inside the library).
+
+    For callers that cannot allocate device memory; see include/seqcdc.h.
+    """
+    _check(load_library().seqcdc_chunk_noalloc(
+        ctypes.byref(p), _ptr(d_in), n, _ptr(d_cuts), cap, _ptr(d_count),
+        _ptr(d_status), _tuning(tuning), _stream_handle(stream)),
+        "seqcdc_chunk_noalloc")
 
 
 def seqcdc_status(d_ws, stream=None) -> int:
