@@ -128,7 +128,7 @@ def make_workload(rank: int, nfiles: int = NFILES):
 
 def _traffic_record(kernel_src_hash: str):
     """DRAM bytes per launch from the committed ncu summary, if still current."""
-    path = os.path.join(ROOT, "profiles", "segment_kernel_traffic.json")
+    path = os.path.join(ROOT, "profiles", "map_kernel_traffic.json")
     try:
         with open(path) as f:
             d = json.load(f)
@@ -396,7 +396,7 @@ def run_gpu(args):
                 "d2h_bytes_per_step": int(d2h)},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
                      "unit": "GB/s", "frac": round(achieved / peak, 4),
-                     "traffic": traffic, "kernel": "segment_kernel",
+                     "traffic": traffic, "kernel": "map_kernel",
                      "peak_source": peak_kind,
                      "kernel_ms": round(seg_ms, 4)},
         "plain_one_launch_per_file": (
