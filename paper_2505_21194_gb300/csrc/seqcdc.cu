@@ -189,20 +189,6 @@ __device__ uint32_t wait_any(const uint32_t *flag, uint32_t mask, WsHeader *hdr)
   return 0;
 }
 
-// Per-byte "a > b" for four unsigned bytes; the answer is in bit 7 of each
-// byte, the other bits are garbage.  Low seven bits are compared with a
-// borrow-free subtraction ((a | 0x80) - (b & 0x7f) - 1 stays within 0..0xff),
-// the high bits decide when they differ.
-__device__ __forceinline__ uint32_t gt_hi(uint32_t a, uint32_t b) {
-  const uint32_t z = (a | 0x80808080u) - (b & 0x7f7f7f7fu) - 0x01010101u;
-  return (a & ~b) | (~(a ^ b) & z);
-}
-
-// Gather bit 7 of each byte into bits 0..3 (byte k -> bit k).
-__device__ __forceinline__ uint32_t pack4(uint32_t m) {
-  return ((m & 0x80808080u) * 0x00204081u) >> 28;
-}
-
 // Position (0..31) of the k-th set bit (1 <= k <= popc(x)).
 __device__ __forceinline__ uint32_t nth_set_bit(uint32_t x, uint32_t k) {
   uint32_t pos = 0;
@@ -217,24 +203,6 @@ __device__ __forceinline__ uint32_t nth_set_bit(uint32_t x, uint32_t k) {
   c = x & 1u;
   if (k > c) { pos += 1; }
   return pos;
-}
-
-// Target / opposing masks (16 positions) for the 16 bytes in v, given the
-// byte before them.  Bit t refers to the pair (byte t-1, byte t).
-__device__ __forceinline__ void classify16(uint32_t prev_byte, uint4 v,
-                                           uint32_t mode, uint32_t &T16,
-                                           uint32_t &O16) {
-  const uint32_t x0 = v.x, x1 = v.y, x2 = v.z, x3 = v.w;
-  const uint32_t y0 = (x0 << 8) | (prev_byte & 0xffu);
-  const uint32_t y1 = __funnelshift_l(x0, x1, 8);
-  const uint32_t y2 = __funnelshift_l(x1, x2, 8);
-  const uint32_t y3 = __funnelshift_l(x2, x3, 8);
-  const uint32_t up = pack4(gt_hi(x0, y0)) | (pack4(gt_hi(x1, y1)) << 4) |
-                      (pack4(gt_hi(x2, y2)) << 8) | (pack4(gt_hi(x3, y3)) << 12);
-  const uint32_t dn = pack4(gt_hi(y0, x0)) | (pack4(gt_hi(y1, x1)) << 4) |
-                      (pack4(gt_hi(y2, x2)) << 8) | (pack4(gt_hi(y3, x3)) << 12);
-  T16 = mode == 0 ? up : dn;
-  O16 = mode == 0 ? dn : up;
 }
 
 // 16 input bytes at global byte index gi (16-aligned); bytes outside
@@ -523,66 +491,98 @@ __device__ __forceinline__ Bits bits_of(const MapSmem &m) {
   return Bits{m.E, m.O, m.eany, m.ocnt};
 }
 
-// Classify one 16-byte group (lane-parallel), chaining the previous byte and
-// the previous group's T bits through the warp; stores E and O halves.
-__device__ __forceinline__ void bitmap_step(const uint4 v, bool live, uint32_t h,
-                                            uint32_t mode, uint32_t R,
-                                            uint32_t &carry_byte,
-                                            uint32_t &carry_T, uint16_t *E16,
-                                            uint16_t *O16) {
+// Target / opposing bits of one 4-byte word x given y, the same word shifted
+// by one byte (y's byte k is the byte before x's byte k).  Both per-byte
+// unsigned compares come from one borrow-free subtraction: with
+// z1 = (x | 0x80) - (y & 0x7f) - 1 per byte (0..0xfe), bit 7 of z1 is
+// [x_low7 > y_low7] and z2 = 0xfe - z1 = (y | 0x80) - (x & 0x7f) - 1 gives
+// [y_low7 > x_low7]; where the top bits differ they decide.  The bit-7 masks
+// are gathered into nibbles by one multiplication each and accumulated at
+// nibble `k` of up / dn.
+__device__ __forceinline__ void classify_word(uint32_t x, uint32_t y, uint32_t k,
+                                              uint32_t &up, uint32_t &dn) {
+  const uint32_t z1 = (x | 0x80808080u) - (y & 0x7f7f7f7fu) - 0x01010101u;
+  const uint32_t z2 = 0xfefefefeu - z1;
+  const uint32_t gt = (x & ~y) | (~(x ^ y) & z1);   // x > y per byte (bit 7)
+  const uint32_t lt = (y & ~x) | (~(x ^ y) & z2);   // x < y per byte (bit 7)
+  up += (((gt & 0x80808080u) * 0x00204081u) >> 28) << (4 * k);
+  dn += (((lt & 0x80808080u) * 0x00204081u) >> 28) << (4 * k);
+}
+
+// One lane step: 32 bytes (two 16-byte loads) -> one 32-bit E word and one O
+// word, chaining the previous byte and the previous word's T bits through the
+// warp (carry from lane 31 of the previous step).
+__device__ __forceinline__ void bitmap_step32(const uint4 v0, const uint4 v1,
+                                              bool live, uint32_t g,
+                                              uint32_t mode, uint32_t R,
+                                              uint32_t &carry_byte,
+                                              uint32_t &carry_T, uint32_t *E,
+                                              uint32_t *O) {
   const int lane = threadIdx.x & 31;
-  uint32_t pb = __shfl_up_sync(0xffffffffu, v.w >> 24, 1);
+  uint32_t pb = __shfl_up_sync(0xffffffffu, v1.w >> 24, 1);
   if (lane == 0) pb = carry_byte;
-  uint32_t t16, o16;
-  classify16(pb, v, mode, t16, o16);
-  uint32_t pt = __shfl_up_sync(0xffffffffu, t16, 1);
+  uint32_t up = 0, dn = 0;
+  classify_word(v0.x, (v0.x << 8) | pb, 0, up, dn);
+  classify_word(v0.y, __funnelshift_l(v0.x, v0.y, 8), 1, up, dn);
+  classify_word(v0.z, __funnelshift_l(v0.y, v0.z, 8), 2, up, dn);
+  classify_word(v0.w, __funnelshift_l(v0.z, v0.w, 8), 3, up, dn);
+  classify_word(v1.x, __funnelshift_l(v0.w, v1.x, 8), 4, up, dn);
+  classify_word(v1.y, __funnelshift_l(v1.x, v1.y, 8), 5, up, dn);
+  classify_word(v1.z, __funnelshift_l(v1.y, v1.z, 8), 6, up, dn);
+  classify_word(v1.w, __funnelshift_l(v1.z, v1.w, 8), 7, up, dn);
+  const uint32_t T = mode == 0 ? up : dn;
+  const uint32_t Ow = mode == 0 ? dn : up;
+  uint32_t pt = __shfl_up_sync(0xffffffffu, T, 1);
   if (lane == 0) pt = carry_T;
-  // E at group position t needs T at t, t-1, ..., t-(R-2): the previous
-  // group's T bits sit below this group's in a 32-bit window.
-  const uint32_t tw = (t16 << 16) | (pt & 0xffffu);
-  uint32_t ew = tw;
-  for (uint32_t k = 1; k + 1 < R; ++k) ew &= tw << k;
+  // E at position t needs T at t, t-1, ..., t-(R-2); the previous word's T
+  // bits supply the positions before this word.
+  uint32_t ew = T;
+  for (uint32_t k = 1; k + 1 < R; ++k) ew &= __funnelshift_l(pt, T, k);
   if (live) {
-    E16[h] = (uint16_t)(ew >> 16);
-    O16[h] = (uint16_t)o16;
+    E[g] = ew;
+    O[g] = Ow;
   }
-  carry_byte = __shfl_sync(0xffffffffu, v.w >> 24, 31);
-  carry_T = __shfl_sync(0xffffffffu, t16, 31);
+  carry_byte = __shfl_sync(0xffffffffu, v1.w >> 24, 31);
+  carry_T = __shfl_sync(0xffffffffu, T, 31);
 }
 
 // E and O bitmaps of the window [B, B + 32 W) and their block summaries.
-// Each lane keeps two 16-byte loads in flight.
+// Each warp covers a contiguous run of 32-byte words; each lane keeps up to
+// four 16-byte loads in flight.
 __device__ void seg_bitmaps(const SegShared &sh, const Geom &g,
                             const DevParams &p, uint32_t *E, uint32_t *O,
                             uint32_t *eany, uint16_t *ocnt) {
   const int tid = threadIdx.x, nthreads = blockDim.x;
   const uint32_t W = sh.W;
   const int64_t gwin = (int64_t)sh.gbase + sh.B;  // global byte index of rel 0
-  uint16_t *E16 = reinterpret_cast<uint16_t *>(E);
-  uint16_t *O16 = reinterpret_cast<uint16_t *>(O);
-  const uint32_t H = 2 * W;  // 16-byte groups
   const int lane = tid & 31, warp = tid >> 5, nwarps = nthreads >> 5;
-  uint32_t per = (H + nwarps - 1) / nwarps;
+  uint32_t per = (W + nwarps - 1) / nwarps;
   per = (per + 63) & ~63u;
-  const uint32_t h0 = warp * per;
-  const uint32_t h1 = min(h0 + per, H);
+  const uint32_t w0 = warp * per;
+  const uint32_t w1 = min(w0 + per, W);
   uint32_t carry_byte = 0, carry_T = 0;
-  if (h0 < h1 && h0 > 0) {
-    // T bits of the 16 positions before this warp's first group (only the top
+  if (w0 < w1 && w0 > 0) {
+    // T bits of the 16 positions before this warp's first word (only the top
     // SeqLength-2 of them matter, so the unknown byte before them is moot).
-    const uint4 pv = load16(g.data, gwin + 16 * (int64_t)(h0 - 1), g.total);
-    uint32_t t16, o16;
-    classify16(0, pv, p.mode, t16, o16);
-    carry_T = t16;
+    const uint4 pv = load16(g.data, gwin + 32 * (int64_t)w0 - 16, g.total);
+    uint32_t up = 0, dn = 0;
+    classify_word(pv.x, pv.x << 8, 0, up, dn);
+    classify_word(pv.y, __funnelshift_l(pv.x, pv.y, 8), 1, up, dn);
+    classify_word(pv.z, __funnelshift_l(pv.y, pv.z, 8), 2, up, dn);
+    classify_word(pv.w, __funnelshift_l(pv.z, pv.w, 8), 3, up, dn);
+    carry_T = (p.mode == 0 ? up : dn) << 16;
     carry_byte = pv.w >> 24;
   }
-  for (uint32_t hb = h0; hb < h1; hb += 64) {
-    const uint32_t ha = hb + lane, hc = hb + 32 + lane;
-    const bool la = ha < h1, lc = hc < h1;
-    const uint4 va = la ? load16(g.data, gwin + 16 * (int64_t)ha, g.total) : make_uint4(0, 0, 0, 0);
-    const uint4 vc = lc ? load16(g.data, gwin + 16 * (int64_t)hc, g.total) : make_uint4(0, 0, 0, 0);
-    bitmap_step(va, la, ha, p.mode, p.R, carry_byte, carry_T, E16, O16);
-    bitmap_step(vc, lc, hc, p.mode, p.R, carry_byte, carry_T, E16, O16);
+  for (uint32_t wb = w0; wb < w1; wb += 64) {
+    const uint32_t ga = wb + lane, gc = wb + 32 + lane;
+    const bool la = ga < w1, lc = gc < w1;
+    const int64_t ba = gwin + 32 * (int64_t)ga, bc = gwin + 32 * (int64_t)gc;
+    const uint4 a0 = la ? load16(g.data, ba, g.total) : make_uint4(0, 0, 0, 0);
+    const uint4 a1 = la ? load16(g.data, ba + 16, g.total) : make_uint4(0, 0, 0, 0);
+    const uint4 c0 = lc ? load16(g.data, bc, g.total) : make_uint4(0, 0, 0, 0);
+    const uint4 c1 = lc ? load16(g.data, bc + 16, g.total) : make_uint4(0, 0, 0, 0);
+    bitmap_step32(a0, a1, la, ga, p.mode, p.R, carry_byte, carry_T, E, O);
+    bitmap_step32(c0, c1, lc, gc, p.mode, p.R, carry_byte, carry_T, E, O);
   }
   __syncthreads();
   // Block summaries; each warp covers 32 consecutive blocks per pass.
@@ -591,8 +591,8 @@ __device__ void seg_bitmaps(const SegShared &sh, const Geom &g,
     const uint32_t b = b0 + lane;
     uint32_t any = 0, cnt = 0;
     if (b < NB) {
-      const uint32_t w0 = b * 8, w1 = min(w0 + 8, W);
-      for (uint32_t w = w0; w < w1; ++w) {
+      const uint32_t v0 = b * 8, v1 = min(v0 + 8, W);
+      for (uint32_t w = v0; w < v1; ++w) {
         any |= E[w];
         cnt += __popc(O[w]);
       }
