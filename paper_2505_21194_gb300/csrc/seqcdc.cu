@@ -409,7 +409,7 @@ struct SegShared {
   int64_t B;          // window base (file-relative); global index of rel 0 is 16-aligned
   uint64_t p_s, q_s, n_f, gbase;
   uint32_t W, NB;     // bitmap words, blocks
-  uint32_t nc, nent, ninvalid, nimg;
+  uint32_t nc, nent, ninvalid, nimg, qhead;
   uint32_t scratch[32];
 };
 
@@ -461,6 +461,23 @@ __device__ __forceinline__ uint32_t find_file(const uint32_t *seg_base,
   return (uint32_t)lo;
 }
 
+// find_file by one warp: a 32-ary search (three rounds cover 32768 files).
+__device__ uint32_t find_file_warp(const uint32_t *seg_base, uint64_t nfiles,
+                                   uint32_t item) {
+  const int lane = threadIdx.x & 31;
+  uint64_t lo = 0, hi = nfiles;  // answer in [lo, hi); seg_base[lo] <= item
+  while (hi - lo > 1) {
+    const uint64_t step = (hi - lo + 31) / 32;
+    const uint64_t probe = lo + (uint64_t)lane * step;
+    const bool ok = probe < hi && seg_base[probe] <= item;
+    const uint32_t m = __ballot_sync(0xffffffffu, ok);
+    const uint64_t nlo = lo + (uint64_t)(31 - __clz(m)) * step;
+    hi = min(nlo + step, hi);
+    lo = nlo;
+  }
+  return (uint32_t)lo;
+}
+
 // Geometry of item (file, seg); one thread.
 __device__ void seg_setup(SegShared &sh, const Geom &g, const DevParams &p,
                           uint32_t item, uint32_t file, uint32_t seg,
@@ -485,6 +502,7 @@ __device__ void seg_setup(SegShared &sh, const Geom &g, const DevParams &p,
   sh.nent = 0;
   sh.ninvalid = 0;
   sh.nimg = 0;
+  sh.qhead = 0;
 }
 
 __device__ __forceinline__ Bits bits_of(const MapSmem &m) {
@@ -622,9 +640,9 @@ map_kernel(Geom g, DevParams p, WsPtrs ws) {
   const uint32_t item = blockIdx.x;
   const uint32_t nitems = ws.hdr->nitems;
   if (item >= nitems) return;
-  if (tid == 0) {
-    const uint32_t f = find_file(ws.seg_base, g.nfiles, item);
-    seg_setup(sh, g, p, item, f, item - ws.seg_base[f], ws.seg_base[f]);
+  if (tid < 32) {
+    const uint32_t f = find_file_warp(ws.seg_base, g.nfiles, item);
+    if (tid == 0) seg_setup(sh, g, p, item, f, item - ws.seg_base[f], ws.seg_base[f]);
   }
   __syncthreads();
   const MapSmem m = carve(smem_raw, sh.W, g.L);
@@ -699,35 +717,79 @@ map_kernel(Geom g, DevParams p, WsPtrs ws) {
   }
 
   // Next cut of every candidate, as a candidate index or a terminal code.
+  // Lanes advance one scan region per iteration and take a new candidate
+  // from a block-wide queue when theirs is done, so a warp's lanes stay busy
+  // however many regions a chunk needs.
   const Bits bits = bits_of(m);
   const uint32_t tmask_lo = ~((1u << (lo & 31)) - 1u);
-  for (uint32_t k = tid; k < nc; k += nthreads) {
-    const uint32_t y = chunk_step(bits, p, m.cpos[k], end_rel);
-    uint32_t code;
-    if (y >= q_rel) {
-      code = kTerminal | (y - ps_rel);
-    } else {
-      const uint32_t e = y - 1;
-      const uint32_t w = e >> 5;
-      const uint32_t bit = 1u << (e & 31);
-      if (m.E[w] & bit) {
-        uint32_t below = m.E[w] & (bit - 1u);
-        if (w == wlo) below &= tmask_lo;
-        code = first + m.erank[w - wlo] + __popc(below);
-      } else {
-        code = kEscape;  // a forced cut inside the item: not a candidate
+  const uint32_t skip_min = p.mn > p.R ? p.mn - p.R : 0u;
+  const int lane = tid & 31;
+  for (int j = tid; j < kImgHash; j += nthreads) m.ihash[j] = kEscape;
+  uint32_t k = kNone, lim = 0, i = 0;
+  while (true) {
+    const uint32_t want = __ballot_sync(0xffffffffu, k == kNone);
+    if (want) {
+      const int leader = __ffs(want) - 1;
+      uint32_t base = 0;
+      if (lane == leader) base = atomicAdd(&sh.qhead, (uint32_t)__popc(want));
+      base = __shfl_sync(0xffffffffu, base, leader);
+      if (k == kNone) {
+        const uint32_t kk = base + __popc(want & ((1u << lane) - 1u));
+        if (kk < nc) {
+          k = kk;
+          const uint32_t c = m.cpos[kk];
+          lim = (end_rel - c > p.mx) ? c + p.mx : end_rel;
+          i = c + skip_min;
+        }
       }
     }
-    m.cnxt[k] = code;
-    m.jmp[k] = (code & kTerminal) ? (uint16_t)k : (uint16_t)code;
+    if (__ballot_sync(0xffffffffu, k != kNone) == 0) break;
+    if (k != kNone) {
+      uint32_t y = kNone;
+      if (i + 1 >= lim) {
+        y = lim;                                    // max size or input end
+      } else {
+        const uint32_t sp = p.T ? nth_O(bits, i + 1, p.T, lim) : kNone;
+        const uint32_t e = first_E(bits, i + p.R - 1, sp == kNone ? lim : sp);
+        if (e != kNone) y = e + 1;                  // boundary run (Sec. III.A)
+        else if (sp == kNone) y = lim;
+        else i = sp + 1 + p.S;                      // content-defined skip (Sec. III.C)
+      }
+      if (y != kNone) {
+        uint32_t code;
+        if (y >= q_rel) {
+          code = kTerminal | (y - ps_rel);
+        } else {
+          const uint32_t e = y - 1;
+          const uint32_t w = e >> 5;
+          const uint32_t bit = 1u << (e & 31);
+          if (m.E[w] & bit) {
+            uint32_t below = m.E[w] & (bit - 1u);
+            if (w == wlo) below &= tmask_lo;
+            code = first + m.erank[w - wlo] + __popc(below);
+          } else {
+            code = kEscape;  // a forced cut inside the item: not a candidate
+          }
+        }
+        m.cnxt[k] = code;
+        m.jmp[k] = (code & kTerminal) ? (uint16_t)k : (uint16_t)code;
+        k = kNone;
+      }
+    }
   }
-  for (int i = tid; i < kImgHash; i += nthreads) m.ihash[i] = kEscape;
   __syncthreads();
-  // Pointer doubling: jmp[k] -> last candidate of k's chain.
-  for (uint32_t r = 1; r < 2 * nc; r <<= 1) {
-    for (uint32_t k = tid; k < nc; k += nthreads) m.jtmp[k] = m.jmp[m.jmp[k]];
-    __syncthreads();
-    for (uint32_t k = tid; k < nc; k += nthreads) m.jmp[k] = m.jtmp[k];
+  // Pointer doubling: jmp[k] -> last candidate of k's chain; stops when no
+  // pointer moves.
+  while (true) {
+    bool moved = false;
+    for (uint32_t c = tid; c < nc; c += nthreads) {
+      const uint16_t j = m.jmp[c];
+      const uint16_t jj = m.jmp[j];
+      m.jtmp[c] = jj;
+      moved |= (jj != j);
+    }
+    if (!__syncthreads_or(moved)) break;
+    for (uint32_t c = tid; c < nc; c += nthreads) m.jmp[c] = m.jtmp[c];
     __syncthreads();
   }
   // Publish the candidate graph and every entry's exit; collect distinct exits.
@@ -907,11 +969,15 @@ resolve_kernel(Geom g, WsPtrs ws) {
   __shared__ ResShared r;
   const uint32_t kMaxCand = g.cap;
   const int lane = threadIdx.x;
+  uint32_t tk = 0;
+  if (lane == 0) tk = atomicAdd(&ws.hdr->ticket, 1u);
+  tk = __shfl_sync(0xffffffffu, tk, 0);
+  const uint32_t fw = (tk < ws.hdr->nitems) ? find_file_warp(ws.seg_base, g.nfiles, tk) : 0u;
   if (lane == 0) {
-    const uint32_t item = atomicAdd(&ws.hdr->ticket, 1u);
+    const uint32_t item = tk;
     r.item = item;
     if (item < ws.hdr->nitems) {
-      const uint32_t f = find_file(ws.seg_base, g.nfiles, item);
+      const uint32_t f = fw;
       r.file = f;
       r.first_item = ws.seg_base[f];
       r.seg = item - r.first_item;
