@@ -60,9 +60,9 @@ extern "C" {
  *                 Sec. VI.D).
  *   skip_size     bytes ignored after a skip fires (Sec. III.C).
  *   min_size      minimum chunk size, >= 1 (Sec. III.B).
- *   max_size      maximum chunk size, >= min_size and <= 262144 (256 KiB:
- *                 one block stages its segment plus max_size bytes in
- *                 shared memory).
+ *   max_size      maximum chunk size, >= min_size and <= 131072 (128 KiB:
+ *                 one block keeps the bitmaps of its segment plus max_size
+ *                 bytes of look-ahead in shared memory).
  */
 typedef struct {
     uint32_t mode;
@@ -75,9 +75,11 @@ typedef struct {
 
 /*
  * Launch tuning (all fields 0 = library default).
- *   segment_bytes  bytes of input one thread block owns (multiple of 1024,
- *                  >= 4096).  Larger segments mean fewer junctions but more
- *                  shared memory.
+ *   segment_bytes  bytes of input one thread block owns (rounded up to a
+ *                  multiple of 1024; at least 4096 and at least max_size;
+ *                  lowered if the block's shared memory would not fit).
+ *                  Larger segments mean fewer junctions but more shared
+ *                  memory per block.
  *   block_threads  threads per block of the segment kernel (128, 256, 512).
  */
 typedef struct {

@@ -59,7 +59,7 @@ constexpr int kMaxImage = 32;      // distinct exits published per item (one per
 constexpr int kFileTile = 1024;    // files per plan block
 constexpr int kItemTile = 256;     // items per compaction block
 constexpr uint32_t kMaxSeqLength = 16;
-constexpr uint64_t kMaxMaxSize = 262144;
+constexpr uint64_t kMaxMaxSize = 131072;
 constexpr uint64_t kWaitNs = 2000000000ull;  // 2 s bound on any device wait
 
 // Item state bits (set once, in this order of availability).
@@ -249,74 +249,62 @@ __device__ uint32_t block_excl_scan(uint32_t v, uint32_t *scratch,
 
 // ---------------------------------------------------------------------------
 // Bitmaps of one item in shared memory.  Positions are relative to the window
-// base B (file-relative): rel = pos - B; word w covers rel 32w .. 32w+31; a
-// block is 8 words (256 positions).
-//   E, O    run-end and opposing-pair bits
-//   eany    bit b set when block b has an E bit
-//   ocnt    number of O bits in block b
+// base B (file-relative): rel = pos - B; word w covers rel 32w .. 32w+31.
+//   E, O   run-end and opposing-pair bits
+//   ne     ne[w]: first word >= w holding an E bit (kNoWord if none)
+//   ocum   ocum[w]: O bits in words < w (ocum[W] = all)
+//   notw   notw[w]: the word holding the T-th O bit counted from the start of
+//          word w (kNoWord if the window has fewer)
+// With these a scan-region query (Sec. III.D: first set bit of the combined
+// run mask; position of the SkipTrigger-th opposing pair) is a few lookups.
 // ---------------------------------------------------------------------------
+constexpr uint16_t kNoWord = 0xFFFFu;
+
 struct Bits {
   const uint32_t *E;
   const uint32_t *O;
-  const uint32_t *eany;
-  const uint16_t *ocnt;
+  const uint16_t *ne;
+  const uint32_t *ocum;
+  const uint16_t *notw;
+  uint32_t W;
 };
 
 // First E position in [x, limit), or kNone.
 __device__ __forceinline__ uint32_t first_E(const Bits &b, uint32_t x,
                                             uint32_t limit) {
   if (x >= limit) return kNone;
-  const uint32_t wl = (limit - 1) >> 5;
   uint32_t w = x >> 5;
   uint32_t m = b.E[w] & (~0u << (x & 31));
-  while (true) {
-    if (m) {
-      const uint32_t pos = (w << 5) + (__ffs(m) - 1);
-      return pos < limit ? pos : kNone;
-    }
-    if (w >= wl) return kNone;
-    ++w;
-    if ((w & 7) == 0) {  // block boundary: jump to the next block with E bits
-      const uint32_t bl = wl >> 3;
-      uint32_t bi = w >> 3;
-      uint32_t fw = bi >> 5;
-      uint32_t fm = b.eany[fw] & (~0u << (bi & 31));
-      while (!fm) {
-        ++fw;
-        if ((fw << 5) > bl) return kNone;
-        fm = b.eany[fw];
-      }
-      bi = (fw << 5) + (__ffs(fm) - 1);
-      if (bi > bl) return kNone;
-      w = bi << 3;
-    }
+  if (!m) {
+    if (w + 1 >= b.W) return kNone;
+    w = b.ne[w + 1];
+    if (w == kNoWord) return kNone;
     m = b.E[w];
   }
+  const uint32_t pos = (w << 5) + (__ffs(m) - 1);
+  return pos < limit ? pos : kNone;
 }
 
-// Position of the need-th O bit at or after x (need >= 1), if < limit; else kNone.
+// Position of the need-th O bit at or after x (need >= 1), if < limit; else
+// kNone.  `need` is SkipTrigger, for which notw was built.
 __device__ __forceinline__ uint32_t nth_O(const Bits &b, uint32_t x,
                                           uint32_t need, uint32_t limit) {
   if (x >= limit) return kNone;
-  const uint32_t wl = (limit - 1) >> 5;
-  uint32_t w = x >> 5;
-  uint32_t m = b.O[w] & (~0u << (x & 31));
+  const uint32_t w0 = x >> 5;
+  // The need-th O bit at or after x is the k-th counted from word w0's start.
+  const uint32_t k = need + __popc(b.O[w0] & ((1u << (x & 31)) - 1u));
+  uint32_t w = b.notw[w0];  // word of the need-th from w0's start; k-th is at or after
+  if (w == kNoWord) return kNone;
+  uint32_t cnt = b.ocum[w] - b.ocum[w0];
+  uint32_t m = b.O[w];
   uint32_t c = __popc(m);
-  while (c < need) {
-    need -= c;
-    if (w >= wl) return kNone;
-    ++w;
-    if ((w & 7) == 0) {  // whole blocks that cannot hold the need-th bit
-      while (w + 8 <= wl + 1 && b.ocnt[w >> 3] < need) {
-        need -= b.ocnt[w >> 3];
-        w += 8;
-      }
-      if (w > wl) return kNone;
-    }
+  while (cnt + c < k) {
+    cnt += c;
+    if (++w >= b.W || (w << 5) >= limit) return kNone;
     m = b.O[w];
     c = __popc(m);
   }
-  const uint32_t pos = (w << 5) + nth_set_bit(m, need);
+  const uint32_t pos = (w << 5) + nth_set_bit(m, k - cnt);
   return pos < limit ? pos : kNone;
 }
 
@@ -408,46 +396,46 @@ struct SegShared {
   uint32_t item, file, seg, first_item;
   int64_t B;          // window base (file-relative); global index of rel 0 is 16-aligned
   uint64_t p_s, q_s, n_f, gbase;
-  uint32_t W, NB;     // bitmap words, blocks
+  uint32_t W;         // bitmap words
   uint32_t nc, nent, ninvalid, nimg, qhead;
   uint32_t scratch[32];
 };
 
-// Shared memory of the map kernel (bitmaps, summaries, candidate graph).
+// Shared memory of the map kernel (bitmaps, query tables, candidate graph).
 struct MapSmem {
-  uint32_t *E, *O, *eany;
-  uint16_t *ocnt;
-  uint16_t *erank;   // candidate run ends in words before w (from the first candidate word)
-  uint32_t *cpos;    // kMaxCand: candidate positions (rel)
-  uint32_t *cnxt;    // kMaxCand: next candidate index or terminal code
-  uint16_t *jmp, *jtmp;  // kMaxCand: pointer doubling
+  uint32_t *E, *O;
+  uint32_t *ocum;    // W + 1
+  uint16_t *ne;      // W
+  uint16_t *notw;    // W
+  uint32_t *cpos;    // cap: candidate positions (rel)
+  uint32_t *cnxt;    // cap: next candidate index or terminal code
+  uint16_t *jmp, *jtmp;  // cap: pointer doubling
   uint32_t *ihash;   // kImgHash: distinct exits
+  uint32_t *bscratch;  // 64: block helpers
 };
 
-__host__ __device__ inline uint32_t nblocks(uint32_t W) { return (W + 7) / 8; }
-
 __device__ __forceinline__ MapSmem carve(unsigned char *raw, uint32_t W, uint32_t L) {
-  const uint32_t kMaxCand = cand_cap(L);
+  const uint32_t cap = cand_cap(L);
+  const uint32_t Wp = (W + 1) & ~1u;  // even stride: E and O take 8-byte stores
   MapSmem m;
-  const uint32_t NB = nblocks(W);
   m.E = reinterpret_cast<uint32_t *>(raw);
-  m.O = m.E + W;
-  m.eany = m.O + W;
-  m.cpos = m.eany + (NB + 31) / 32;
-  m.cnxt = m.cpos + kMaxCand;
-  m.ihash = m.cnxt + kMaxCand;
-  m.ocnt = reinterpret_cast<uint16_t *>(m.ihash + kImgHash);
-  m.erank = m.ocnt + NB;
-  m.jmp = m.erank + (L / 32 + 4);
-  m.jtmp = m.jmp + kMaxCand;
+  m.O = m.E + Wp;
+  m.ocum = m.O + Wp;
+  m.cpos = m.ocum + W + 1;
+  m.cnxt = m.cpos + cap;
+  m.ihash = m.cnxt + cap;
+  m.bscratch = m.ihash + kImgHash;
+  m.ne = reinterpret_cast<uint16_t *>(m.bscratch + 64);
+  m.notw = m.ne + W;
+  m.jmp = m.notw + W;
+  m.jtmp = m.jmp + cap;
   return m;
 }
 
 __host__ __device__ inline size_t map_smem_bytes(uint32_t W, uint32_t L) {
-  const uint32_t NB = nblocks(W);
-  const uint32_t kMaxCand = cand_cap(L);
-  return (size_t)W * 8 + ((NB + 31) / 32) * 4 + (size_t)kMaxCand * 8 +
-         kImgHash * 4 + (size_t)NB * 2 + (L / 32 + 4) * 2 + kMaxCand * 4 + 16;
+  const uint32_t cap = cand_cap(L);
+  // E, O (even stride), ocum (W + 1), ne, notw: at most 16 bytes per word + 8.
+  return (size_t)(W + 1) * 16 + 8 + (size_t)cap * 12 + kImgHash * 4 + 64 * 4 + 16;
 }
 
 __device__ __forceinline__ uint32_t find_file(const uint32_t *seg_base,
@@ -497,7 +485,6 @@ __device__ void seg_setup(SegShared &sh, const Geom &g, const DevParams &p,
   gb = gb >= 0 ? (gb & ~(int64_t)15) : -(((-gb) + 15) & ~(int64_t)15);
   sh.B = gb - (int64_t)sh.gbase;
   sh.W = (uint32_t)(((int64_t)w1 - sh.B + 31) >> 5);
-  sh.NB = nblocks(sh.W);
   sh.nc = 0;
   sh.nent = 0;
   sh.ninvalid = 0;
@@ -505,8 +492,8 @@ __device__ void seg_setup(SegShared &sh, const Geom &g, const DevParams &p,
   sh.qhead = 0;
 }
 
-__device__ __forceinline__ Bits bits_of(const MapSmem &m) {
-  return Bits{m.E, m.O, m.eany, m.ocnt};
+__device__ __forceinline__ Bits bits_of(const MapSmem &m, uint32_t W) {
+  return Bits{m.E, m.O, m.ne, m.ocum, m.notw, W};
 }
 
 // Target / opposing bits of one 4-byte word x given y, the same word shifted
@@ -527,20 +514,13 @@ __device__ __forceinline__ void classify_word(uint32_t x, uint32_t y, uint32_t k
   dn += (((lt & 0x80808080u) * 0x00204081u) >> 28) << (4 * k);
 }
 
-// One lane step: 32 bytes (two 16-byte loads) -> one 32-bit E word and one O
-// word, chaining the previous byte and the previous word's T bits through the
-// warp (carry from lane 31 of the previous step).
-__device__ __forceinline__ void bitmap_step32(const uint4 v0, const uint4 v1,
-                                              bool live, uint32_t g,
-                                              uint32_t mode, uint32_t R,
-                                              uint32_t &carry_byte,
-                                              uint32_t &carry_T, uint32_t *E,
-                                              uint32_t *O) {
-  const int lane = threadIdx.x & 31;
-  uint32_t pb = __shfl_up_sync(0xffffffffu, v1.w >> 24, 1);
-  if (lane == 0) pb = carry_byte;
+// 32 bytes (two 16-byte vectors) with the byte before them -> T and O bits
+// of the 32 positions (bit t = pair (byte t-1, byte t)).
+__device__ __forceinline__ void classify32(uint4 v0, uint4 v1, uint32_t prev_byte,
+                                           uint32_t mode, uint32_t &T,
+                                           uint32_t &Ow) {
   uint32_t up = 0, dn = 0;
-  classify_word(v0.x, (v0.x << 8) | pb, 0, up, dn);
+  classify_word(v0.x, (v0.x << 8) | (prev_byte & 0xffu), 0, up, dn);
   classify_word(v0.y, __funnelshift_l(v0.x, v0.y, 8), 1, up, dn);
   classify_word(v0.z, __funnelshift_l(v0.y, v0.z, 8), 2, up, dn);
   classify_word(v0.w, __funnelshift_l(v0.z, v0.w, 8), 3, up, dn);
@@ -548,30 +528,55 @@ __device__ __forceinline__ void bitmap_step32(const uint4 v0, const uint4 v1,
   classify_word(v1.y, __funnelshift_l(v1.x, v1.y, 8), 5, up, dn);
   classify_word(v1.z, __funnelshift_l(v1.y, v1.z, 8), 6, up, dn);
   classify_word(v1.w, __funnelshift_l(v1.z, v1.w, 8), 7, up, dn);
-  const uint32_t T = mode == 0 ? up : dn;
-  const uint32_t Ow = mode == 0 ? dn : up;
-  uint32_t pt = __shfl_up_sync(0xffffffffu, T, 1);
-  if (lane == 0) pt = carry_T;
-  // E at position t needs T at t, t-1, ..., t-(R-2); the previous word's T
-  // bits supply the positions before this word.
-  uint32_t ew = T;
-  for (uint32_t k = 1; k + 1 < R; ++k) ew &= __funnelshift_l(pt, T, k);
-  if (live) {
-    E[g] = ew;
-    O[g] = Ow;
-  }
-  carry_byte = __shfl_sync(0xffffffffu, v1.w >> 24, 31);
-  carry_T = __shfl_sync(0xffffffffu, T, 31);
+  T = mode == 0 ? up : dn;
+  Ow = mode == 0 ? dn : up;
 }
 
-// E and O bitmaps of the window [B, B + 32 W) and their block summaries.
-// Each warp covers a contiguous run of 32-byte words; each lane keeps up to
-// four 16-byte loads in flight.
+// E at position t needs T at t, t-1, ..., t-(R-2); `pt` holds the T bits of
+// the 32 positions before.
+__device__ __forceinline__ uint32_t run_ends(uint32_t pt, uint32_t T, uint32_t R) {
+  uint32_t ew = T;
+  for (uint32_t k = 1; k + 1 < R; ++k) ew &= __funnelshift_l(pt, T, k);
+  return ew;
+}
+
+// Inclusive suffix minimum over the block's threads (value per thread).
+__device__ uint32_t block_suffix_min_excl(uint32_t v, uint32_t *scratch) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nwarps = blockDim.x >> 5;
+  uint32_t x = v;  // inclusive suffix min within the warp
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint32_t y = __shfl_down_sync(0xffffffffu, x, d);
+    if (lane + d < 32) x = min(x, y);
+  }
+  if (lane == 0) scratch[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t t = lane < nwarps ? scratch[lane] : 0xffffffffu;
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint32_t y = __shfl_down_sync(0xffffffffu, t, d);
+      if (lane + d < 32) t = min(t, y);
+    }
+    if (lane < nwarps) scratch[32 + lane] = t;  // suffix min of warps >= lane
+  }
+  __syncthreads();
+  // exclusive: min over threads after this one
+  uint32_t after = __shfl_down_sync(0xffffffffu, x, 1);
+  if (lane == 31) after = 0xffffffffu;
+  const uint32_t later = (warp + 1 < nwarps) ? scratch[32 + warp + 1] : 0xffffffffu;
+  const uint32_t r = min(after, later);
+  __syncthreads();
+  return r;
+}
+
+// E and O bitmaps of the window [B, B + 32 W) and their query tables.  Each
+// warp covers a contiguous run of words; a lane takes 64 bytes (two words)
+// per step with four 16-byte loads in flight.
 __device__ void seg_bitmaps(const SegShared &sh, const Geom &g,
-                            const DevParams &p, uint32_t *E, uint32_t *O,
-                            uint32_t *eany, uint16_t *ocnt) {
+                            const DevParams &p, const MapSmem &m) {
   const int tid = threadIdx.x, nthreads = blockDim.x;
   const uint32_t W = sh.W;
+  const uint8_t *base = g.data;
   const int64_t gwin = (int64_t)sh.gbase + sh.B;  // global byte index of rel 0
   const int lane = tid & 31, warp = tid >> 5, nwarps = nthreads >> 5;
   uint32_t per = (W + nwarps - 1) / nwarps;
@@ -582,7 +587,7 @@ __device__ void seg_bitmaps(const SegShared &sh, const Geom &g,
   if (w0 < w1 && w0 > 0) {
     // T bits of the 16 positions before this warp's first word (only the top
     // SeqLength-2 of them matter, so the unknown byte before them is moot).
-    const uint4 pv = load16(g.data, gwin + 32 * (int64_t)w0 - 16, g.total);
+    const uint4 pv = load16(base, gwin + 32 * (int64_t)w0 - 16, g.total);
     uint32_t up = 0, dn = 0;
     classify_word(pv.x, pv.x << 8, 0, up, dn);
     classify_word(pv.y, __funnelshift_l(pv.x, pv.y, 8), 1, up, dn);
@@ -592,32 +597,85 @@ __device__ void seg_bitmaps(const SegShared &sh, const Geom &g,
     carry_byte = pv.w >> 24;
   }
   for (uint32_t wb = w0; wb < w1; wb += 64) {
-    const uint32_t ga = wb + lane, gc = wb + 32 + lane;
-    const bool la = ga < w1, lc = gc < w1;
-    const int64_t ba = gwin + 32 * (int64_t)ga, bc = gwin + 32 * (int64_t)gc;
-    const uint4 a0 = la ? load16(g.data, ba, g.total) : make_uint4(0, 0, 0, 0);
-    const uint4 a1 = la ? load16(g.data, ba + 16, g.total) : make_uint4(0, 0, 0, 0);
-    const uint4 c0 = lc ? load16(g.data, bc, g.total) : make_uint4(0, 0, 0, 0);
-    const uint4 c1 = lc ? load16(g.data, bc + 16, g.total) : make_uint4(0, 0, 0, 0);
-    bitmap_step32(a0, a1, la, ga, p.mode, p.R, carry_byte, carry_T, E, O);
-    bitmap_step32(c0, c1, lc, gc, p.mode, p.R, carry_byte, carry_T, E, O);
+    const uint32_t wa = wb + 2 * lane;          // this lane's words wa, wa+1
+    const bool la = wa < w1, lb = wa + 1 < w1;
+    const int64_t gi = gwin + 32 * (int64_t)wa;
+    uint4 v0 = make_uint4(0, 0, 0, 0), v1 = v0, v2 = v0, v3 = v0;
+    if (la) {
+      if (gi >= 0 && (uint64_t)gi + 64 <= g.total) {
+        const uint4 *q = reinterpret_cast<const uint4 *>(base + gi);
+        v0 = __ldg(q);
+        v1 = __ldg(q + 1);
+        v2 = __ldg(q + 2);
+        v3 = __ldg(q + 3);
+      } else {
+        v0 = load16(base, gi, g.total);
+        v1 = load16(base, gi + 16, g.total);
+        v2 = load16(base, gi + 32, g.total);
+        v3 = load16(base, gi + 48, g.total);
+      }
+    }
+    uint32_t pb = __shfl_up_sync(0xffffffffu, v3.w >> 24, 1);
+    if (lane == 0) pb = carry_byte;
+    uint32_t TA, OA, TB, OB;
+    classify32(v0, v1, pb, p.mode, TA, OA);
+    classify32(v2, v3, v1.w >> 24, p.mode, TB, OB);
+    uint32_t pt = __shfl_up_sync(0xffffffffu, TB, 1);
+    if (lane == 0) pt = carry_T;
+    const uint32_t EA = run_ends(pt, TA, p.R);
+    const uint32_t EB = run_ends(TA, TB, p.R);
+    if (lb) {
+      *reinterpret_cast<uint2 *>(m.E + wa) = make_uint2(EA, EB);
+      *reinterpret_cast<uint2 *>(m.O + wa) = make_uint2(OA, OB);
+    } else if (la) {
+      m.E[wa] = EA;
+      m.O[wa] = OA;
+    }
+    carry_byte = __shfl_sync(0xffffffffu, v3.w >> 24, 31);
+    carry_T = __shfl_sync(0xffffffffu, TB, 31);
   }
   __syncthreads();
-  // Block summaries; each warp covers 32 consecutive blocks per pass.
-  const uint32_t NB = sh.NB;
-  for (uint32_t b0 = warp * 32; b0 < NB; b0 += nwarps * 32) {
-    const uint32_t b = b0 + lane;
-    uint32_t any = 0, cnt = 0;
-    if (b < NB) {
-      const uint32_t v0 = b * 8, v1 = min(v0 + 8, W);
-      for (uint32_t w = v0; w < v1; ++w) {
-        any |= E[w];
-        cnt += __popc(O[w]);
-      }
-      ocnt[b] = (uint16_t)cnt;
+
+  // Query tables.  Each thread owns a contiguous range of words.
+  const uint32_t tper = (W + nthreads - 1) / nthreads;
+  const uint32_t ta = min((uint32_t)tid * tper, W), tz = min(ta + tper, W);
+  // ocum: exclusive prefix of O popcounts.
+  uint32_t osum = 0, fnz = kNoWord;
+  for (uint32_t w = ta; w < tz; ++w) {
+    osum += __popc(m.O[w]);
+    if (fnz == kNoWord && m.E[w]) fnz = w;
+  }
+  uint32_t total;
+  uint32_t run = block_excl_scan(osum, m.bscratch, &total);
+  for (uint32_t w = ta; w < tz; ++w) {
+    m.ocum[w] = run;
+    run += __popc(m.O[w]);
+  }
+  if (tid == 0) m.ocum[W] = total;
+  // ne: next word with an E bit, from the right.
+  uint32_t nxt = block_suffix_min_excl(fnz, m.bscratch);
+  if (nxt > kNoWord) nxt = kNoWord;
+  for (uint32_t w = tz; w > ta;) {
+    --w;
+    if (m.E[w]) nxt = w;
+    m.ne[w] = (uint16_t)nxt;
+  }
+  __syncthreads();
+  // notw: two-pointer from each thread's first word (found by binary search).
+  if (p.T != 0 && ta < tz) {
+    const uint32_t T = p.T;
+    // smallest j >= ta with ocum[j+1] - ocum[ta] >= T
+    uint32_t lo2 = ta, hi2 = W;  // answer in [lo2, hi2]; W = none
+    while (lo2 < hi2) {
+      const uint32_t mid = (lo2 + hi2) >> 1;
+      if (m.ocum[mid + 1] - m.ocum[ta] >= T) hi2 = mid; else lo2 = mid + 1;
     }
-    const uint32_t bal = __ballot_sync(0xffffffffu, any != 0);
-    if (lane == 0) eany[b0 >> 5] = bal;
+    uint32_t j = lo2;
+    for (uint32_t w = ta; w < tz; ++w) {
+      if (j < w) j = w;
+      while (j < W && m.ocum[j + 1] - m.ocum[w] < T) ++j;
+      m.notw[w] = j < W ? (uint16_t)j : kNoWord;
+    }
   }
 }
 
@@ -646,7 +704,7 @@ map_kernel(Geom g, DevParams p, WsPtrs ws) {
   }
   __syncthreads();
   const MapSmem m = carve(smem_raw, sh.W, g.L);
-  seg_bitmaps(sh, g, p, m.E, m.O, m.eany, m.ocnt);
+  seg_bitmaps(sh, g, p, m);
   __syncthreads();
 
   const int64_t B = sh.B;
@@ -692,7 +750,6 @@ map_kernel(Geom g, DevParams p, WsPtrs ws) {
       const uint32_t base = w << 5;
       if (lo > base) v &= ~0u << (lo - base);
       if (hi - base < 32) v &= (1u << (hi - base)) - 1u;
-      m.erank[w - wlo] = (uint16_t)(o - first);
       while (v) {
         const uint32_t bpos = __ffs(v) - 1;
         v &= v - 1;
@@ -720,8 +777,7 @@ map_kernel(Geom g, DevParams p, WsPtrs ws) {
   // Lanes advance one scan region per iteration and take a new candidate
   // from a block-wide queue when theirs is done, so a warp's lanes stay busy
   // however many regions a chunk needs.
-  const Bits bits = bits_of(m);
-  const uint32_t tmask_lo = ~((1u << (lo & 31)) - 1u);
+  const Bits bits = bits_of(m, sh.W);
   const uint32_t skip_min = p.mn > p.R ? p.mn - p.R : 0u;
   const int lane = tid & 31;
   for (int j = tid; j < kImgHash; j += nthreads) m.ihash[j] = kEscape;
@@ -760,16 +816,15 @@ map_kernel(Geom g, DevParams p, WsPtrs ws) {
         if (y >= q_rel) {
           code = kTerminal | (y - ps_rel);
         } else {
-          const uint32_t e = y - 1;
-          const uint32_t w = e >> 5;
-          const uint32_t bit = 1u << (e & 31);
-          if (m.E[w] & bit) {
-            uint32_t below = m.E[w] & (bit - 1u);
-            if (w == wlo) below &= tmask_lo;
-            code = first + m.erank[w - wlo] + __popc(below);
-          } else {
-            code = kEscape;  // a forced cut inside the item: not a candidate
+          // Index of y among the candidates (sorted), if it is one.
+          uint32_t lo2 = 0, hi2 = nc;
+          while (lo2 < hi2) {
+            const uint32_t mid = (lo2 + hi2) >> 1;
+            if (m.cpos[mid] < y) lo2 = mid + 1; else hi2 = mid;
           }
+          code = (lo2 < nc && m.cpos[lo2] == y)
+                     ? lo2
+                     : kEscape;  // a forced cut inside the item: not a candidate
         }
         m.cnxt[k] = code;
         m.jmp[k] = (code & kTerminal) ? (uint16_t)k : (uint16_t)code;
@@ -1103,10 +1158,10 @@ repair_kernel(Geom g, DevParams p, WsPtrs ws) {
       __syncthreads();
       if (s_run) {
         const MapSmem m = carve(smem_raw, sh.W, g.L);
-        seg_bitmaps(sh, g, p, m.E, m.O, m.eany, m.ocnt);
+        seg_bitmaps(sh, g, p, m);
         __syncthreads();
         if (tid == 0) {
-          const Bits bits = bits_of(m);
+          const Bits bits = bits_of(m, sh.W);
           const int64_t B = sh.B;
           const uint32_t end_rel = (uint32_t)((int64_t)sh.n_f - B);
           const uint32_t q_rel = (uint32_t)((int64_t)sh.q_s - B);
@@ -1221,6 +1276,12 @@ bool params_ok(const seqcdc_params_t *p) {
   return true;
 }
 
+uint32_t max_words(uint32_t L, uint64_t mx) {
+  return (uint32_t)((L + mx + 64 + 31) / 32 + 2);
+}
+
+constexpr size_t kSmemBudget = 220 * 1024;
+
 uint32_t pick_segment(const seqcdc_params_t *p, const seqcdc_tuning_t *t) {
   uint32_t L = (t && t->segment_bytes) ? t->segment_bytes : 65536u;
   // An item must be at least max_size long so that its entries (natural cuts
@@ -1229,6 +1290,11 @@ uint32_t pick_segment(const seqcdc_params_t *p, const seqcdc_tuning_t *t) {
   L = (L + 1023u) & ~1023u;
   if (L < 4096u) L = 4096u;
   if (L > (1u << 20)) L = 1u << 20;
+  // Shrink until the block's shared memory fits (never below max_size).
+  const uint64_t mx = p ? p->max_size : 0;
+  while (L > 4096u && L - 1024u >= mx &&
+         map_smem_bytes(max_words(L, mx), L) > kSmemBudget)
+    L -= 1024u;
   return L;
 }
 
@@ -1236,10 +1302,6 @@ uint32_t pick_threads(const seqcdc_tuning_t *t) {
   uint32_t n = (t && t->block_threads) ? t->block_threads : 256u;
   if (n != 128u && n != 256u && n != 512u) n = 256u;
   return n;
-}
-
-uint32_t max_words(uint32_t L, uint64_t mx) {
-  return (uint32_t)((L + mx + 64 + 31) / 32 + 2);
 }
 
 Layout make_layout(const seqcdc_params_t *p, uint64_t total, uint64_t nfiles,
@@ -1327,7 +1389,7 @@ int run(const seqcdc_params_t *p, const uint8_t *d_data, uint64_t total,
   DevParams dp{p->mode, p->seq_length, p->skip_trigger, p->skip_size,
                (uint32_t)p->min_size, (uint32_t)p->max_size};
   const size_t smem = map_smem_bytes(max_words(L, p->max_size), L);
-  if (smem > 227 * 1024) return SEQCDC_ERANGE;
+  if (smem > kSmemBudget) return SEQCDC_ERANGE;
   static size_t configured = 0;
   if (smem > 48 * 1024 && smem > configured) {
     if (cudaFuncSetAttribute(map_kernel,

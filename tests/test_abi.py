@@ -52,7 +52,7 @@ def test_presets_match_oracle(seqcdc_lib):
     (0, 17, 50, 256, 4096, 16384),  # seq_length > 16
     (0, 5, 50, 256, 0, 16384),      # min 0
     (0, 5, 50, 256, 8192, 4096),    # max < min
-    (0, 5, 50, 256, 4096, 1 << 20), # max beyond the supported bound
+    (0, 5, 50, 256, 4096, 1 << 18), # max beyond the supported bound
 ])
 def test_validate_rejects(seqcdc_lib, bad):
     p = seqcdc_lib.Params(*bad)
