@@ -365,7 +365,7 @@ def run_gpu(args):
     traffic = None
     if rec is not None:
         traffic = float(rec["dram_bytes_per_byte"]) * total
-    launches_per_step = 7
+    launches_per_step = 8  # plan_tiles, plan_scan, map, resolve, verify, repair, count_tiles, emit
     if rank != 0:
         return
     line = {

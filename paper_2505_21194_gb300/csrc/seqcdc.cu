@@ -189,19 +189,15 @@ __device__ uint32_t wait_any(const uint32_t *flag, uint32_t mask, WsHeader *hdr)
   return 0;
 }
 
-// Position (0..31) of the k-th set bit (1 <= k <= popc(x)).
+// Position (0..31) of the k-th set bit (1 <= k <= popc(x)); a branch-free
+// binary descent over halves, quarters, ... of the word.
 __device__ __forceinline__ uint32_t nth_set_bit(uint32_t x, uint32_t k) {
-  uint32_t pos = 0;
-  uint32_t c = __popc(x & 0xffffu);
-  if (k > c) { k -= c; x >>= 16; pos += 16; }
-  c = __popc(x & 0xffu);
-  if (k > c) { k -= c; x >>= 8; pos += 8; }
-  c = __popc(x & 0xfu);
-  if (k > c) { k -= c; x >>= 4; pos += 4; }
-  c = __popc(x & 0x3u);
-  if (k > c) { k -= c; x >>= 2; pos += 2; }
-  c = x & 1u;
-  if (k > c) { pos += 1; }
+  uint32_t pos = 0, c, t;
+  c = __popc(x & 0xffffu); t = k > c; k -= t ? c : 0u; x >>= t ? 16 : 0; pos += t ? 16 : 0;
+  c = __popc(x & 0xffu);   t = k > c; k -= t ? c : 0u; x >>= t ? 8 : 0;  pos += t ? 8 : 0;
+  c = __popc(x & 0xfu);    t = k > c; k -= t ? c : 0u; x >>= t ? 4 : 0;  pos += t ? 4 : 0;
+  c = __popc(x & 0x3u);    t = k > c; k -= t ? c : 0u; x >>= t ? 2 : 0;  pos += t ? 2 : 0;
+  c = x & 1u;              t = k > c;                                    pos += t ? 1 : 0;
   return pos;
 }
 
@@ -410,6 +406,7 @@ struct MapSmem {
   uint32_t *cpos;    // cap: candidate positions (rel)
   uint32_t *cnxt;    // cap: next candidate index or terminal code
   uint16_t *jmp, *jtmp;  // cap: pointer doubling
+  uint16_t *erank;   // L/32 + 4: natural cuts before each word of the candidate range
   uint32_t *ihash;   // kImgHash: distinct exits
   uint32_t *bscratch;  // 64: block helpers
 };
@@ -429,13 +426,15 @@ __device__ __forceinline__ MapSmem carve(unsigned char *raw, uint32_t W, uint32_
   m.notw = m.ne + W;
   m.jmp = m.notw + W;
   m.jtmp = m.jmp + cap;
+  m.erank = m.jtmp + cap;
   return m;
 }
 
 __host__ __device__ inline size_t map_smem_bytes(uint32_t W, uint32_t L) {
   const uint32_t cap = cand_cap(L);
   // E, O (even stride), ocum (W + 1), ne, notw: at most 16 bytes per word + 8.
-  return (size_t)(W + 1) * 16 + 8 + (size_t)cap * 12 + kImgHash * 4 + 64 * 4 + 16;
+  return (size_t)(W + 1) * 16 + 8 + (size_t)cap * 12 + (L / 32 + 4) * 2 +
+         kImgHash * 4 + 64 * 4 + 16;
 }
 
 __device__ __forceinline__ uint32_t find_file(const uint32_t *seg_base,
@@ -496,22 +495,26 @@ __device__ __forceinline__ Bits bits_of(const MapSmem &m, uint32_t W) {
   return Bits{m.E, m.O, m.ne, m.ocum, m.notw, W};
 }
 
-// Target / opposing bits of one 4-byte word x given y, the same word shifted
-// by one byte (y's byte k is the byte before x's byte k).  Both per-byte
-// unsigned compares come from one borrow-free subtraction: with
+// Per-byte unsigned compares of a 4-byte word x with y, the same word shifted
+// by one byte (y's byte k is the byte before x's byte k), answers in bit 7 of
+// each byte.  Both come from one borrow-free subtraction: with
 // z1 = (x | 0x80) - (y & 0x7f) - 1 per byte (0..0xfe), bit 7 of z1 is
 // [x_low7 > y_low7] and z2 = 0xfe - z1 = (y | 0x80) - (x & 0x7f) - 1 gives
-// [y_low7 > x_low7]; where the top bits differ they decide.  The bit-7 masks
-// are gathered into nibbles by one multiplication each and accumulated at
-// nibble `k` of up / dn.
-__device__ __forceinline__ void classify_word(uint32_t x, uint32_t y, uint32_t k,
-                                              uint32_t &up, uint32_t &dn) {
+// [y_low7 > x_low7]; where the top bits differ they decide.
+__device__ __forceinline__ void cmp_word(uint32_t x, uint32_t y, uint32_t &gt,
+                                         uint32_t &lt) {
   const uint32_t z1 = (x | 0x80808080u) - (y & 0x7f7f7f7fu) - 0x01010101u;
   const uint32_t z2 = 0xfefefefeu - z1;
-  const uint32_t gt = (x & ~y) | (~(x ^ y) & z1);   // x > y per byte (bit 7)
-  const uint32_t lt = (y & ~x) | (~(x ^ y) & z2);   // x < y per byte (bit 7)
-  up += (((gt & 0x80808080u) * 0x00204081u) >> 28) << (4 * k);
-  dn += (((lt & 0x80808080u) * 0x00204081u) >> 28) << (4 * k);
+  gt = ((x & ~y) | (~(x ^ y) & z1)) & 0x80808080u;   // x > y per byte
+  lt = ((y & ~x) | (~(x ^ y) & z2)) & 0x80808080u;   // x < y per byte
+}
+
+// Bit 7 of the 8 bytes of two words (a = bytes 0..3, b = bytes 4..7) -> bits
+// 0..7 in byte order.  With a's bits moved to 3, 11, 19, 27 and b's at 7, 15,
+// 23, 31, one multiplication by 1 + 2^7 + 2^14 + 2^21 lands them at 24..31 in
+// order; the other partial products stay below bit 24 without overlapping.
+__device__ __forceinline__ uint32_t gather8(uint32_t a, uint32_t b) {
+  return (((a >> 4) | b) * 0x00204081u) >> 24;
 }
 
 // 32 bytes (two 16-byte vectors) with the byte before them -> T and O bits
@@ -519,15 +522,19 @@ __device__ __forceinline__ void classify_word(uint32_t x, uint32_t y, uint32_t k
 __device__ __forceinline__ void classify32(uint4 v0, uint4 v1, uint32_t prev_byte,
                                            uint32_t mode, uint32_t &T,
                                            uint32_t &Ow) {
-  uint32_t up = 0, dn = 0;
-  classify_word(v0.x, (v0.x << 8) | (prev_byte & 0xffu), 0, up, dn);
-  classify_word(v0.y, __funnelshift_l(v0.x, v0.y, 8), 1, up, dn);
-  classify_word(v0.z, __funnelshift_l(v0.y, v0.z, 8), 2, up, dn);
-  classify_word(v0.w, __funnelshift_l(v0.z, v0.w, 8), 3, up, dn);
-  classify_word(v1.x, __funnelshift_l(v0.w, v1.x, 8), 4, up, dn);
-  classify_word(v1.y, __funnelshift_l(v1.x, v1.y, 8), 5, up, dn);
-  classify_word(v1.z, __funnelshift_l(v1.y, v1.z, 8), 6, up, dn);
-  classify_word(v1.w, __funnelshift_l(v1.z, v1.w, 8), 7, up, dn);
+  uint32_t g0, l0, g1, l1, g2, l2, g3, l3, g4, l4, g5, l5, g6, l6, g7, l7;
+  cmp_word(v0.x, (v0.x << 8) | (prev_byte & 0xffu), g0, l0);
+  cmp_word(v0.y, __funnelshift_l(v0.x, v0.y, 8), g1, l1);
+  cmp_word(v0.z, __funnelshift_l(v0.y, v0.z, 8), g2, l2);
+  cmp_word(v0.w, __funnelshift_l(v0.z, v0.w, 8), g3, l3);
+  cmp_word(v1.x, __funnelshift_l(v0.w, v1.x, 8), g4, l4);
+  cmp_word(v1.y, __funnelshift_l(v1.x, v1.y, 8), g5, l5);
+  cmp_word(v1.z, __funnelshift_l(v1.y, v1.z, 8), g6, l6);
+  cmp_word(v1.w, __funnelshift_l(v1.z, v1.w, 8), g7, l7);
+  const uint32_t up = gather8(g0, g1) | (gather8(g2, g3) << 8) |
+                      (gather8(g4, g5) << 16) | (gather8(g6, g7) << 24);
+  const uint32_t dn = gather8(l0, l1) | (gather8(l2, l3) << 8) |
+                      (gather8(l4, l5) << 16) | (gather8(l6, l7) << 24);
   T = mode == 0 ? up : dn;
   Ow = mode == 0 ? dn : up;
 }
@@ -588,12 +595,9 @@ __device__ void seg_bitmaps(const SegShared &sh, const Geom &g,
     // T bits of the 16 positions before this warp's first word (only the top
     // SeqLength-2 of them matter, so the unknown byte before them is moot).
     const uint4 pv = load16(base, gwin + 32 * (int64_t)w0 - 16, g.total);
-    uint32_t up = 0, dn = 0;
-    classify_word(pv.x, pv.x << 8, 0, up, dn);
-    classify_word(pv.y, __funnelshift_l(pv.x, pv.y, 8), 1, up, dn);
-    classify_word(pv.z, __funnelshift_l(pv.y, pv.z, 8), 2, up, dn);
-    classify_word(pv.w, __funnelshift_l(pv.z, pv.w, 8), 3, up, dn);
-    carry_T = (p.mode == 0 ? up : dn) << 16;
+    uint32_t Tp, Op;
+    classify32(make_uint4(0, 0, 0, 0), pv, 0, p.mode, Tp, Op);
+    carry_T = Tp;  // the top 16 bits are the 16 positions before this word
     carry_byte = pv.w >> 24;
   }
   for (uint32_t wb = w0; wb < w1; wb += 64) {
@@ -750,6 +754,7 @@ map_kernel(Geom g, DevParams p, WsPtrs ws) {
       const uint32_t base = w << 5;
       if (lo > base) v &= ~0u << (lo - base);
       if (hi - base < 32) v &= (1u << (hi - base)) - 1u;
+      m.erank[w - wlo] = (uint16_t)(o - first);
       while (v) {
         const uint32_t bpos = __ffs(v) - 1;
         v &= v - 1;
@@ -778,6 +783,7 @@ map_kernel(Geom g, DevParams p, WsPtrs ws) {
   // from a block-wide queue when theirs is done, so a warp's lanes stay busy
   // however many regions a chunk needs.
   const Bits bits = bits_of(m, sh.W);
+  const uint32_t tmask_lo = ~((1u << (lo & 31)) - 1u);
   const uint32_t skip_min = p.mn > p.R ? p.mn - p.R : 0u;
   const int lane = tid & 31;
   for (int j = tid; j < kImgHash; j += nthreads) m.ihash[j] = kEscape;
@@ -816,15 +822,18 @@ map_kernel(Geom g, DevParams p, WsPtrs ws) {
         if (y >= q_rel) {
           code = kTerminal | (y - ps_rel);
         } else {
-          // Index of y among the candidates (sorted), if it is one.
-          uint32_t lo2 = 0, hi2 = nc;
-          while (lo2 < hi2) {
-            const uint32_t mid = (lo2 + hi2) >> 1;
-            if (m.cpos[mid] < y) lo2 = mid + 1; else hi2 = mid;
+          // Index of y among the candidates: its rank among the run ends of
+          // the candidate range, if y - 1 is one.
+          const uint32_t e = y - 1;
+          const uint32_t w = e >> 5;
+          const uint32_t bit = 1u << (e & 31);
+          if (e >= lo && (m.E[w] & bit)) {
+            uint32_t below = m.E[w] & (bit - 1u);
+            if (w == wlo) below &= tmask_lo;
+            code = first + m.erank[w - wlo] + __popc(below);
+          } else {
+            code = kEscape;  // a forced cut inside the item: not a candidate
           }
-          code = (lo2 < nc && m.cpos[lo2] == y)
-                     ? lo2
-                     : kEscape;  // a forced cut inside the item: not a candidate
         }
         m.cnxt[k] = code;
         m.jmp[k] = (code & kTerminal) ? (uint16_t)k : (uint16_t)code;
