@@ -212,6 +212,7 @@ def run_gpu(args):
     nfiles = offs_np.size - 1
     p = seqcdc.seqcdc_params(KIB, MODE)
     tuning = seqcdc.Tuning(args.segment_bytes, args.threads)
+    eff = seqcdc.seqcdc_resolve_tuning(p, tuning)
     cap = total // p.min_size + nfiles
     ws_bytes = seqcdc.seqcdc_workspace_size(p, total, nfiles, tuning)
 
@@ -386,8 +387,8 @@ def run_gpu(args):
                         "4 KiB..64 MiB), half random / half Markov text, CSR; "
                         "8 KiB setting, increasing mode" % nfiles,
             "total_bytes": total, "nfiles": nfiles, "cuts": ncuts,
-            "segment_bytes": args.segment_bytes or 65536,
-            "block_threads": args.threads or 256,
+            "segment_bytes": eff.segment_bytes,
+            "block_threads": eff.block_threads,
             "l2": "inputs (%.1f GiB) far larger than L2; no flush" % (total / 2**30),
             "parallelism": "1 GPU per rank, independent batches (weak scaling)",
         },

@@ -80,12 +80,23 @@ typedef struct {
  *                  lowered if the block's shared memory would not fit).
  *                  Larger segments mean fewer junctions but more shared
  *                  memory per block.
- *   block_threads  threads per block of the segment kernel (128, 256, 512).
+ *   block_threads  threads per block of the segment kernel (128, 256, 512;
+ *                  any other value means the default).
  */
 typedef struct {
     uint32_t segment_bytes;
     uint32_t block_threads;
 } seqcdc_tuning_t;
+
+/*
+ * Fill *out with the segment size and block size that a chunking call with
+ * these parameters and this tuning (NULL or zero fields: library defaults)
+ * runs with.  The defaults are 512 threads and the largest of 128, 96 and
+ * 64 KiB segments for which two blocks share an SM.  Returns SEQCDC_EINVAL
+ * for an invalid parameter set or a NULL out.
+ */
+int seqcdc_resolve_tuning(const seqcdc_params_t *p, const seqcdc_tuning_t *tuning,
+                          seqcdc_tuning_t *out);
 
 /*
  * Fill *out with the paper's parameters for an expected average chunk size

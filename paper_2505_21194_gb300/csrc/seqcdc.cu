@@ -247,77 +247,98 @@ __device__ uint32_t block_excl_scan(uint32_t v, uint32_t *scratch,
 // Bitmaps of one item in shared memory.  Positions are relative to the window
 // base B (file-relative): rel = pos - B; word w covers rel 32w .. 32w+31.
 //   E, O   run-end and opposing-pair bits
-//   ne     ne[w]: first word >= w holding an E bit (kNoWord if none)
 //   ocum   ocum[w]: O bits in words < w (ocum[W] = all)
-//   notw   notw[w]: the word holding the T-th O bit counted from the start of
-//          word w (kNoWord if the window has fewer)
+//   erank  erank[w]: E bits in words < w (erank[W] = all)
+//   nz     bit w of the mask: E[w] != 0
+//   sel    sel[j]: the word holding O bit number 32 j (bits numbered from 1
+//          in window order); sel[0] = 0
 // With these a scan-region query (Sec. III.D: first set bit of the combined
 // run mask; position of the SkipTrigger-th opposing pair) is a few lookups.
 // ---------------------------------------------------------------------------
-constexpr uint16_t kNoWord = 0xFFFFu;
-
 struct Bits {
   const uint32_t *E;
   const uint32_t *O;
-  const uint16_t *ne;
   const uint32_t *ocum;
-  const uint16_t *notw;
+  const uint32_t *nz;
+  const uint16_t *sel;
   uint32_t W;
+  uint32_t otot;  // O bits in the window
 };
 
-// First E position in [x, limit), or kNone.
-__device__ __forceinline__ uint32_t first_E(const Bits &b, uint32_t x,
-                                            uint32_t limit) {
-  if (x >= limit) return kNone;
-  uint32_t w = x >> 5;
-  uint32_t m = b.E[w] & (~0u << (x & 31));
-  if (!m) {
-    if (w + 1 >= b.W) return kNone;
-    w = b.ne[w + 1];
-    if (w == kNoWord) return kNone;
-    m = b.E[w];
+// One scan region of the chunker (Sec. III.A-C) from scan position i with
+// chunk limit lim: returns the cut (run end + 1 when a run completes before
+// the SkipTrigger-th opposing pair; lim when the chunk reaches its maximum
+// size or the input end), or kNone after moving i past a content-defined skip.
+// The run end and the opposing pair are looked up independently, and every
+// index is clamped into the window, so lanes without work (lim = 0, result
+// lim) run the same instructions; the only loops are the short walks to the
+// wanted O bit and to the next word holding an E bit.
+__device__ __forceinline__ uint32_t region_step(const Bits &b, const DevParams &p,
+                                                uint32_t &i, uint32_t lim) {
+  const uint32_t Wm1 = b.W - 1;
+  const bool open = i + 1 < lim;
+  // sp: the SkipTrigger-th O bit at or after i + 1, if below lim.
+  uint32_t sp = kNone;
+  if (p.T) {
+    const uint32_t x = i + 1;
+    const uint32_t w0 = min(x >> 5, Wm1);
+    // number (from 1, window order) of the wanted O bit
+    const uint32_t t = b.ocum[w0] + __popc(b.O[w0] & ((1u << (x & 31)) - 1u)) + p.T;
+    const bool ok = open && t <= b.otot;
+    // its word is at or after w0 and at or after the word of bit 32 (t / 32)
+    uint32_t w = min(max(w0, (uint32_t)b.sel[min(t >> 5, b.W)]), Wm1);
+    uint32_t cnt = b.ocum[w], m = b.O[w], c = __popc(m);
+    while (ok && cnt + c < t && ((w + 1) << 5) < lim) {
+      cnt += c;
+      ++w;
+      m = b.O[w];
+      c = __popc(m);
+    }
+    if (ok && cnt + c >= t) {
+      const uint32_t pos = (w << 5) + nth_set_bit(m, t - cnt);
+      if (pos < lim) sp = pos;
+    }
   }
-  const uint32_t pos = (w << 5) + (__ffs(m) - 1);
-  return pos < limit ? pos : kNone;
-}
-
-// Position of the need-th O bit at or after x (need >= 1), if < limit; else
-// kNone.  `need` is SkipTrigger, for which notw was built.
-__device__ __forceinline__ uint32_t nth_O(const Bits &b, uint32_t x,
-                                          uint32_t need, uint32_t limit) {
-  if (x >= limit) return kNone;
-  const uint32_t w0 = x >> 5;
-  // The need-th O bit at or after x is the k-th counted from word w0's start.
-  const uint32_t k = need + __popc(b.O[w0] & ((1u << (x & 31)) - 1u));
-  uint32_t w = b.notw[w0];  // word of the need-th from w0's start; k-th is at or after
-  if (w == kNoWord) return kNone;
-  uint32_t cnt = b.ocum[w] - b.ocum[w0];
-  uint32_t m = b.O[w];
-  uint32_t c = __popc(m);
-  while (cnt + c < k) {
-    cnt += c;
-    if (++w >= b.W || (w << 5) >= limit) return kNone;
-    m = b.O[w];
-    c = __popc(m);
+  // e: the first E bit at or after i + SeqLength - 1, if below lim.
+  uint32_t e = kNone;
+  {
+    const uint32_t x = i + p.R - 1;
+    uint32_t w = min(x >> 5, Wm1);
+    uint32_t m = b.E[w] & (~0u << (x & 31));
+    if (!m && open) {
+      const uint32_t w1 = w + 1;
+      if ((w1 << 5) < lim) {
+        uint32_t q = w1 >> 5;
+        uint32_t z = b.nz[q] & (~0u << (w1 & 31));
+        while (!z && ((q + 1) << 10) < lim) z = b.nz[++q];
+        if (z) {
+          w = (q << 5) + (__ffs(z) - 1);
+          m = b.E[w];
+        }
+      }
+    }
+    if (m && x < lim) {
+      const uint32_t pos = (w << 5) + (__ffs(m) - 1);
+      if (pos < lim) e = pos;
+    }
   }
-  const uint32_t pos = (w << 5) + nth_set_bit(m, k - cnt);
-  return pos < limit ? pos : kNone;
+  if (!open) return lim;              // maximum size or end of input (Sec. IV)
+  if (e < sp) return e + 1;           // boundary run ends first (Sec. III.A)
+  if (sp == kNone) return lim;
+  i = sp + 1 + p.S;                   // content-defined skip (Sec. III.C)
+  return kNone;
 }
 
 // One chunk: from chunk start c (rel) return its end (rel).  `end_rel` is the
 // rel position of the file end.
 __device__ uint32_t chunk_step(const Bits &b, const DevParams &p, uint32_t c,
                                uint32_t end_rel) {
-  const uint32_t limit = (end_rel - c > p.mx) ? c + p.mx : end_rel;
+  const uint32_t lim = (end_rel - c > p.mx) ? c + p.mx : end_rel;
   uint32_t i = c + (p.mn > p.R ? p.mn - p.R : 0u);
-  while (i + 1 < limit) {
-    const uint32_t s = p.T ? nth_O(b, i + 1, p.T, limit) : kNone;
-    const uint32_t e = first_E(b, i + p.R - 1, s == kNone ? limit : s);
-    if (e != kNone) return e + 1;     // boundary run ends first (Sec. III.A)
-    if (s == kNone) break;
-    i = s + 1 + p.S;                  // content-defined skip (Sec. III.C)
+  while (true) {
+    const uint32_t y = region_step(b, p, i, lim);
+    if (y != kNone) return y;
   }
-  return limit;                       // max size or end of input (Sec. IV)
 }
 
 
@@ -401,40 +422,42 @@ struct SegShared {
 struct MapSmem {
   uint32_t *E, *O;
   uint32_t *ocum;    // W + 1
-  uint16_t *ne;      // W
-  uint16_t *notw;    // W
+  uint32_t *erank;   // W + 1
+  uint32_t *nz;      // nz_words(W)
+  uint16_t *sel;     // W + 2
   uint32_t *cpos;    // cap: candidate positions (rel)
   uint32_t *cnxt;    // cap: next candidate index or terminal code
   uint16_t *jmp, *jtmp;  // cap: pointer doubling
-  uint16_t *erank;   // L/32 + 4: natural cuts before each word of the candidate range
   uint32_t *ihash;   // kImgHash: distinct exits
   uint32_t *bscratch;  // 64: block helpers
 };
 
+// Words of the nonzero-E mask: one bit per bitmap word, whole 64-word steps.
+__host__ __device__ inline uint32_t nz_words(uint32_t W) { return ((W + 63) >> 6) * 2 + 2; }
+
 __device__ __forceinline__ MapSmem carve(unsigned char *raw, uint32_t W, uint32_t L) {
   const uint32_t cap = cand_cap(L);
-  const uint32_t Wp = (W + 1) & ~1u;  // even stride: E and O take 8-byte stores
   MapSmem m;
   m.E = reinterpret_cast<uint32_t *>(raw);
-  m.O = m.E + Wp;
-  m.ocum = m.O + Wp;
-  m.cpos = m.ocum + W + 1;
+  m.O = m.E + W + 1;
+  m.ocum = m.O + W + 1;
+  m.erank = m.ocum + W + 1;
+  m.nz = m.erank + W + 1;
+  m.cpos = m.nz + nz_words(W);
   m.cnxt = m.cpos + cap;
   m.ihash = m.cnxt + cap;
   m.bscratch = m.ihash + kImgHash;
-  m.ne = reinterpret_cast<uint16_t *>(m.bscratch + 64);
-  m.notw = m.ne + W;
-  m.jmp = m.notw + W;
+  m.sel = reinterpret_cast<uint16_t *>(m.bscratch + 64);
+  m.jmp = m.sel + W + 2;
   m.jtmp = m.jmp + cap;
-  m.erank = m.jtmp + cap;
   return m;
 }
 
 __host__ __device__ inline size_t map_smem_bytes(uint32_t W, uint32_t L) {
   const uint32_t cap = cand_cap(L);
-  // E, O (even stride), ocum (W + 1), ne, notw: at most 16 bytes per word + 8.
-  return (size_t)(W + 1) * 16 + 8 + (size_t)cap * 12 + (L / 32 + 4) * 2 +
-         kImgHash * 4 + 64 * 4 + 16;
+  return (size_t)4 * (4 * (size_t)(W + 1) + nz_words(W) + 2 * (size_t)cap +
+                      kImgHash + 64) +
+         (size_t)2 * ((W + 2) + 2 * (size_t)cap) + 16;
 }
 
 __device__ __forceinline__ uint32_t find_file(const uint32_t *seg_base,
@@ -492,7 +515,7 @@ __device__ void seg_setup(SegShared &sh, const Geom &g, const DevParams &p,
 }
 
 __device__ __forceinline__ Bits bits_of(const MapSmem &m, uint32_t W) {
-  return Bits{m.E, m.O, m.ne, m.ocum, m.notw, W};
+  return Bits{m.E, m.O, m.ocum, m.nz, m.sel, W, m.ocum[W]};
 }
 
 // Per-byte unsigned compares of a 4-byte word x with y, the same word shifted
@@ -547,40 +570,42 @@ __device__ __forceinline__ uint32_t run_ends(uint32_t pt, uint32_t T, uint32_t R
   return ew;
 }
 
-// Inclusive suffix minimum over the block's threads (value per thread).
-__device__ uint32_t block_suffix_min_excl(uint32_t v, uint32_t *scratch) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int nwarps = blockDim.x >> 5;
-  uint32_t x = v;  // inclusive suffix min within the warp
-  for (int d = 1; d < 32; d <<= 1) {
-    const uint32_t y = __shfl_down_sync(0xffffffffu, x, d);
-    if (lane + d < 32) x = min(x, y);
-  }
-  if (lane == 0) scratch[warp] = x;
-  __syncthreads();
-  if (warp == 0) {
-    uint32_t t = lane < nwarps ? scratch[lane] : 0xffffffffu;
-    for (int d = 1; d < 32; d <<= 1) {
-      const uint32_t y = __shfl_down_sync(0xffffffffu, t, d);
-      if (lane + d < 32) t = min(t, y);
-    }
-    if (lane < nwarps) scratch[32 + lane] = t;  // suffix min of warps >= lane
-  }
-  __syncthreads();
-  // exclusive: min over threads after this one
-  uint32_t after = __shfl_down_sync(0xffffffffu, x, 1);
-  if (lane == 31) after = 0xffffffffu;
-  const uint32_t later = (warp + 1 < nwarps) ? scratch[32 + warp + 1] : 0xffffffffu;
-  const uint32_t r = min(after, later);
-  __syncthreads();
-  return r;
+// The natural cuts an item tabulates: run ends e in [lo, hi) give cut e + 1
+// at index first + (rank of e among the E bits from lo on); those with e < eh
+// are entries.  With want == false nothing is tabulated (repair pass).
+struct CandRange {
+  uint32_t lo, hi, eh, first, cap, ps_rel;
+  bool want;
+};
+
+struct CandCount {
+  uint32_t nc_nat;    // natural cuts in the range
+  uint32_t nent_nat;  // of which entries
+  uint32_t elo;       // E bits before lo
+};
+
+// E bits before rel position x (x <= 32 W) while erank holds warp-local
+// counts: lane k of xE holds the base of warp k, whose words are
+// [k per, (k + 1) per).  Called by all lanes of a warp.
+__device__ __forceinline__ uint32_t erank_local(const MapSmem &m, uint32_t W,
+                                                uint32_t per, uint32_t xE,
+                                                uint32_t totE, uint32_t x) {
+  const uint32_t w = x >> 5;
+  const uint32_t bk = __shfl_sync(0xffffffffu, xE, min(w, W - 1) / per);
+  if (w >= W) return totE;
+  return m.erank[w] + bk + __popc(m.E[w] & ((1u << (x & 31)) - 1u));
 }
 
-// E and O bitmaps of the window [B, B + 32 W) and their query tables.  Each
-// warp covers a contiguous run of words; a lane takes 64 bytes (two words)
-// per step with four 16-byte loads in flight.
-__device__ void seg_bitmaps(const SegShared &sh, const Geom &g,
-                            const DevParams &p, const MapSmem &m) {
+// E and O bitmaps of the window [B, B + 32 W), their query tables and the
+// item's natural cuts.  Warp k covers the words [k per, (k + 1) per); per
+// step, lane j takes words wb + j and wb + 32 + j (32 bytes each), so a
+// ballot gives the nonzero-E mask in word order and one warp scan per half
+// gives running O and E counts.  After one barrier every warp adds its base
+// to its counts and scatters the select table and the candidate positions.
+__device__ __forceinline__ CandCount seg_bitmaps(const SegShared &sh, const Geom &g,
+                                 const DevParams &p, const MapSmem &m,
+                                 const CandRange &cr) {
+  constexpr uint32_t kAll = 0xffffffffu;
   const int tid = threadIdx.x, nthreads = blockDim.x;
   const uint32_t W = sh.W;
   const uint8_t *base = g.data;
@@ -588,7 +613,7 @@ __device__ void seg_bitmaps(const SegShared &sh, const Geom &g,
   const int lane = tid & 31, warp = tid >> 5, nwarps = nthreads >> 5;
   uint32_t per = (W + nwarps - 1) / nwarps;
   per = (per + 63) & ~63u;
-  const uint32_t w0 = warp * per;
+  const uint32_t w0 = min(warp * per, W);
   const uint32_t w1 = min(w0 + per, W);
   uint32_t carry_byte = 0, carry_T = 0;
   if (w0 < w1 && w0 > 0) {
@@ -600,87 +625,133 @@ __device__ void seg_bitmaps(const SegShared &sh, const Geom &g,
     carry_T = Tp;  // the top 16 bits are the 16 positions before this word
     carry_byte = pv.w >> 24;
   }
+  uint32_t cO = 0, cE = 0;  // O and E bits so far in this warp's words
   for (uint32_t wb = w0; wb < w1; wb += 64) {
-    const uint32_t wa = wb + 2 * lane;          // this lane's words wa, wa+1
-    const bool la = wa < w1, lb = wa + 1 < w1;
-    const int64_t gi = gwin + 32 * (int64_t)wa;
-    uint4 v0 = make_uint4(0, 0, 0, 0), v1 = v0, v2 = v0, v3 = v0;
-    if (la) {
-      if (gi >= 0 && (uint64_t)gi + 64 <= g.total) {
-        const uint4 *q = reinterpret_cast<const uint4 *>(base + gi);
-        v0 = __ldg(q);
-        v1 = __ldg(q + 1);
-        v2 = __ldg(q + 2);
-        v3 = __ldg(q + 3);
-      } else {
-        v0 = load16(base, gi, g.total);
-        v1 = load16(base, gi + 16, g.total);
-        v2 = load16(base, gi + 32, g.total);
-        v3 = load16(base, gi + 48, g.total);
-      }
+    const uint32_t wa = wb + lane, wc = wa + 32;
+    const bool la = wa < w1, lc = wc < w1;
+    const int64_t gs = gwin + 32 * (int64_t)wb;
+    uint4 a0, a1, c0, c1;
+    if (gs >= 0 && (uint64_t)gs + 2048 <= g.total) {
+      const uint4 *q = reinterpret_cast<const uint4 *>(base + gs) + 2 * lane;
+      a0 = __ldg(q);
+      a1 = __ldg(q + 1);
+      c0 = __ldg(q + 64);
+      c1 = __ldg(q + 65);
+    } else {
+      const int64_t ga = gs + 32 * lane, gc = ga + 1024;
+      a0 = load16(base, ga, g.total);
+      a1 = load16(base, ga + 16, g.total);
+      c0 = load16(base, gc, g.total);
+      c1 = load16(base, gc + 16, g.total);
     }
-    uint32_t pb = __shfl_up_sync(0xffffffffu, v3.w >> 24, 1);
-    if (lane == 0) pb = carry_byte;
-    uint32_t TA, OA, TB, OB;
-    classify32(v0, v1, pb, p.mode, TA, OA);
-    classify32(v2, v3, v1.w >> 24, p.mode, TB, OB);
-    uint32_t pt = __shfl_up_sync(0xffffffffu, TB, 1);
-    if (lane == 0) pt = carry_T;
-    const uint32_t EA = run_ends(pt, TA, p.R);
-    const uint32_t EB = run_ends(TA, TB, p.R);
-    if (lb) {
-      *reinterpret_cast<uint2 *>(m.E + wa) = make_uint2(EA, EB);
-      *reinterpret_cast<uint2 *>(m.O + wa) = make_uint2(OA, OB);
-    } else if (la) {
-      m.E[wa] = EA;
-      m.O[wa] = OA;
+    const uint32_t lastA = a1.w >> 24, lastC = c1.w >> 24;
+    uint32_t pbA = __shfl_up_sync(kAll, lastA, 1);
+    uint32_t pbC = __shfl_up_sync(kAll, lastC, 1);
+    const uint32_t lastA31 = __shfl_sync(kAll, lastA, 31);
+    if (lane == 0) {
+      pbA = carry_byte;
+      pbC = lastA31;
     }
-    carry_byte = __shfl_sync(0xffffffffu, v3.w >> 24, 31);
-    carry_T = __shfl_sync(0xffffffffu, TB, 31);
+    uint32_t TA, OA, TC, OC;
+    classify32(a0, a1, pbA, p.mode, TA, OA);
+    classify32(c0, c1, pbC, p.mode, TC, OC);
+    uint32_t ptA = __shfl_up_sync(kAll, TA, 1);
+    uint32_t ptC = __shfl_up_sync(kAll, TC, 1);
+    const uint32_t TA31 = __shfl_sync(kAll, TA, 31);
+    if (lane == 0) {
+      ptA = carry_T;
+      ptC = TA31;
+    }
+    uint32_t EA = run_ends(ptA, TA, p.R), EC = run_ends(ptC, TC, p.R);
+    if (!la) { EA = 0; OA = 0; }
+    if (!lc) { EC = 0; OC = 0; }
+    carry_byte = __shfl_sync(kAll, lastC, 31);
+    carry_T = __shfl_sync(kAll, TC, 31);
+    if (la) { m.E[wa] = EA; m.O[wa] = OA; }
+    if (lc) { m.E[wc] = EC; m.O[wc] = OC; }
+    const uint32_t nzA = __ballot_sync(kAll, EA != 0);
+    const uint32_t nzC = __ballot_sync(kAll, EC != 0);
+    if (lane == 0) {
+      m.nz[wb >> 5] = nzA;
+      m.nz[(wb >> 5) + 1] = nzC;
+    }
+    // Running counts, O in the low half and E in the high half (a step adds
+    // at most 1024 to each).
+    const uint32_t xA = __popc(OA) | (__popc(EA) << 16);
+    const uint32_t xC = __popc(OC) | (__popc(EC) << 16);
+    uint32_t sA = xA, sC = xC;
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint32_t yA = __shfl_up_sync(kAll, sA, d);
+      const uint32_t yC = __shfl_up_sync(kAll, sC, d);
+      if (lane >= d) { sA += yA; sC += yC; }
+    }
+    const uint32_t tA = __shfl_sync(kAll, sA, 31), tC = __shfl_sync(kAll, sC, 31);
+    const uint32_t eA = sA - xA, eC = sC - xC + tA;
+    if (la) { m.ocum[wa] = cO + (eA & 0xffffu); m.erank[wa] = cE + (eA >> 16); }
+    if (lc) { m.ocum[wc] = cO + (eC & 0xffffu); m.erank[wc] = cE + (eC >> 16); }
+    const uint32_t tt = tA + tC;
+    cO += tt & 0xffffu;
+    cE += tt >> 16;
+  }
+  if (lane == 0) {
+    m.bscratch[warp] = cO;
+    m.bscratch[32 + warp] = cE;
   }
   __syncthreads();
 
-  // Query tables.  Each thread owns a contiguous range of words.
-  const uint32_t tper = (W + nthreads - 1) / nthreads;
-  const uint32_t ta = min((uint32_t)tid * tper, W), tz = min(ta + tper, W);
-  // ocum: exclusive prefix of O popcounts.
-  uint32_t osum = 0, fnz = kNoWord;
-  for (uint32_t w = ta; w < tz; ++w) {
-    osum += __popc(m.O[w]);
-    if (fnz == kNoWord && m.E[w]) fnz = w;
+  // Warp bases (exclusive scans over the warps' totals); lane k holds warp k's.
+  const uint32_t vO = lane < nwarps ? m.bscratch[lane] : 0u;
+  const uint32_t vE = lane < nwarps ? m.bscratch[32 + lane] : 0u;
+  uint32_t sO = vO, sE = vE;
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint32_t yO = __shfl_up_sync(kAll, sO, d);
+    const uint32_t yE = __shfl_up_sync(kAll, sE, d);
+    if (lane >= d) { sO += yO; sE += yE; }
   }
-  uint32_t total;
-  uint32_t run = block_excl_scan(osum, m.bscratch, &total);
-  for (uint32_t w = ta; w < tz; ++w) {
-    m.ocum[w] = run;
-    run += __popc(m.O[w]);
+  const uint32_t totO = __shfl_sync(kAll, sO, 31), totE = __shfl_sync(kAll, sE, 31);
+  const uint32_t xO = sO - vO, xE = sE - vE;
+  const uint32_t baseO = __shfl_sync(kAll, xO, warp);
+  const uint32_t baseE = __shfl_sync(kAll, xE, warp);
+  CandCount cc;
+  cc.elo = erank_local(m, W, per, xE, totE, cr.lo);
+  cc.nc_nat = erank_local(m, W, per, xE, totE, cr.hi) - cc.elo;
+  cc.nent_nat = erank_local(m, W, per, xE, totE, min(max(cr.eh, cr.lo), cr.hi)) - cc.elo;
+  const bool tab = cr.want && cr.first + cc.nc_nat <= cr.cap;
+  __syncthreads();  // every warp has read the local counts it needs
+  for (uint32_t w = w0 + lane; w < w1; w += 32) {
+    const uint32_t o = m.ocum[w] + baseO;
+    const uint32_t e = m.erank[w] + baseE;
+    m.ocum[w] = o;
+    m.erank[w] = e;
+    const uint32_t oe = o + __popc(m.O[w]);
+    if ((oe >> 5) != (o >> 5)) m.sel[oe >> 5] = (uint16_t)w;
+    if (tab) {
+      const uint32_t ew = m.E[w];
+      const uint32_t bw = w << 5;
+      uint32_t v = 0;
+      if (ew && bw + 32 > cr.lo && bw < cr.hi) {
+        v = ew;
+        if (cr.lo > bw) v &= ~0u << (cr.lo - bw);
+        if (cr.hi - bw < 32) v &= (1u << (cr.hi - bw)) - 1u;
+      }
+      if (v) {
+        uint32_t idx = cr.first + e - cc.elo + __popc(ew & ((1u << (__ffs(v) - 1)) - 1u));
+        while (v) {
+          const uint32_t b = __ffs(v) - 1;
+          v &= v - 1;
+          m.cpos[idx++] = bw + b + 1;
+        }
+      }
+    }
   }
-  if (tid == 0) m.ocum[W] = total;
-  // ne: next word with an E bit, from the right.
-  uint32_t nxt = block_suffix_min_excl(fnz, m.bscratch);
-  if (nxt > kNoWord) nxt = kNoWord;
-  for (uint32_t w = tz; w > ta;) {
-    --w;
-    if (m.E[w]) nxt = w;
-    m.ne[w] = (uint16_t)nxt;
+  if (tid == 0) {
+    m.ocum[W] = totO;
+    m.erank[W] = totE;
+    m.sel[0] = 0;
+    if (tab && cr.first) m.cpos[0] = cr.ps_rel;
   }
   __syncthreads();
-  // notw: two-pointer from each thread's first word (found by binary search).
-  if (p.T != 0 && ta < tz) {
-    const uint32_t T = p.T;
-    // smallest j >= ta with ocum[j+1] - ocum[ta] >= T
-    uint32_t lo2 = ta, hi2 = W;  // answer in [lo2, hi2]; W = none
-    while (lo2 < hi2) {
-      const uint32_t mid = (lo2 + hi2) >> 1;
-      if (m.ocum[mid + 1] - m.ocum[ta] >= T) hi2 = mid; else lo2 = mid + 1;
-    }
-    uint32_t j = lo2;
-    for (uint32_t w = ta; w < tz; ++w) {
-      if (j < w) j = w;
-      while (j < W && m.ocum[j + 1] - m.ocum[w] < T) ++j;
-      m.notw[w] = j < W ? (uint16_t)j : kNoWord;
-    }
-  }
+  return cc;
 }
 
 // ---------------------------------------------------------------------------
@@ -693,7 +764,7 @@ __device__ void seg_bitmaps(const SegShared &sh, const Geom &g,
 //   exits       by pointer doubling, the terminal of every entry candidate
 //               (those below p_s + max_size), and their distinct values.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(512)
+__global__ void __launch_bounds__(512, 2)
 map_kernel(Geom g, DevParams p, WsPtrs ws) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const uint32_t kMaxCand = g.cap;
@@ -708,9 +779,6 @@ map_kernel(Geom g, DevParams p, WsPtrs ws) {
   }
   __syncthreads();
   const MapSmem m = carve(smem_raw, sh.W, g.L);
-  seg_bitmaps(sh, g, p, m);
-  __syncthreads();
-
   const int64_t B = sh.B;
   const uint64_t p_s = sh.p_s, n_f = sh.n_f;
   const uint32_t end_rel = (uint32_t)((int64_t)n_f - B);
@@ -719,53 +787,18 @@ map_kernel(Geom g, DevParams p, WsPtrs ws) {
   const uint32_t first = sh.seg == 0 ? 1u : 0u;
   // Candidate run ends e in [lo, hi): x = e + 1 in [p_s, q_s).  In a file's
   // first item, run ends before byte SeqLength-1 would need bytes before the
-  // file start, so they are not candidates.
+  // file start, so they are not candidates.  Entries: x < p_s + max_size.
   const uint32_t lo = first ? ps_rel + p.R - 1 : ps_rel - 1;
   const uint32_t hi = max(q_rel - 1, lo);
   const uint32_t ent_end = (uint32_t)((int64_t)min(p_s + (uint64_t)p.mx, n_f) - B);
-  const uint32_t wlo = lo >> 5, whi = (hi + 31) >> 5;
-  const uint32_t nw = whi - wlo;
-  const uint32_t per = (nw + nthreads - 1) / nthreads;
-  const uint32_t a = wlo + tid * per, z = min(a + per, whi);
-  uint32_t cnt = 0, cent = 0;
-  for (uint32_t w = a; w < z; ++w) {
-    uint32_t v = m.E[w];
-    const uint32_t base = w << 5;
-    if (lo > base) v &= ~0u << (lo - base);
-    if (hi - base < 32) v &= (1u << (hi - base)) - 1u;
-    cnt += __popc(v);
-    // entries: e + 1 < ent_end
-    const uint32_t eh = ent_end - 1;  // e < eh
-    uint32_t ve = v;
-    if (eh <= base) ve = 0;
-    else if (eh - base < 32) ve &= (1u << (eh - base)) - 1u;
-    cent += __popc(ve);
-  }
-  uint32_t nc_nat;
-  const uint32_t off = block_excl_scan(cnt, sh.scratch, &nc_nat);
-  uint32_t nent_nat;
-  (void)block_excl_scan(cent, sh.scratch, &nent_nat);
-  const uint32_t nc = nc_nat + first;
+  const CandRange cr{lo, hi, ent_end - 1, first, (uint32_t)kMaxCand, ps_rel, true};
+  const CandCount cc = seg_bitmaps(sh, g, p, m, cr);
+  const uint32_t nc = cc.nc_nat + first;
+  const uint32_t elo = cc.elo;
   const bool abnormal = nc > (uint32_t)kMaxCand;
-  if (!abnormal) {
-    uint32_t o = off + first;
-    for (uint32_t w = a; w < z; ++w) {
-      uint32_t v = m.E[w];
-      const uint32_t base = w << 5;
-      if (lo > base) v &= ~0u << (lo - base);
-      if (hi - base < 32) v &= (1u << (hi - base)) - 1u;
-      m.erank[w - wlo] = (uint16_t)(o - first);
-      while (v) {
-        const uint32_t bpos = __ffs(v) - 1;
-        v &= v - 1;
-        m.cpos[o++] = base + bpos + 1;
-      }
-    }
-    if (tid == 0) {
-      if (first) m.cpos[0] = ps_rel;
-      sh.nc = nc;
-      sh.nent = first ? 1u : nent_nat;
-    }
+  if (!abnormal && tid == 0) {
+    sh.nc = nc;
+    sh.nent = first ? 1u : cc.nent_nat;
   }
   __syncthreads();
   if (abnormal) {
@@ -783,62 +816,46 @@ map_kernel(Geom g, DevParams p, WsPtrs ws) {
   // from a block-wide queue when theirs is done, so a warp's lanes stay busy
   // however many regions a chunk needs.
   const Bits bits = bits_of(m, sh.W);
-  const uint32_t tmask_lo = ~((1u << (lo & 31)) - 1u);
   const uint32_t skip_min = p.mn > p.R ? p.mn - p.R : 0u;
   const int lane = tid & 31;
   for (int j = tid; j < kImgHash; j += nthreads) m.ihash[j] = kEscape;
+  const uint32_t Wm1 = sh.W - 1;
   uint32_t k = kNone, lim = 0, i = 0;
+  bool more = true;  // the queue still holds candidates (same in all lanes)
   while (true) {
-    const uint32_t want = __ballot_sync(0xffffffffu, k == kNone);
-    if (want) {
-      const int leader = __ffs(want) - 1;
-      uint32_t base = 0;
-      if (lane == leader) base = atomicAdd(&sh.qhead, (uint32_t)__popc(want));
-      base = __shfl_sync(0xffffffffu, base, leader);
-      if (k == kNone) {
-        const uint32_t kk = base + __popc(want & ((1u << lane) - 1u));
-        if (kk < nc) {
+    if (more) {
+      const uint32_t want = __ballot_sync(0xffffffffu, k == kNone);
+      if (want) {
+        const int leader = __ffs(want) - 1;
+        uint32_t qb = 0;
+        if (lane == leader) qb = atomicAdd(&sh.qhead, (uint32_t)__popc(want));
+        qb = __shfl_sync(0xffffffffu, qb, leader);
+        const uint32_t kk = qb + __popc(want & ((1u << lane) - 1u));
+        if (k == kNone && kk < nc) {
           k = kk;
           const uint32_t c = m.cpos[kk];
           lim = (end_rel - c > p.mx) ? c + p.mx : end_rel;
           i = c + skip_min;
         }
+        more = qb + __popc(want) < nc;
       }
     }
     if (__ballot_sync(0xffffffffu, k != kNone) == 0) break;
-    if (k != kNone) {
-      uint32_t y = kNone;
-      if (i + 1 >= lim) {
-        y = lim;                                    // max size or input end
-      } else {
-        const uint32_t sp = p.T ? nth_O(bits, i + 1, p.T, lim) : kNone;
-        const uint32_t e = first_E(bits, i + p.R - 1, sp == kNone ? lim : sp);
-        if (e != kNone) y = e + 1;                  // boundary run (Sec. III.A)
-        else if (sp == kNone) y = lim;
-        else i = sp + 1 + p.S;                      // content-defined skip (Sec. III.C)
-      }
-      if (y != kNone) {
-        uint32_t code;
-        if (y >= q_rel) {
-          code = kTerminal | (y - ps_rel);
-        } else {
-          // Index of y among the candidates: its rank among the run ends of
-          // the candidate range, if y - 1 is one.
-          const uint32_t e = y - 1;
-          const uint32_t w = e >> 5;
-          const uint32_t bit = 1u << (e & 31);
-          if (e >= lo && (m.E[w] & bit)) {
-            uint32_t below = m.E[w] & (bit - 1u);
-            if (w == wlo) below &= tmask_lo;
-            code = first + m.erank[w - wlo] + __popc(below);
-          } else {
-            code = kEscape;  // a forced cut inside the item: not a candidate
-          }
-        }
-        m.cnxt[k] = code;
-        m.jmp[k] = (code & kTerminal) ? (uint16_t)k : (uint16_t)code;
-        k = kNone;
-      }
+    const uint32_t y = region_step(bits, p, i, k != kNone ? lim : 0u);
+    // The next cut as a code: terminal (at or after q_s), the index of the
+    // candidate it is (its rank among the run ends from lo on), or escape (a
+    // forced cut inside the item, which is not a candidate).
+    const uint32_t ye = y - 1;
+    const uint32_t w = min(ye >> 5, Wm1);
+    const uint32_t ew = m.E[w];
+    const uint32_t bit = 1u << (ye & 31);
+    uint32_t code = kEscape;
+    if (y >= q_rel) code = kTerminal | (y - ps_rel);
+    else if (ye >= lo && (ew & bit)) code = first + m.erank[w] + __popc(ew & (bit - 1u)) - elo;
+    if (k != kNone && y != kNone) {
+      m.cnxt[k] = code;
+      m.jmp[k] = (code & kTerminal) ? (uint16_t)k : (uint16_t)code;
+      k = kNone;
     }
   }
   __syncthreads();
@@ -1167,8 +1184,7 @@ repair_kernel(Geom g, DevParams p, WsPtrs ws) {
       __syncthreads();
       if (s_run) {
         const MapSmem m = carve(smem_raw, sh.W, g.L);
-        seg_bitmaps(sh, g, p, m);
-        __syncthreads();
+        (void)seg_bitmaps(sh, g, p, m, CandRange{0, 0, 0, 0, 0, 0, false});
         if (tid == 0) {
           const Bits bits = bits_of(m, sh.W);
           const int64_t B = sh.B;
@@ -1291,8 +1307,18 @@ uint32_t max_words(uint32_t L, uint64_t mx) {
 
 constexpr size_t kSmemBudget = 220 * 1024;
 
+// Default segment: the largest of 128, 96 and 64 KiB whose block still leaves
+// room for a second resident block (two blocks of 512 threads per SM).
+constexpr size_t kSmemPair = 112 * 1024;
+uint32_t default_segment(uint64_t mx) {
+  for (uint32_t L = 131072u; L > 65536u; L -= 32768u)
+    if (L >= mx && map_smem_bytes(max_words(L, mx), L) <= kSmemPair) return L;
+  return 65536u;
+}
+
 uint32_t pick_segment(const seqcdc_params_t *p, const seqcdc_tuning_t *t) {
-  uint32_t L = (t && t->segment_bytes) ? t->segment_bytes : 65536u;
+  uint32_t L = (t && t->segment_bytes) ? t->segment_bytes
+                                       : default_segment(p ? p->max_size : 0);
   // An item must be at least max_size long so that its entries (natural cuts
   // below p_s + max_size) all lie inside it.
   if (p && L < p->max_size) L = (uint32_t)p->max_size;
@@ -1308,8 +1334,8 @@ uint32_t pick_segment(const seqcdc_params_t *p, const seqcdc_tuning_t *t) {
 }
 
 uint32_t pick_threads(const seqcdc_tuning_t *t) {
-  uint32_t n = (t && t->block_threads) ? t->block_threads : 256u;
-  if (n != 128u && n != 256u && n != 512u) n = 256u;
+  uint32_t n = (t && t->block_threads) ? t->block_threads : 512u;
+  if (n != 128u && n != 256u && n != 512u) n = 512u;
   return n;
 }
 
@@ -1485,6 +1511,14 @@ int seqcdc_params(uint32_t expected_kib, uint32_t mode, seqcdc_params_t *out) {
 
 int seqcdc_validate(const seqcdc_params_t *p) {
   return params_ok(p) ? SEQCDC_OK : SEQCDC_EINVAL;
+}
+
+int seqcdc_resolve_tuning(const seqcdc_params_t *p, const seqcdc_tuning_t *tuning,
+                          seqcdc_tuning_t *out) {
+  if (!params_ok(p) || !out) return SEQCDC_EINVAL;
+  out->segment_bytes = pick_segment(p, tuning);
+  out->block_threads = pick_threads(tuning);
+  return SEQCDC_OK;
 }
 
 size_t seqcdc_workspace_size(const seqcdc_params_t *p, uint64_t total_bytes,

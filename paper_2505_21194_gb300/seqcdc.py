@@ -84,6 +84,8 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
         lib.seqcdc_params.restype = ctypes.c_int
         lib.seqcdc_validate.argtypes = [P]
         lib.seqcdc_validate.restype = ctypes.c_int
+        lib.seqcdc_resolve_tuning.argtypes = [P, T, T]
+        lib.seqcdc_resolve_tuning.restype = ctypes.c_int
         lib.seqcdc_workspace_size.argtypes = [P, u64, u64, T]
         lib.seqcdc_workspace_size.restype = ctypes.c_size_t
         lib.seqcdc_chunk.argtypes = [P, vp, u64, vp, u64, vp, vp, ctypes.c_size_t, T, vp]
@@ -150,6 +152,15 @@ def make_params(mode, seq_length, skip_trigger, skip_size, min_size,
 
 def seqcdc_validate(p: Params) -> int:
     return load_library().seqcdc_validate(ctypes.byref(p))
+
+
+def seqcdc_resolve_tuning(p: Params, tuning=None) -> Tuning:
+    """Segment size and block size a call with this tuning runs with."""
+    out = Tuning()
+    _check(load_library().seqcdc_resolve_tuning(ctypes.byref(p), _tuning(tuning),
+                                                ctypes.byref(out)),
+           "seqcdc_resolve_tuning")
+    return out
 
 
 def seqcdc_workspace_size(p: Params, total_bytes: int, nfiles: int,
