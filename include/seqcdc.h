@@ -91,8 +91,8 @@ typedef struct {
 /*
  * Fill *out with the segment size and block size that a chunking call with
  * these parameters and this tuning (NULL or zero fields: library defaults)
- * runs with.  The defaults are 512 threads and the largest of 128, 96 and
- * 64 KiB segments for which two blocks share an SM.  Returns SEQCDC_EINVAL
+ * runs with.  The defaults are 256 threads and 64 KiB segments (max_size if
+ * larger).  Returns SEQCDC_EINVAL
  * for an invalid parameter set or a NULL out.
  */
 int seqcdc_resolve_tuning(const seqcdc_params_t *p, const seqcdc_tuning_t *tuning,

@@ -322,10 +322,10 @@ __device__ __forceinline__ uint32_t region_step(const Bits &b, const DevParams &
       if (pos < lim) e = pos;
     }
   }
-  if (!open) return lim;              // maximum size or end of input (Sec. IV)
-  if (e < sp) return e + 1;           // boundary run ends first (Sec. III.A)
-  if (sp == kNone) return lim;
-  i = sp + 1 + p.S;                   // content-defined skip (Sec. III.C)
+  // No run end before lim: no later region can cut either.
+  if (!open || e == kNone) return lim;  // maximum size or end of input (Sec. IV)
+  if (e < sp) return e + 1;             // boundary run ends first (Sec. III.A)
+  i = sp + 1 + p.S;                     // content-defined skip (Sec. III.C)
   return kNone;
 }
 
@@ -409,11 +409,18 @@ __global__ void plan_scan_kernel(Geom g, WsPtrs ws, uint64_t nftiles,
 // ---------------------------------------------------------------------------
 // Per-item machinery.
 // ---------------------------------------------------------------------------
-struct SegShared {
-  uint32_t item, file, seg, first_item;
+// Geometry of one item: segment `seg` of a file.
+struct SegGeom {
   int64_t B;          // window base (file-relative); global index of rel 0 is 16-aligned
-  uint64_t p_s, q_s, n_f, gbase;
-  uint32_t W;         // bitmap words
+  uint64_t p_s, q_s;  // the item's bytes [p_s, q_s) (file-relative)
+  uint64_t n_f;       // file size
+  uint64_t gbase;     // global index of the file's first byte
+  uint32_t W;         // bitmap words of the window [B, B + 32 W)
+  uint32_t seg;
+};
+
+struct SegShared {
+  SegGeom gm;
   uint32_t nc, nent, ninvalid, nimg, qhead;
   uint32_t scratch[32];
 };
@@ -427,7 +434,6 @@ struct MapSmem {
   uint16_t *sel;     // W + 2
   uint32_t *cpos;    // cap: candidate positions (rel)
   uint32_t *cnxt;    // cap: next candidate index or terminal code
-  uint16_t *jmp, *jtmp;  // cap: pointer doubling
   uint32_t *ihash;   // kImgHash: distinct exits
   uint32_t *bscratch;  // 64: block helpers
 };
@@ -448,8 +454,6 @@ __device__ __forceinline__ MapSmem carve(unsigned char *raw, uint32_t W, uint32_
   m.ihash = m.cnxt + cap;
   m.bscratch = m.ihash + kImgHash;
   m.sel = reinterpret_cast<uint16_t *>(m.bscratch + 64);
-  m.jmp = m.sel + W + 2;
-  m.jtmp = m.jmp + cap;
   return m;
 }
 
@@ -457,7 +461,7 @@ __host__ __device__ inline size_t map_smem_bytes(uint32_t W, uint32_t L) {
   const uint32_t cap = cand_cap(L);
   return (size_t)4 * (4 * (size_t)(W + 1) + nz_words(W) + 2 * (size_t)cap +
                       kImgHash + 64) +
-         (size_t)2 * ((W + 2) + 2 * (size_t)cap) + 16;
+         (size_t)2 * (W + 2) + 16;
 }
 
 __device__ __forceinline__ uint32_t find_file(const uint32_t *seg_base,
@@ -488,30 +492,23 @@ __device__ uint32_t find_file_warp(const uint32_t *seg_base, uint64_t nfiles,
   return (uint32_t)lo;
 }
 
-// Geometry of item (file, seg); one thread.
-__device__ void seg_setup(SegShared &sh, const Geom &g, const DevParams &p,
-                          uint32_t item, uint32_t file, uint32_t seg,
-                          uint32_t first_item) {
-  sh.item = item;
-  sh.file = file;
-  sh.seg = seg;
-  sh.first_item = first_item;
-  sh.n_f = file_size(g, file);
-  sh.gbase = file_start(g, file);
-  sh.p_s = (uint64_t)seg * g.L;
-  sh.q_s = min(sh.p_s + g.L, sh.n_f);
-  const uint64_t w1 = min(sh.q_s + p.mx, sh.n_f);
+// Geometry of segment `seg` of `file`.
+__device__ __forceinline__ SegGeom seg_geom(const Geom &g, const DevParams &p,
+                                            uint32_t file, uint32_t seg) {
+  SegGeom gm;
+  gm.seg = seg;
+  gm.n_f = file_size(g, file);
+  gm.gbase = file_start(g, file);
+  gm.p_s = (uint64_t)seg * g.L;
+  gm.q_s = min(gm.p_s + g.L, gm.n_f);
+  const uint64_t w1 = min(gm.q_s + p.mx, gm.n_f);
   // Window base: 32 bytes before the item, rounded down so that its global
   // byte index is 16-aligned.
-  int64_t gb = (int64_t)(sh.gbase + sh.p_s) - 32;
+  int64_t gb = (int64_t)(gm.gbase + gm.p_s) - 32;
   gb = gb >= 0 ? (gb & ~(int64_t)15) : -(((-gb) + 15) & ~(int64_t)15);
-  sh.B = gb - (int64_t)sh.gbase;
-  sh.W = (uint32_t)(((int64_t)w1 - sh.B + 31) >> 5);
-  sh.nc = 0;
-  sh.nent = 0;
-  sh.ninvalid = 0;
-  sh.nimg = 0;
-  sh.qhead = 0;
+  gm.B = gb - (int64_t)gm.gbase;
+  gm.W = (uint32_t)(((int64_t)w1 - gm.B + 31) >> 5);
+  return gm;
 }
 
 __device__ __forceinline__ Bits bits_of(const MapSmem &m, uint32_t W) {
@@ -602,14 +599,14 @@ __device__ __forceinline__ uint32_t erank_local(const MapSmem &m, uint32_t W,
 // ballot gives the nonzero-E mask in word order and one warp scan per half
 // gives running O and E counts.  After one barrier every warp adds its base
 // to its counts and scatters the select table and the candidate positions.
-__device__ __forceinline__ CandCount seg_bitmaps(const SegShared &sh, const Geom &g,
+__device__ __forceinline__ CandCount seg_bitmaps(const SegGeom &gm, const Geom &g,
                                  const DevParams &p, const MapSmem &m,
                                  const CandRange &cr) {
   constexpr uint32_t kAll = 0xffffffffu;
   const int tid = threadIdx.x, nthreads = blockDim.x;
-  const uint32_t W = sh.W;
+  const uint32_t W = gm.W;
   const uint8_t *base = g.data;
-  const int64_t gwin = (int64_t)sh.gbase + sh.B;  // global byte index of rel 0
+  const int64_t gwin = (int64_t)gm.gbase + gm.B;  // global byte index of rel 0
   const int lane = tid & 31, warp = tid >> 5, nwarps = nthreads >> 5;
   uint32_t per = (W + nwarps - 1) / nwarps;
   per = (per + 63) & ~63u;
@@ -761,8 +758,9 @@ __device__ __forceinline__ CandCount seg_bitmaps(const SegShared &sh, const Geom
 //   next        the chunker's next cut from each candidate, as the index of
 //               that candidate, or a terminal code (first cut >= q_s) or an
 //               escape code (a forced cut inside the item: not a candidate);
-//   exits       by pointer doubling, the terminal of every entry candidate
-//               (those below p_s + max_size), and their distinct values.
+//   exits       the terminal of every entry candidate (those below
+//               p_s + max_size), by following its chain of next codes, and
+//               their distinct values.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(512, 2)
 map_kernel(Geom g, DevParams p, WsPtrs ws) {
@@ -773,18 +771,24 @@ map_kernel(Geom g, DevParams p, WsPtrs ws) {
   const uint32_t item = blockIdx.x;
   const uint32_t nitems = ws.hdr->nitems;
   if (item >= nitems) return;
-  if (tid < 32) {
-    const uint32_t f = find_file_warp(ws.seg_base, g.nfiles, item);
-    if (tid == 0) seg_setup(sh, g, p, item, f, item - ws.seg_base[f], ws.seg_base[f]);
+  // Every warp finds the item's file and geometry itself: no barrier before
+  // the bitmap pass.
+  const uint32_t f = find_file_warp(ws.seg_base, g.nfiles, item);
+  const SegGeom gm = seg_geom(g, p, f, item - ws.seg_base[f]);
+  if (tid == 0) {
+    sh.nc = 0;
+    sh.nent = 0;
+    sh.ninvalid = 0;
+    sh.nimg = 0;
+    sh.qhead = 0;
   }
-  __syncthreads();
-  const MapSmem m = carve(smem_raw, sh.W, g.L);
-  const int64_t B = sh.B;
-  const uint64_t p_s = sh.p_s, n_f = sh.n_f;
+  const MapSmem m = carve(smem_raw, gm.W, g.L);
+  const int64_t B = gm.B;
+  const uint64_t p_s = gm.p_s, n_f = gm.n_f;
   const uint32_t end_rel = (uint32_t)((int64_t)n_f - B);
-  const uint32_t q_rel = (uint32_t)((int64_t)sh.q_s - B);
+  const uint32_t q_rel = (uint32_t)((int64_t)gm.q_s - B);
   const uint32_t ps_rel = (uint32_t)((int64_t)p_s - B);
-  const uint32_t first = sh.seg == 0 ? 1u : 0u;
+  const uint32_t first = gm.seg == 0 ? 1u : 0u;
   // Candidate run ends e in [lo, hi): x = e + 1 in [p_s, q_s).  In a file's
   // first item, run ends before byte SeqLength-1 would need bytes before the
   // file start, so they are not candidates.  Entries: x < p_s + max_size.
@@ -792,7 +796,7 @@ map_kernel(Geom g, DevParams p, WsPtrs ws) {
   const uint32_t hi = max(q_rel - 1, lo);
   const uint32_t ent_end = (uint32_t)((int64_t)min(p_s + (uint64_t)p.mx, n_f) - B);
   const CandRange cr{lo, hi, ent_end - 1, first, (uint32_t)kMaxCand, ps_rel, true};
-  const CandCount cc = seg_bitmaps(sh, g, p, m, cr);
+  const CandCount cc = seg_bitmaps(gm, g, p, m, cr);
   const uint32_t nc = cc.nc_nat + first;
   const uint32_t elo = cc.elo;
   const bool abnormal = nc > (uint32_t)kMaxCand;
@@ -815,11 +819,11 @@ map_kernel(Geom g, DevParams p, WsPtrs ws) {
   // Lanes advance one scan region per iteration and take a new candidate
   // from a block-wide queue when theirs is done, so a warp's lanes stay busy
   // however many regions a chunk needs.
-  const Bits bits = bits_of(m, sh.W);
+  const Bits bits = bits_of(m, gm.W);
   const uint32_t skip_min = p.mn > p.R ? p.mn - p.R : 0u;
   const int lane = tid & 31;
   for (int j = tid; j < kImgHash; j += nthreads) m.ihash[j] = kEscape;
-  const uint32_t Wm1 = sh.W - 1;
+  const uint32_t Wm1 = gm.W - 1;
   uint32_t k = kNone, lim = 0, i = 0;
   bool more = true;  // the queue still holds candidates (same in all lanes)
   while (true) {
@@ -854,25 +858,10 @@ map_kernel(Geom g, DevParams p, WsPtrs ws) {
     else if (ye >= lo && (ew & bit)) code = first + m.erank[w] + __popc(ew & (bit - 1u)) - elo;
     if (k != kNone && y != kNone) {
       m.cnxt[k] = code;
-      m.jmp[k] = (code & kTerminal) ? (uint16_t)k : (uint16_t)code;
       k = kNone;
     }
   }
   __syncthreads();
-  // Pointer doubling: jmp[k] -> last candidate of k's chain; stops when no
-  // pointer moves.
-  while (true) {
-    bool moved = false;
-    for (uint32_t c = tid; c < nc; c += nthreads) {
-      const uint16_t j = m.jmp[c];
-      const uint16_t jj = m.jmp[j];
-      m.jtmp[c] = jj;
-      moved |= (jj != j);
-    }
-    if (!__syncthreads_or(moved)) break;
-    for (uint32_t c = tid; c < nc; c += nthreads) m.jmp[c] = m.jtmp[c];
-    __syncthreads();
-  }
   // Publish the candidate graph and every entry's exit; collect distinct exits.
   const uint32_t nent = sh.nent;
   uint32_t *gpos = ws.cand_pos + (uint64_t)item * kMaxCand;
@@ -882,7 +871,10 @@ map_kernel(Geom g, DevParams p, WsPtrs ws) {
     gpos[k] = m.cpos[k] - ps_rel;
     gnxt[k] = m.cnxt[k];
     if (k < nent) {
-      const uint32_t t = m.cnxt[m.jmp[k]];
+      // The entry's exit: follow its chain (indices only grow) to the code
+      // that ends it.
+      uint32_t t = m.cnxt[k];
+      while (!(t & kTerminal)) t = m.cnxt[t];
       const uint32_t ex = (t == kEscape) ? kEscape : (t & ~kTerminal);
       gterm[k] = ex;
       if (ex == kEscape) {
@@ -1177,19 +1169,20 @@ repair_kernel(Geom g, DevParams p, WsPtrs ws) {
         s_run = !((ws.state[item] & F_INCL) && ws.incl[item] != kBad &&
                   ws.entry[item] == cur);
         if (s_run) {
-          seg_setup(sh, g, p, item, (uint32_t)f, s, base);
+          sh.gm = seg_geom(g, p, (uint32_t)f, s);
           atomicAdd(&ws.hdr->stats[ST_RECOMPUTED], 1u);
         }
       }
       __syncthreads();
       if (s_run) {
-        const MapSmem m = carve(smem_raw, sh.W, g.L);
-        (void)seg_bitmaps(sh, g, p, m, CandRange{0, 0, 0, 0, 0, 0, false});
+        const SegGeom gm = sh.gm;
+        const MapSmem m = carve(smem_raw, gm.W, g.L);
+        (void)seg_bitmaps(gm, g, p, m, CandRange{0, 0, 0, 0, 0, 0, false});
         if (tid == 0) {
-          const Bits bits = bits_of(m, sh.W);
-          const int64_t B = sh.B;
-          const uint32_t end_rel = (uint32_t)((int64_t)sh.n_f - B);
-          const uint32_t q_rel = (uint32_t)((int64_t)sh.q_s - B);
+          const Bits bits = bits_of(m, gm.W);
+          const int64_t B = gm.B;
+          const uint32_t end_rel = (uint32_t)((int64_t)gm.n_f - B);
+          const uint32_t q_rel = (uint32_t)((int64_t)gm.q_s - B);
           uint64_t *out = ws.slot + (uint64_t)item * ws.slot_cap;
           uint32_t nout = 0;
           uint32_t c = (uint32_t)((int64_t)cur - B);
@@ -1307,14 +1300,10 @@ uint32_t max_words(uint32_t L, uint64_t mx) {
 
 constexpr size_t kSmemBudget = 220 * 1024;
 
-// Default segment: the largest of 128, 96 and 64 KiB whose block still leaves
-// room for a second resident block (two blocks of 512 threads per SM).
-constexpr size_t kSmemPair = 112 * 1024;
-uint32_t default_segment(uint64_t mx) {
-  for (uint32_t L = 131072u; L > 65536u; L -= 32768u)
-    if (L >= mx && map_smem_bytes(max_words(L, mx), L) <= kSmemPair) return L;
-  return 65536u;
-}
+// Default segment: 64 KiB (at least max_size), with 256 threads: four
+// blocks share an SM, which hides the latency of each block's barriers and
+// of its longest chunk better than fewer, larger blocks.
+uint32_t default_segment(uint64_t mx) { return mx > 65536u ? (uint32_t)mx : 65536u; }
 
 uint32_t pick_segment(const seqcdc_params_t *p, const seqcdc_tuning_t *t) {
   uint32_t L = (t && t->segment_bytes) ? t->segment_bytes
@@ -1334,8 +1323,8 @@ uint32_t pick_segment(const seqcdc_params_t *p, const seqcdc_tuning_t *t) {
 }
 
 uint32_t pick_threads(const seqcdc_tuning_t *t) {
-  uint32_t n = (t && t->block_threads) ? t->block_threads : 512u;
-  if (n != 128u && n != 256u && n != 512u) n = 512u;
+  uint32_t n = (t && t->block_threads) ? t->block_threads : 256u;
+  if (n != 128u && n != 256u && n != 512u) n = 256u;
   return n;
 }
 

@@ -101,14 +101,14 @@ def test_strerror(seqcdc_lib):
 
 def test_resolve_tuning_defaults_and_rules(seqcdc_lib):
     s = seqcdc_lib
-    for kib, seg in ((4, 131072), (8, 131072), (16, 98304)):
+    for kib in (4, 8, 16):
         t = s.seqcdc_resolve_tuning(s.seqcdc_params(kib, 0))
-        assert (t.segment_bytes, t.block_threads) == (seg, 512)
+        assert (t.segment_bytes, t.block_threads) == (65536, 256)
     p = s.seqcdc_params(8, 0)
     t = s.seqcdc_resolve_tuning(p, (4096, 128))      # raised to max_size
     assert (t.segment_bytes, t.block_threads) == (16384, 128)
     t = s.seqcdc_resolve_tuning(p, (70000, 300))     # 1 KiB multiple; default threads
-    assert (t.segment_bytes, t.block_threads) == (70656, 512)
+    assert (t.segment_bytes, t.block_threads) == (70656, 256)
     t = s.seqcdc_resolve_tuning(p, (1 << 22, 256))   # capped at 1 MiB, then by smem
     assert t.segment_bytes <= 1 << 20 and t.segment_bytes % 1024 == 0
     with pytest.raises(s.SeqCDCError):
