@@ -54,6 +54,7 @@ namespace {
 // ---------------------------------------------------------------------------
 // Limits and layout constants.
 // ---------------------------------------------------------------------------
+constexpr uint32_t kCandPerLane = 3;  // chunk-step candidates per lane (map kernel)
 constexpr int kImgHash = 128;      // distinct-exit hash slots (power of two)
 constexpr int kMaxImage = 32;      // distinct exits published per item (one per lane)
 constexpr int kFileTile = 1024;    // files per plan block
@@ -246,65 +247,44 @@ __device__ uint32_t block_excl_scan(uint32_t v, uint32_t *scratch,
 // ---------------------------------------------------------------------------
 // Bitmaps of one item in shared memory.  Positions are relative to the window
 // base B (file-relative): rel = pos - B; word w covers rel 32w .. 32w+31.
-//   E, O   run-end and opposing-pair bits
-//   ocum   ocum[w]: O bits in words < w (ocum[W] = all)
-//   erank  erank[w]: E bits in words < w (erank[W] = all)
+//   E, O   run-end and opposing-pair bits (O padded to whole 16-byte groups)
 //   nz     bit w of the mask: E[w] != 0
-//   sel    sel[j]: the word holding O bit number 32 j (bits numbered from 1
-//          in window order); sel[0] = 0
-// With these a scan-region query (Sec. III.D: first set bit of the combined
-// run mask; position of the SkipTrigger-th opposing pair) is a few lookups.
+//   sbE    sbE[s]: E bits in the words before step s (64 words per step)
+//   locE   locE[w]: E bits in the words of w's step before w
+// A scan-region query (Sec. III.D: first set bit of the combined run mask;
+// position of the SkipTrigger-th opposing pair) is a short walk over these.
 // ---------------------------------------------------------------------------
 struct Bits {
   const uint32_t *E;
   const uint32_t *O;
-  const uint32_t *ocum;
   const uint32_t *nz;
-  const uint16_t *sel;
   uint32_t W;
-  uint32_t otot;  // O bits in the window
 };
 
 // One scan region of the chunker (Sec. III.A-C) from scan position i with
 // chunk limit lim: returns the cut (run end + 1 when a run completes before
 // the SkipTrigger-th opposing pair; lim when the chunk reaches its maximum
 // size or the input end), or kNone after moving i past a content-defined skip.
-// The run end and the opposing pair are looked up independently, and every
-// index is clamped into the window, so lanes without work (lim = 0, result
-// lim) run the same instructions; the only loops are the short walks to the
-// wanted O bit and to the next word holding an E bit.
+// The first run end e at or after i + SeqLength - 1 comes from the nonzero
+// mask; then the opposing pairs in [i + 1, e) are counted four words at a
+// time: the SkipTrigger-th of them, if any, is the skip point.  Every index
+// is clamped into the window, so lanes without work (lim = 0, result lim) run
+// the same instructions.
 __device__ __forceinline__ uint32_t region_step(const Bits &b, const DevParams &p,
                                                 uint32_t &i, uint32_t lim) {
   const uint32_t Wm1 = b.W - 1;
   const bool open = i + 1 < lim;
-  // sp: the SkipTrigger-th O bit at or after i + 1, if below lim.
-  uint32_t sp = kNone;
-  if (p.T) {
-    const uint32_t x = i + 1;
-    const uint32_t w0 = min(x >> 5, Wm1);
-    // number (from 1, window order) of the wanted O bit
-    const uint32_t t = b.ocum[w0] + __popc(b.O[w0] & ((1u << (x & 31)) - 1u)) + p.T;
-    const bool ok = open && t <= b.otot;
-    // its word is at or after w0 and at or after the word of bit 32 (t / 32)
-    uint32_t w = min(max(w0, (uint32_t)b.sel[min(t >> 5, b.W)]), Wm1);
-    uint32_t cnt = b.ocum[w], m = b.O[w], c = __popc(m);
-    while (ok && cnt + c < t && ((w + 1) << 5) < lim) {
-      cnt += c;
-      ++w;
-      m = b.O[w];
-      c = __popc(m);
-    }
-    if (ok && cnt + c >= t) {
-      const uint32_t pos = (w << 5) + nth_set_bit(m, t - cnt);
-      if (pos < lim) sp = pos;
-    }
-  }
-  // e: the first E bit at or after i + SeqLength - 1, if below lim.
+  const uint32_t x = i + 1;
+  const uint32_t w0 = min(x >> 5, Wm1);
+  uint32_t g = w0 & ~3u;
+  // First group of O words, loaded before the run-end search so that the two
+  // overlap.
+  uint4 v = *reinterpret_cast<const uint4 *>(b.O + g);
   uint32_t e = kNone;
   {
-    const uint32_t x = i + p.R - 1;
-    uint32_t w = min(x >> 5, Wm1);
-    uint32_t m = b.E[w] & (~0u << (x & 31));
+    const uint32_t xs = i + p.R - 1;
+    uint32_t w = min(xs >> 5, Wm1);
+    uint32_t m = b.E[w] & (~0u << (xs & 31));
     if (!m && open) {
       const uint32_t w1 = w + 1;
       if ((w1 << 5) < lim) {
@@ -317,16 +297,47 @@ __device__ __forceinline__ uint32_t region_step(const Bits &b, const DevParams &
         }
       }
     }
-    if (m && x < lim) {
+    if (m && xs < lim) {
       const uint32_t pos = (w << 5) + (__ffs(m) - 1);
       if (pos < lim) e = pos;
     }
   }
   // No run end before lim: no later region can cut either.
   if (!open || e == kNone) return lim;  // maximum size or end of input (Sec. IV)
-  if (e < sp) return e + 1;             // boundary run ends first (Sec. III.A)
-  i = sp + 1 + p.S;                     // content-defined skip (Sec. III.C)
-  return kNone;
+  if (p.T == 0) return e + 1;           // skipping disabled
+  // The SkipTrigger-th O bit in [x, e), if there is one, is the skip point.
+  const uint32_t we = e >> 5;
+  const uint32_t lo_bits = ~0u << (x & 31);
+  const uint32_t hi_bits = (1u << (e & 31)) - 1u;
+  uint32_t need = p.T;
+  while (true) {
+    uint32_t m[4] = {v.x, v.y, v.z, v.w};
+    uint32_t c[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const uint32_t wi = g + j;
+      if (wi < w0) m[j] = 0;
+      else if (wi == w0) m[j] &= lo_bits;
+      if (wi > we) m[j] = 0;
+      else if (wi == we) m[j] &= hi_bits;
+      c[j] = __popc(m[j]);
+    }
+    const uint32_t c01 = c[0] + c[1], c012 = c01 + c[2], call = c012 + c[3];
+    if (need <= call) {
+      uint32_t mw, wj, k;
+      if (need <= c[0]) { mw = m[0]; wj = 0; k = need; }
+      else if (need <= c01) { mw = m[1]; wj = 1; k = need - c[0]; }
+      else if (need <= c012) { mw = m[2]; wj = 2; k = need - c01; }
+      else { mw = m[3]; wj = 3; k = need - c012; }
+      const uint32_t sp = ((g + wj) << 5) + nth_set_bit(mw, k);
+      i = sp + 1 + p.S;                  // content-defined skip (Sec. III.C)
+      return kNone;
+    }
+    need -= call;
+    g += 4;
+    if (g > we) return e + 1;            // boundary run ends first (Sec. III.A)
+    v = *reinterpret_cast<const uint4 *>(b.O + g);
+  }
 }
 
 // One chunk: from chunk start c (rel) return its end (rel).  `end_rel` is the
@@ -427,40 +438,41 @@ struct SegShared {
 
 // Shared memory of the map kernel (bitmaps, query tables, candidate graph).
 struct MapSmem {
-  uint32_t *E, *O;
-  uint32_t *ocum;    // W + 1
-  uint32_t *erank;   // W + 1
+  uint32_t *O;       // o_words(W): 16-byte groups
+  uint32_t *E;       // W + 1
   uint32_t *nz;      // nz_words(W)
-  uint16_t *sel;     // W + 2
+  uint32_t *sbE;     // W / 64 + 2
   uint32_t *cpos;    // cap: candidate positions (rel)
   uint32_t *cnxt;    // cap: next candidate index or terminal code
   uint32_t *ihash;   // kImgHash: distinct exits
   uint32_t *bscratch;  // 64: block helpers
+  uint16_t *locE;    // W + 2
 };
 
 // Words of the nonzero-E mask: one bit per bitmap word, whole 64-word steps.
 __host__ __device__ inline uint32_t nz_words(uint32_t W) { return ((W + 63) >> 6) * 2 + 2; }
+// O words: whole groups of four, plus one spare group.
+__host__ __device__ inline uint32_t o_words(uint32_t W) { return ((W + 3) & ~3u) + 4; }
 
 __device__ __forceinline__ MapSmem carve(unsigned char *raw, uint32_t W, uint32_t L) {
   const uint32_t cap = cand_cap(L);
   MapSmem m;
-  m.E = reinterpret_cast<uint32_t *>(raw);
-  m.O = m.E + W + 1;
-  m.ocum = m.O + W + 1;
-  m.erank = m.ocum + W + 1;
-  m.nz = m.erank + W + 1;
-  m.cpos = m.nz + nz_words(W);
+  m.O = reinterpret_cast<uint32_t *>(raw);  // 16-byte aligned
+  m.E = m.O + o_words(W);
+  m.nz = m.E + W + 1;
+  m.sbE = m.nz + nz_words(W);
+  m.cpos = m.sbE + (W >> 6) + 2;
   m.cnxt = m.cpos + cap;
   m.ihash = m.cnxt + cap;
   m.bscratch = m.ihash + kImgHash;
-  m.sel = reinterpret_cast<uint16_t *>(m.bscratch + 64);
+  m.locE = reinterpret_cast<uint16_t *>(m.bscratch + 64);
   return m;
 }
 
 __host__ __device__ inline size_t map_smem_bytes(uint32_t W, uint32_t L) {
   const uint32_t cap = cand_cap(L);
-  return (size_t)4 * (4 * (size_t)(W + 1) + nz_words(W) + 2 * (size_t)cap +
-                      kImgHash + 64) +
+  return (size_t)4 * (o_words(W) + (W + 1) + nz_words(W) + (W >> 6) + 2 +
+                      2 * (size_t)cap + kImgHash + 64) +
          (size_t)2 * (W + 2) + 16;
 }
 
@@ -512,7 +524,7 @@ __device__ __forceinline__ SegGeom seg_geom(const Geom &g, const DevParams &p,
 }
 
 __device__ __forceinline__ Bits bits_of(const MapSmem &m, uint32_t W) {
-  return Bits{m.E, m.O, m.ocum, m.nz, m.sel, W, m.ocum[W]};
+  return Bits{m.E, m.O, m.nz, W};
 }
 
 // Per-byte unsigned compares of a 4-byte word x with y, the same word shifted
@@ -581,27 +593,23 @@ struct CandCount {
   uint32_t elo;       // E bits before lo
 };
 
-// E bits before rel position x (x <= 32 W) while erank holds warp-local
-// counts: lane k of xE holds the base of warp k, whose words are
-// [k per, (k + 1) per).  Called by all lanes of a warp.
-__device__ __forceinline__ uint32_t erank_local(const MapSmem &m, uint32_t W,
-                                                uint32_t per, uint32_t xE,
-                                                uint32_t totE, uint32_t x) {
+// E bits before rel position x (x <= 32 W) once sbE holds block-wide counts.
+__device__ __forceinline__ uint32_t erank_at(const MapSmem &m, uint32_t W,
+                                             uint32_t etot, uint32_t x) {
   const uint32_t w = x >> 5;
-  const uint32_t bk = __shfl_sync(0xffffffffu, xE, min(w, W - 1) / per);
-  if (w >= W) return totE;
-  return m.erank[w] + bk + __popc(m.E[w] & ((1u << (x & 31)) - 1u));
+  if (w >= W) return etot;
+  return m.sbE[w >> 6] + m.locE[w] + __popc(m.E[w] & ((1u << (x & 31)) - 1u));
 }
 
 // E and O bitmaps of the window [B, B + 32 W), their query tables and the
-// item's natural cuts.  Warp k covers the words [k per, (k + 1) per); per
-// step, lane j takes words wb + j and wb + 32 + j (32 bytes each), so a
-// ballot gives the nonzero-E mask in word order and one warp scan per half
-// gives running O and E counts.  After one barrier every warp adds its base
-// to its counts and scatters the select table and the candidate positions.
+// item's natural cuts.  Warp k covers the words [k per, (k + 1) per) in steps
+// of 64; per step, lane j takes words wb + j and wb + 32 + j (32 bytes each),
+// so a ballot gives the nonzero-E mask in word order and one warp scan gives
+// the E counts of both halves.  Three barriers: after the pass, after each
+// warp has made its step counts block-wide, after the candidate scatter.
 __device__ __forceinline__ CandCount seg_bitmaps(const SegGeom &gm, const Geom &g,
-                                 const DevParams &p, const MapSmem &m,
-                                 const CandRange &cr) {
+                                                 const DevParams &p, const MapSmem &m,
+                                                 const CandRange &cr) {
   constexpr uint32_t kAll = 0xffffffffu;
   const int tid = threadIdx.x, nthreads = blockDim.x;
   const uint32_t W = gm.W;
@@ -622,7 +630,7 @@ __device__ __forceinline__ CandCount seg_bitmaps(const SegGeom &gm, const Geom &
     carry_T = Tp;  // the top 16 bits are the 16 positions before this word
     carry_byte = pv.w >> 24;
   }
-  uint32_t cO = 0, cE = 0;  // O and E bits so far in this warp's words
+  uint32_t cE = 0;  // E bits so far in this warp's words
   for (uint32_t wb = w0; wb < w1; wb += 64) {
     const uint32_t wa = wb + lane, wc = wa + 32;
     const bool la = wa < w1, lc = wc < w1;
@@ -668,71 +676,58 @@ __device__ __forceinline__ CandCount seg_bitmaps(const SegGeom &gm, const Geom &
     if (lc) { m.E[wc] = EC; m.O[wc] = OC; }
     const uint32_t nzA = __ballot_sync(kAll, EA != 0);
     const uint32_t nzC = __ballot_sync(kAll, EC != 0);
+    // E counts before each word within the step: first half in the low 16
+    // bits, second half in the high 16 bits (each at most 1024).
+    const uint32_t xv = __popc(EA) | (__popc(EC) << 16);
+    uint32_t sv = xv;
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint32_t y = __shfl_up_sync(kAll, sv, d);
+      if (lane >= d) sv += y;
+    }
+    const uint32_t tv = __shfl_sync(kAll, sv, 31);
+    const uint32_t ev = sv - xv;
+    const uint32_t tA = tv & 0xffffu;
+    if (la) m.locE[wa] = (uint16_t)(ev & 0xffffu);
+    if (lc) m.locE[wc] = (uint16_t)(tA + (ev >> 16));
     if (lane == 0) {
       m.nz[wb >> 5] = nzA;
       m.nz[(wb >> 5) + 1] = nzC;
+      m.sbE[wb >> 6] = cE;
     }
-    // Running counts, O in the low half and E in the high half (a step adds
-    // at most 1024 to each).
-    const uint32_t xA = __popc(OA) | (__popc(EA) << 16);
-    const uint32_t xC = __popc(OC) | (__popc(EC) << 16);
-    uint32_t sA = xA, sC = xC;
-    for (int d = 1; d < 32; d <<= 1) {
-      const uint32_t yA = __shfl_up_sync(kAll, sA, d);
-      const uint32_t yC = __shfl_up_sync(kAll, sC, d);
-      if (lane >= d) { sA += yA; sC += yC; }
-    }
-    const uint32_t tA = __shfl_sync(kAll, sA, 31), tC = __shfl_sync(kAll, sC, 31);
-    const uint32_t eA = sA - xA, eC = sC - xC + tA;
-    if (la) { m.ocum[wa] = cO + (eA & 0xffffu); m.erank[wa] = cE + (eA >> 16); }
-    if (lc) { m.ocum[wc] = cO + (eC & 0xffffu); m.erank[wc] = cE + (eC >> 16); }
-    const uint32_t tt = tA + tC;
-    cO += tt & 0xffffu;
-    cE += tt >> 16;
+    cE += tA + (tv >> 16);
   }
-  if (lane == 0) {
-    m.bscratch[warp] = cO;
-    m.bscratch[32 + warp] = cE;
+  if (lane == 0) m.bscratch[warp] = cE;
+  __syncthreads();
+
+  // Warp bases (exclusive scan over the warps' totals) added to the step
+  // counts of this warp's words.
+  const uint32_t vE = lane < nwarps ? m.bscratch[lane] : 0u;
+  uint32_t sE = vE;
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint32_t y = __shfl_up_sync(kAll, sE, d);
+    if (lane >= d) sE += y;
+  }
+  const uint32_t etot = __shfl_sync(kAll, sE, 31);
+  const uint32_t baseE = __shfl_sync(kAll, sE - vE, warp);
+  if (w0 < w1 && baseE) {  // a warp without words owns no step
+    for (uint32_t st = (w0 >> 6) + lane; (st << 6) < w1; st += 32) m.sbE[st] += baseE;
   }
   __syncthreads();
 
-  // Warp bases (exclusive scans over the warps' totals); lane k holds warp k's.
-  const uint32_t vO = lane < nwarps ? m.bscratch[lane] : 0u;
-  const uint32_t vE = lane < nwarps ? m.bscratch[32 + lane] : 0u;
-  uint32_t sO = vO, sE = vE;
-  for (int d = 1; d < 32; d <<= 1) {
-    const uint32_t yO = __shfl_up_sync(kAll, sO, d);
-    const uint32_t yE = __shfl_up_sync(kAll, sE, d);
-    if (lane >= d) { sO += yO; sE += yE; }
-  }
-  const uint32_t totO = __shfl_sync(kAll, sO, 31), totE = __shfl_sync(kAll, sE, 31);
-  const uint32_t xO = sO - vO, xE = sE - vE;
-  const uint32_t baseO = __shfl_sync(kAll, xO, warp);
-  const uint32_t baseE = __shfl_sync(kAll, xE, warp);
   CandCount cc;
-  cc.elo = erank_local(m, W, per, xE, totE, cr.lo);
-  cc.nc_nat = erank_local(m, W, per, xE, totE, cr.hi) - cc.elo;
-  cc.nent_nat = erank_local(m, W, per, xE, totE, min(max(cr.eh, cr.lo), cr.hi)) - cc.elo;
-  const bool tab = cr.want && cr.first + cc.nc_nat <= cr.cap;
-  __syncthreads();  // every warp has read the local counts it needs
-  for (uint32_t w = w0 + lane; w < w1; w += 32) {
-    const uint32_t o = m.ocum[w] + baseO;
-    const uint32_t e = m.erank[w] + baseE;
-    m.ocum[w] = o;
-    m.erank[w] = e;
-    const uint32_t oe = o + __popc(m.O[w]);
-    if ((oe >> 5) != (o >> 5)) m.sel[oe >> 5] = (uint16_t)w;
-    if (tab) {
+  cc.elo = erank_at(m, W, etot, cr.lo);
+  cc.nc_nat = erank_at(m, W, etot, cr.hi) - cc.elo;
+  cc.nent_nat = erank_at(m, W, etot, min(max(cr.eh, cr.lo), cr.hi)) - cc.elo;
+  if (cr.want && cr.first + cc.nc_nat <= cr.cap) {
+    for (uint32_t w = (cr.lo >> 5) + tid; (w << 5) < cr.hi; w += nthreads) {
       const uint32_t ew = m.E[w];
       const uint32_t bw = w << 5;
-      uint32_t v = 0;
-      if (ew && bw + 32 > cr.lo && bw < cr.hi) {
-        v = ew;
-        if (cr.lo > bw) v &= ~0u << (cr.lo - bw);
-        if (cr.hi - bw < 32) v &= (1u << (cr.hi - bw)) - 1u;
-      }
+      uint32_t v = ew;
+      if (cr.lo > bw) v &= ~0u << (cr.lo - bw);
+      if (cr.hi - bw < 32) v &= (1u << (cr.hi - bw)) - 1u;
       if (v) {
-        uint32_t idx = cr.first + e - cc.elo + __popc(ew & ((1u << (__ffs(v) - 1)) - 1u));
+        uint32_t idx = cr.first + m.sbE[w >> 6] + m.locE[w] - cc.elo +
+                       __popc(ew & ((1u << (__ffs(v) - 1)) - 1u));
         while (v) {
           const uint32_t b = __ffs(v) - 1;
           v &= v - 1;
@@ -740,12 +735,7 @@ __device__ __forceinline__ CandCount seg_bitmaps(const SegGeom &gm, const Geom &
         }
       }
     }
-  }
-  if (tid == 0) {
-    m.ocum[W] = totO;
-    m.erank[W] = totE;
-    m.sel[0] = 0;
-    if (tab && cr.first) m.cpos[0] = cr.ps_rel;
+    if (tid == 0 && cr.first) m.cpos[0] = cr.ps_rel;
   }
   __syncthreads();
   return cc;
@@ -762,7 +752,11 @@ __device__ __forceinline__ CandCount seg_bitmaps(const SegGeom &gm, const Geom &
 //               p_s + max_size), by following its chain of next codes, and
 //               their distinct values.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(512, 2)
+// Instantiated per block size, each capped at 40 registers so that the
+// blocks that shared memory allows (six of 256 threads at 64 KiB segments)
+// are not limited by registers.
+template <int kThreads, int kMinBlocks>
+__global__ void __launch_bounds__(kThreads, kMinBlocks)
 map_kernel(Geom g, DevParams p, WsPtrs ws) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const uint32_t kMaxCand = g.cap;
@@ -824,9 +818,15 @@ map_kernel(Geom g, DevParams p, WsPtrs ws) {
   const int lane = tid & 31;
   for (int j = tid; j < kImgHash; j += nthreads) m.ihash[j] = kEscape;
   const uint32_t Wm1 = gm.W - 1;
+  // Only as many warps as give each lane about kCandPerLane candidates take
+  // part: a lane then runs through several chunks, so fewer lanes idle in
+  // the tail of the longest chunk; the other warps wait at the barrier
+  // without issuing.
+  const uint32_t step_warps =
+      min((uint32_t)(nthreads >> 5), max(1u, (nc + 32 * kCandPerLane - 1) / (32 * kCandPerLane)));
   uint32_t k = kNone, lim = 0, i = 0;
-  bool more = true;  // the queue still holds candidates (same in all lanes)
-  while (true) {
+  bool more = (uint32_t)(tid >> 5) < step_warps;  // the queue may hold candidates
+  while ((uint32_t)(tid >> 5) < step_warps) {
     if (more) {
       const uint32_t want = __ballot_sync(0xffffffffu, k == kNone);
       if (want) {
@@ -855,8 +855,13 @@ map_kernel(Geom g, DevParams p, WsPtrs ws) {
     const uint32_t bit = 1u << (ye & 31);
     uint32_t code = kEscape;
     if (y >= q_rel) code = kTerminal | (y - ps_rel);
-    else if (ye >= lo && (ew & bit)) code = first + m.erank[w] + __popc(ew & (bit - 1u)) - elo;
+    else if (ye >= lo && (ew & bit))
+      code = first + m.sbE[w >> 6] + m.locE[w] + __popc(ew & (bit - 1u)) - elo;
     if (k != kNone && y != kNone) {
+      // A candidate's next cut lies after it: a candidate code must be a
+      // later index (anything else would be a table fault; escaping sends the
+      // item to the exact repair pass).
+      if (!(code & kTerminal) && (code <= k || code >= nc)) code = kEscape;
       m.cnxt[k] = code;
       k = kNone;
     }
@@ -874,7 +879,9 @@ map_kernel(Geom g, DevParams p, WsPtrs ws) {
       // The entry's exit: follow its chain (indices only grow) to the code
       // that ends it.
       uint32_t t = m.cnxt[k];
-      while (!(t & kTerminal)) t = m.cnxt[t];
+      for (uint32_t hop = 0; !(t & kTerminal); ++hop) {
+        t = hop < nc ? m.cnxt[t] : kEscape;  // indices grow: at most nc hops
+      }
       const uint32_t ex = (t == kEscape) ? kEscape : (t & ~kTerminal);
       gterm[k] = ex;
       if (ex == kEscape) {
@@ -1103,6 +1110,7 @@ resolve_kernel(Geom g, WsPtrs ws) {
         if (k >= 0) {
           uint32_t code = gnxt[k];
           while (!(code & kTerminal) && nout < ws.slot_cap) {
+            if (code >= r.nc) { code = kEscape; break; }  // never: codes are checked when made
             out[nout++] = r.p_s + gpos[code];
             code = gnxt[code];
           }
@@ -1393,6 +1401,29 @@ WsPtrs ws_ptrs(void *d_ws, const Layout &l) {
 thread_local cudaEvent_t g_prof_begin = nullptr;
 thread_local cudaEvent_t g_prof_end = nullptr;
 
+constexpr int kMaxDevices = 64;
+
+// Allow `smem` bytes of dynamic shared memory for the map kernel of this
+// block size and for the repair kernel on the current device; remembered per
+// device so that the attribute is set once per size.
+bool smem_configured(uint32_t threads, size_t smem,
+                     void (*map_fn)(Geom, DevParams, WsPtrs)) {
+  static std::mutex mu;
+  static size_t done[kMaxDevices][3] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return false;
+  const int k = threads == 128u ? 0 : threads == 512u ? 2 : 1;
+  std::lock_guard<std::mutex> lock(mu);
+  if (done[dev][k] >= smem) return true;
+  if (cudaFuncSetAttribute(map_fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem) != cudaSuccess ||
+      cudaFuncSetAttribute(repair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem) != cudaSuccess)
+    return false;
+  done[dev][k] = smem;
+  return true;
+}
+
 int run(const seqcdc_params_t *p, const uint8_t *d_data, uint64_t total,
         const uint64_t *d_offsets, uint64_t nfiles, uint64_t *d_cuts,
         uint64_t cap, uint64_t *d_cut_offsets, uint64_t *d_count, void *d_ws,
@@ -1414,21 +1445,14 @@ int run(const seqcdc_params_t *p, const uint8_t *d_data, uint64_t total,
                (uint32_t)p->min_size, (uint32_t)p->max_size};
   const size_t smem = map_smem_bytes(max_words(L, p->max_size), L);
   if (smem > kSmemBudget) return SEQCDC_ERANGE;
-  static size_t configured = 0;
-  if (smem > 48 * 1024 && smem > configured) {
-    if (cudaFuncSetAttribute(map_kernel,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem) != cudaSuccess ||
-        cudaFuncSetAttribute(repair_kernel,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem) != cudaSuccess)
-      return SEQCDC_ECUDA;
-    configured = smem;
-  }
+  void (*map_fn)(Geom, DevParams, WsPtrs) =
+      threads == 128u ? map_kernel<128, 12>
+                      : threads == 512u ? map_kernel<512, 3> : map_kernel<256, 6>;
+  if (smem > 48 * 1024 && !smem_configured(threads, smem, map_fn)) return SEQCDC_ECUDA;
   plan_tiles_kernel<<<(unsigned)l.nftiles, 256, 0, st>>>(g, w);
   plan_scan_kernel<<<(unsigned)l.nftiles, 256, 0, st>>>(g, w, l.nftiles, l.imax);
   if (g_prof_begin) cudaEventRecord(g_prof_begin, st);
-  map_kernel<<<(unsigned)l.imax, threads, smem, st>>>(g, dp, w);
+  map_fn<<<(unsigned)l.imax, threads, smem, st>>>(g, dp, w);
   if (g_prof_end) cudaEventRecord(g_prof_end, st);
   resolve_kernel<<<(unsigned)l.imax, 32, 0, st>>>(g, w);
   const uint64_t vblocks = (l.imax + 255) / 256;
@@ -1453,7 +1477,6 @@ __global__ void copy_status_kernel(const WsHeader *hdr, uint32_t *out) {
   *out = hdr->status;
 }
 
-constexpr int kMaxDevices = 64;
 
 // Device address of g_noalloc_scratch on the current device (set-up on first
 // use per device, with that device current).  nullptr on failure.
