@@ -504,6 +504,14 @@ __device__ uint32_t find_file_warp(const uint32_t *seg_base, uint64_t nfiles,
   return (uint32_t)lo;
 }
 
+// The file end relative to the window base, for chunk limits.  A file can be
+// far longer than 4 GiB; any value past the window (at most L + max_size + 64
+// bytes long) gives the same limits, so it is clamped to 32 bits.
+__device__ __forceinline__ uint32_t end_rel_of(uint64_t n_f, int64_t B) {
+  const int64_t r = (int64_t)n_f - B;
+  return r >= (int64_t)0xffffffffLL ? 0xffffffffu : (uint32_t)r;
+}
+
 // Geometry of segment `seg` of `file`.
 __device__ __forceinline__ SegGeom seg_geom(const Geom &g, const DevParams &p,
                                             uint32_t file, uint32_t seg) {
@@ -779,7 +787,7 @@ map_kernel(Geom g, DevParams p, WsPtrs ws) {
   const MapSmem m = carve(smem_raw, gm.W, g.L);
   const int64_t B = gm.B;
   const uint64_t p_s = gm.p_s, n_f = gm.n_f;
-  const uint32_t end_rel = (uint32_t)((int64_t)n_f - B);
+  const uint32_t end_rel = end_rel_of(n_f, B);
   const uint32_t q_rel = (uint32_t)((int64_t)gm.q_s - B);
   const uint32_t ps_rel = (uint32_t)((int64_t)p_s - B);
   const uint32_t first = gm.seg == 0 ? 1u : 0u;
@@ -1189,7 +1197,7 @@ repair_kernel(Geom g, DevParams p, WsPtrs ws) {
         if (tid == 0) {
           const Bits bits = bits_of(m, gm.W);
           const int64_t B = gm.B;
-          const uint32_t end_rel = (uint32_t)((int64_t)gm.n_f - B);
+          const uint32_t end_rel = end_rel_of(gm.n_f, B);
           const uint32_t q_rel = (uint32_t)((int64_t)gm.q_s - B);
           uint64_t *out = ws.slot + (uint64_t)item * ws.slot_cap;
           uint32_t nout = 0;

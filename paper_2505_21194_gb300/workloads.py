@@ -180,11 +180,16 @@ def adversarial_block(index: int, seed: int, block: int = 16 * MIB) -> np.ndarra
     if kind == "zeros":
         return np.zeros(block, dtype=np.uint8)
     if kind == "ramp":
-        return (np.arange(block, dtype=np.int64) % 256).astype(np.uint8)
+        return _tile(np.arange(256, dtype=np.uint8), block)
     rng = np.random.default_rng((seed << 32) ^ index)
     period = int(rng.integers(3, 10))
-    return ((np.arange(block, dtype=np.int64) % period)
-            * (256 // period)).astype(np.uint8)
+    return _tile((np.arange(period) * (256 // period)).astype(np.uint8), block)
+
+
+def _tile(pattern: np.ndarray, n: int) -> np.ndarray:
+    """``pattern`` repeated from its start, cut to ``n`` bytes."""
+    reps = -(-n // pattern.size)
+    return np.tile(pattern, reps)[:n].copy()
 
 
 def adversarial_stream(nblocks: int, seed: int = 0, block: int = 16 * MIB):

@@ -171,3 +171,29 @@ def test_config3_batched_10k_files(gpu):
     ecuts, eco = oracle.chunk_batch_threaded(data, offs, p, os.cpu_count() or 4)
     assert_same(co, eco)
     assert_same(cuts, ecuts)
+
+
+@pytest.mark.slow
+def test_single_stream_beyond_4gib(gpu):
+    """Offsets past 2^32 in one stream: 4 GiB + 64 KiB of zeros, then 16 MiB of
+    random bytes.  Zeros hold no run, so every chunk there is cut at max_size
+    (Sec. VI); the tail is checked against the oracle restarted at the last
+    cut before it."""
+    import torch
+    s = gpu
+    p = oracle.presets(16)
+    zeros = (4 << 30) + (64 << 10)
+    tail = W.uniform_random(16 << 20, 77)
+    n = zeros + tail.size
+    d = torch.zeros(n, dtype=torch.uint8, device="cuda")
+    d[zeros:].copy_(torch.from_numpy(tail))
+    got = s.chunk(d, _p(s, p)).cpu().numpy().astype(np.int64)
+    del d
+    torch.cuda.empty_cache()
+    mx = p.max_size
+    head = got[got <= zeros]
+    assert np.array_equal(head, np.arange(1, head.size + 1, dtype=np.int64) * mx)
+    start = int(head[-1])
+    window = np.concatenate([np.zeros(zeros - start, np.uint8), tail])
+    exp = oracle.chunk(window, p).astype(np.int64) + start
+    assert np.array_equal(got[head.size:], exp)
