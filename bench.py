@@ -10,7 +10,9 @@ to HBM once, and are far larger than L2 (no flush needed between steps).
 Printed: one JSON line with the metric, the device-resident throughput
 (`value`), the end-to-end throughput through host buffers (`e2e`), the
 roofline of the dominant kernel, the plain one-launch-per-file loop for
-comparison, clocks, and the CPU oracle as a reported baseline.
+comparison, clocks, the CPU oracle as a reported baseline, and `serve`:
+p50/p99 latency and sustained GB/s of the continuous-batching server under
+open-loop Poisson arrivals at 25, 50, 100 and 200 GB/s offered load.
 
 `--impl reference` times the CPU oracle (the plain single-threaded chunker,
 files spread over the host cores) on the same workload instead.
@@ -410,6 +412,8 @@ def run_gpu(args):
         "path_stats": path_stats,
         "clocks": clocks,
     }
+    if not args.no_serve:
+        line["serve"] = serve_levels(dev, p, tuning, SERVE_LOADS_GBS)
     if world == 1 and not args.no_cpu:
         threads = os.cpu_count() or 1
         dt, _ = cpu_oracle_pass(data_np, offs_np, threads)
@@ -426,6 +430,57 @@ def run_gpu(args):
     print(json.dumps(line), flush=True)
 
 
+SERVE_LOADS_GBS = (25, 50, 100, 200)
+
+
+def serve_levels(dev, p, tuning, loads, duration_s=1.0):
+    """Open-loop serving at each offered load (GB/s): Poisson arrivals of
+    requests drawn from the 64 versions (about 16 MiB each) of the backup-like
+    stream, admitted under a 64 GiB HBM budget, batched continuously.  One
+    request in a hundred is checked against the oracle and against the same
+    payload chunked alone."""
+    import torch
+    import oracle
+    from paper_2505_21194_gb300 import seqcdc, workloads as W
+    from paper_2505_21194_gb300.serve import Server, poisson_arrivals
+    stream, voffs = W.backup_stream(SEED)
+    voffs = voffs.astype(np.int64)
+    sizes = np.diff(voffs)
+    pool = torch.from_numpy(stream).pin_memory()
+    srv = Server(p, pool, voffs, budget_bytes=64 << 30, max_batch_bytes=4 << 30,
+                 tuning=tuning, device=str(dev))
+    op = oracle.Params(p.mode, p.seq_length, p.skip_trigger, p.skip_size,
+                       p.min_size, p.max_size)
+    expect, alone = {}, {}
+    levels, checked, bad = [], 0, 0
+    srv.run(poisson_arrivals(20.0, 0.2, len(sizes), sizes, SEED))  # warm-up
+    for gbs in loads:
+        rate = gbs * 1e9 / float(sizes.mean())
+        arr = poisson_arrivals(rate, duration_s, len(sizes), sizes, SEED + int(gbs))
+        keep = {r.rid for r in arr if r.rid % 100 == 0}
+        st = srv.run(arr, keep=keep)
+        for r in arr:
+            if r.rid not in keep:
+                continue
+            k = r.payload
+            if k not in expect:
+                b = stream[voffs[k]:voffs[k + 1]]
+                expect[k] = oracle.chunk(b, op).astype(np.int64)
+                alone[k] = seqcdc.chunk(torch.from_numpy(b).to(dev), p, tuning).cpu().numpy()
+            got = st.results[r.rid]
+            checked += 1
+            bad += int(not (np.array_equal(got, expect[k]) and np.array_equal(got, alone[k])))
+        levels.append({"offered_GBs": gbs, "requests": st.requests, "batches": st.batches,
+                       "sustained_GBs": round(st.sustained_gbs, 2),
+                       "p50_ms": round(st.latency["p50_ms"], 3),
+                       "p99_ms": round(st.latency["p99_ms"], 3)})
+    return {"requests_from": "64 versions (~16 MiB each) of the 1 GiB backup-like stream",
+            "arrivals": "Poisson, open loop, %.1f s per level" % duration_s,
+            "hbm_budget_GiB": 64, "max_batch_GiB": 4, "levels": levels,
+            "checked": checked, "mismatches": bad,
+            "latency": "arrival to completion of the batch's copy back (device clock)"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -437,6 +492,8 @@ def main():
     ap.add_argument("--skip-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true",
                     help="skip the CPU-oracle baseline (profiling runs)")
+    ap.add_argument("--no-serve", action="store_true",
+                    help="skip the serving measurement (open-loop Poisson arrivals)")
     ap.add_argument("--nfiles", type=int, default=NFILES,
                     help="files in the batch (default: the 10,000-file workload)")
     args = ap.parse_args()
