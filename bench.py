@@ -213,6 +213,19 @@ def run_gpu(args):
     total = int(data_np.size)
     nfiles = offs_np.size - 1
     p = seqcdc.seqcdc_params(KIB, MODE)
+    tune_src = "library default"
+    if args.segment_bytes or args.threads:
+        tune_src = "command line"
+    elif not args.no_autotune:
+        # Launch tuning from the autotuner, timed on the first 1,000 files of
+        # the same workload (cached per GPU model / parameters / file sizes).
+        from paper_2505_21194_gb300 import autotune
+        nsamp = min(1000, offs_np.size - 1)
+        d_s = torch.from_numpy(data_np[:int(offs_np[nsamp])]).to(dev)
+        o_s = torch.from_numpy(offs_np[:nsamp + 1].astype(np.int64)).to(dev)
+        args.segment_bytes, args.threads = autotune.autotune(p, d_s, o_s)
+        tune_src = "autotuned on the first %d files" % nsamp
+        del d_s, o_s
     tuning = seqcdc.Tuning(args.segment_bytes, args.threads)
     eff = seqcdc.seqcdc_resolve_tuning(p, tuning)
     cap = total // p.min_size + nfiles
@@ -391,6 +404,7 @@ def run_gpu(args):
             "total_bytes": total, "nfiles": nfiles, "cuts": ncuts,
             "segment_bytes": eff.segment_bytes,
             "block_threads": eff.block_threads,
+            "tuning": tune_src,
             "l2": "inputs (%.1f GiB) far larger than L2; no flush" % (total / 2**30),
             "parallelism": "1 GPU per rank, independent batches (weak scaling)",
         },
@@ -492,6 +506,8 @@ def main():
     ap.add_argument("--skip-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true",
                     help="skip the CPU-oracle baseline (profiling runs)")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="library default launch tuning instead of the autotuner")
     ap.add_argument("--no-serve", action="store_true",
                     help="skip the serving measurement (open-loop Poisson arrivals)")
     ap.add_argument("--nfiles", type=int, default=NFILES,
