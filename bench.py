@@ -381,7 +381,9 @@ def run_gpu(args):
     traffic = None
     if rec is not None:
         traffic = float(rec["dram_bytes_per_byte"]) * total
-    launches_per_step = 8  # plan_tiles, plan_scan, map, resolve, verify, repair, count_tiles, emit
+    # plan_tiles, plan_scan, map, resolve, 2 x (verify, run_repair), verify,
+    # repair, count_tiles, emit
+    launches_per_step = 12
     if rank != 0:
         return
     line = {

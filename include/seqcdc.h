@@ -202,9 +202,11 @@ int seqcdc_status(const void *d_ws, void *stream);
  * natural entries could not all be walked, [2] segments with more distinct
  * exits than the library publishes, [3] look-backs that had to wait for a
  * predecessor's true exit, [4] segments found inconsistent by the verify
- * pass, [5] segments re-chunked by the repair pass, [6] emissions that stepped
- * from an entry that was not a natural cut, [7] total look-back depth.  The
- * counters describe which code paths ran; the output is exact either way.
+ * pass, [5] segments re-chunked by the repair passes, [6] segments the
+ * resolve pass emitted from a guessed entry (or could not emit) because their
+ * true entry was unknown or not one of their natural cuts, [7] total
+ * look-back depth.  The counters describe which code paths ran; the output is
+ * exact either way.
  */
 int seqcdc_stats(const void *d_ws, void *stream, uint32_t *out, uint32_t n);
 

@@ -69,6 +69,9 @@ constexpr uint32_t F_NOIMG = 2u;   // no image (more than kMaxImage exits)
 constexpr uint32_t F_AGG = 4u;     // map predecessor image -> exits published
 constexpr uint32_t F_NOAGG = 8u;   // no such map (predecessor had no image)
 constexpr uint32_t F_INCL = 16u;   // true exit, entry and cuts published
+constexpr uint32_t F_RUN = 32u;    // first item of a run of inconsistent items
+// Rounds of verify + parallel run repair before the sequential fallback.
+constexpr uint32_t kRepairRounds = 2;
 
 constexpr uint32_t kNone = 0xFFFFFFFFu;
 constexpr uint32_t kTerminal = 0x80000000u;  // candidate next: first cut >= item end
@@ -91,7 +94,9 @@ struct WsHeader {
   uint32_t ticket;
   uint32_t nitems;
   uint32_t stats[8];  // see seqcdc_stats()
-  uint32_t pad[53];
+  uint32_t nruns[kRepairRounds];  // runs of inconsistent items found by each verify round
+  uint32_t runq[kRepairRounds];   // run queue head of each parallel repair round
+  uint32_t pad[53 - 2 * kRepairRounds];
 };
 
 enum : uint32_t {
@@ -101,13 +106,13 @@ enum : uint32_t {
   ST_LB_WAITS = 3,      // look-backs that had to wait for a true exit
   ST_INCONSISTENT = 4,  // items whose entry disagreed with the predecessor
   ST_RECOMPUTED = 5,    // items re-chunked by the repair pass
-  ST_REPLAYED = 6,      // items left to the repair pass by the resolve kernel
+  ST_REPLAYED = 6,      // items the resolve kernel emitted from a guessed entry (or could not emit)
   ST_LB_STEPS = 7,      // total look-back depth
 };
 
 struct Layout {
   size_t hdr, seg_base, ftile, state, incl, entry, first_bad, count, img_n,
-      img, agg, cand_n, ent_n, cand_pos, cand_nxt, ent_term, slot, itile, total;
+      img, agg, cand_n, ent_n, cand_pos, cand_nxt, ent_term, slot, itile, runs, total;
   uint64_t imax;     // upper bound on items
   uint64_t nftiles;  // plan tiles
   uint64_t nitiles;  // compaction tiles
@@ -154,6 +159,7 @@ struct WsPtrs {
   uint32_t *ent_term;   // per item x kMaxCand: exit of each entry (relative) or escape
   uint64_t *slot;       // per item x slot_cap (file-relative cuts)
   uint32_t *itile;      // per compaction tile
+  uint32_t *runs;       // per item: first items of runs to repair (verify rounds)
   uint32_t slot_cap;
 };
 
@@ -406,6 +412,7 @@ __global__ void plan_scan_kernel(Geom g, WsPtrs ws, uint64_t nftiles,
     ws.hdr->ticket = 0;
     ws.hdr->status = 0;
     for (int k = 0; k < 8; ++k) ws.hdr->stats[k] = 0;
+    for (uint32_t k = 0; k < kRepairRounds; ++k) ws.hdr->nruns[k] = ws.hdr->runq[k] = 0;
   }
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < imax;
        i += (uint64_t)gridDim.x * blockDim.x) {
@@ -432,6 +439,8 @@ struct SegGeom {
 
 struct SegShared {
   SegGeom gm;
+  uint64_t exit;      // repair: exit of the item just re-chunked
+  uint32_t flag;      // repair: broadcast from thread 0
   uint32_t nc, nent, ninvalid, nimg, qhead;
   uint32_t scratch[32];
 };
@@ -1095,49 +1104,62 @@ resolve_kernel(Geom g, WsPtrs ws) {
     }
     x = lookback(r, ws);
   }
-  // Emission from x along the candidate links (lane 0).
+  // Emission from x along the candidate links (lane 0).  When x is not known
+  // or is not one of the item's tabulated entries (a forced cut entered it),
+  // the item's first entry is taken instead: its cuts and exit let the items
+  // after it resolve, and since the recorded entry is then not the
+  // predecessor's exit, the verify pass sends the item to the repair pass.
   if (lane == 0) {
     uint64_t *out = ws.slot + (uint64_t)item * ws.slot_cap;
     uint32_t nout = 0;
-    uint64_t exit_pos = x;
-    bool bad = (x == kBad);
-    if (!bad && x < r.q_s) {
-      bad = true;
-      if (r.nc != kAbnormal && x >= r.p_s) {
+    uint64_t exit_pos = kBad, entry = x;
+    bool done = false;
+    if (x != kBad && x >= r.q_s) {
+      exit_pos = x;  // the entry lies past the item: no cut inside it
+      done = true;
+    } else if (r.nc != kAbnormal) {
+      const uint32_t *gpos = ws.cand_pos + (uint64_t)item * kMaxCand;
+      const uint32_t *gnxt = ws.cand_nxt + (uint64_t)item * kMaxCand;
+      int k = -1;
+      if (x != kBad && x >= r.p_s) {
         const uint32_t want = (uint32_t)(x - r.p_s);
-        const uint32_t *gpos = ws.cand_pos + (uint64_t)item * kMaxCand;
-        const uint32_t *gnxt = ws.cand_nxt + (uint64_t)item * kMaxCand;
         uint32_t lo = 0, hi = r.nent;
-        int k = -1;
         while (lo < hi) {
           const uint32_t mid = (lo + hi) >> 1;
           const uint32_t v = gpos[mid];
           if (v == want) { k = (int)mid; break; }
           if (v < want) lo = mid + 1; else hi = mid;
         }
-        if (k >= 0) {
-          uint32_t code = gnxt[k];
-          while (!(code & kTerminal) && nout < ws.slot_cap) {
-            if (code >= r.nc) { code = kEscape; break; }  // never: codes are checked when made
-            out[nout++] = r.p_s + gpos[code];
-            code = gnxt[code];
-          }
-          if (code != kEscape && nout < ws.slot_cap) {
-            exit_pos = r.p_s + (code & ~kTerminal);
-            out[nout++] = exit_pos;
-            bad = false;
-          }
+      }
+      const bool guess = k < 0 && r.nent > 0;
+      if (guess) {
+        k = 0;
+        entry = r.p_s + gpos[0];
+      }
+      if (k >= 0) {
+        uint32_t code = gnxt[k];
+        while (!(code & kTerminal) && nout < ws.slot_cap) {
+          if (code >= r.nc) { code = kEscape; break; }  // never: codes are checked when made
+          out[nout++] = r.p_s + gpos[code];
+          code = gnxt[code];
+        }
+        if (code != kEscape && nout < ws.slot_cap) {
+          exit_pos = r.p_s + (code & ~kTerminal);
+          out[nout++] = exit_pos;
+          done = true;
         }
       }
+      if (guess && done) atomicAdd(&ws.hdr->stats[ST_REPLAYED], 1u);
     }
-    if (bad) {
+    if (!done) {
       nout = 0;
       exit_pos = kBad;
+      entry = x;
       atomicAdd(&ws.hdr->stats[ST_REPLAYED], 1u);
     }
     ws.count[item] = nout;
     ws.incl[item] = exit_pos;
-    ws.entry[item] = x;
+    ws.entry[item] = entry;
     __threadfence();
     atomicOr(&ws.state[item], F_INCL);
     atomicAdd(&ws.hdr->stats[ST_ITEMS], 1u);
@@ -1146,32 +1168,125 @@ resolve_kernel(Geom g, WsPtrs ws) {
 
 // Verify: item s of a file is consistent when it was emitted and its entry
 // equals the exit its predecessor computed.  By induction from the file start
-// (always a true entry), a file whose items are all consistent is exact.  The
-// first inconsistent item of each file is recorded for the repair pass.
-__global__ void verify_kernel(Geom g, WsPtrs ws) {
+// (always a true entry), a file whose items are all consistent is exact.
+__device__ __forceinline__ bool item_consistent(const WsPtrs &ws, uint64_t i, uint32_t s) {
+  bool ok = (ws.state[i] & F_INCL) && ws.incl[i] != kBad && ws.entry[i] != kBad;
+  if (ok) ok = ws.entry[i] == (s > 0 ? ws.incl[i - 1] : 0ull);
+  return ok;
+}
+
+// Rounds 0 .. kRepairRounds-1 list the first item of every run of
+// inconsistent items (and flag it) for the parallel repair; the last round
+// records the first inconsistent item of each file for the sequential repair.
+__global__ void verify_kernel(Geom g, WsPtrs ws, uint32_t round) {
+  // Nothing was inconsistent in the previous round, so nothing changed.
+  if (round > 0 && ws.hdr->nruns[round - 1] == 0) return;
   const uint32_t nitems = ws.hdr->nitems;
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nitems;
        i += (uint64_t)gridDim.x * blockDim.x) {
     const uint32_t f = find_file(ws.seg_base, g.nfiles, (uint32_t)i);
     const uint32_t s = (uint32_t)i - ws.seg_base[f];
-    bool ok = (ws.state[i] & F_INCL) && ws.incl[i] != kBad && ws.entry[i] != kBad;
-    if (ok) ok = ws.entry[i] == (s > 0 ? ws.incl[i - 1] : 0ull);
-    if (!ok) {
+    const bool ok = item_consistent(ws, i, s);
+    if (round < kRepairRounds) {
+      const bool start = !ok && (s == 0 || item_consistent(ws, i - 1, s - 1));
+      if (start) {
+        ws.runs[atomicAdd(&ws.hdr->nruns[round], 1u)] = (uint32_t)i;
+        atomicOr(&ws.state[i], F_RUN);
+      } else if (ws.state[i] & F_RUN) {
+        atomicAnd(&ws.state[i], ~F_RUN);
+      }
+      if (round == 0 && !ok) atomicAdd(&ws.hdr->stats[ST_INCONSISTENT], 1u);
+    } else if (!ok) {
       atomicMin(&ws.first_bad[f], s);
-      atomicAdd(&ws.hdr->stats[ST_INCONSISTENT], 1u);
     }
   }
 }
 
-// Repair: one block per file with an inconsistent item.  From the first
-// inconsistent item on, items are re-chunked from the true exit of their
-// predecessor (bitmaps rebuilt from the input, chunker stepped sequentially);
-// an item whose recorded entry already equals that exit is kept.
+// Re-chunk `item` (segment `seg` of `file`) from entry `cur` (file-relative):
+// the block rebuilds the bitmaps from the input, thread 0 steps the chunker.
+// Called by every thread of the block; returns the item's new exit.
+__device__ uint64_t rechunk_item(const Geom &g, const DevParams &p, const WsPtrs &ws,
+                                 SegShared &sh, unsigned char *smem_raw, uint32_t item,
+                                 uint32_t file, uint32_t seg, uint64_t cur) {
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    sh.gm = seg_geom(g, p, file, seg);
+    atomicAdd(&ws.hdr->stats[ST_RECOMPUTED], 1u);
+  }
+  __syncthreads();
+  const SegGeom gm = sh.gm;
+  const MapSmem m = carve(smem_raw, gm.W, g.L);
+  (void)seg_bitmaps(gm, g, p, m, CandRange{0, 0, 0, 0, 0, 0, false});
+  if (tid == 0) {
+    const Bits bits = bits_of(m, gm.W);
+    const int64_t B = gm.B;
+    const uint32_t end_rel = end_rel_of(gm.n_f, B);
+    const uint32_t q_rel = (uint32_t)((int64_t)gm.q_s - B);
+    uint64_t *out = ws.slot + (uint64_t)item * ws.slot_cap;
+    uint32_t nout = 0;
+    uint32_t c = (uint32_t)((int64_t)cur - B);
+    while (c < q_rel && nout < ws.slot_cap) {
+      c = chunk_step(bits, p, c, end_rel);
+      out[nout++] = (uint64_t)(B + (int64_t)c);
+    }
+    const uint64_t e = nout ? (uint64_t)(B + (int64_t)c) : cur;
+    ws.count[item] = nout;
+    ws.entry[item] = cur;
+    ws.incl[item] = e;
+    atomicOr(&ws.state[item], F_INCL);
+    sh.exit = e;
+  }
+  __syncthreads();
+  const uint64_t e = sh.exit;
+  __syncthreads();
+  return e;
+}
+
+// Parallel repair: persistent blocks take runs from the list of this round.
+// A run is re-chunked item by item from the exit of the item before it, until
+// an item's recorded entry equals the new exit (it was already chunked from
+// the right entry) or the next run's first item (which its own block takes).
+// A run whose starting exit changes meanwhile is found by the next round.
+__global__ void __launch_bounds__(512)
+run_repair_kernel(Geom g, DevParams p, WsPtrs ws, uint32_t round) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ SegShared sh;
+  const int tid = threadIdx.x;
+  const uint32_t nruns = ws.hdr->nruns[round];
+  while (true) {
+    if (tid == 0) sh.flag = atomicAdd(&ws.hdr->runq[round], 1u);
+    __syncthreads();
+    const uint32_t r = sh.flag;
+    __syncthreads();
+    if (r >= nruns) return;
+    const uint32_t i0 = ws.runs[r];
+    const uint32_t f = find_file(ws.seg_base, g.nfiles, i0);
+    const uint32_t base = ws.seg_base[f], end = ws.seg_base[f + 1];
+    uint64_t cur = (i0 == base) ? 0ull : __ldcg(&ws.incl[i0 - 1]);
+    for (uint32_t it = i0; it < end; ++it) {
+      if (it > i0) {
+        if (tid == 0) {
+          const uint32_t st = __ldcg(&ws.state[it]);
+          sh.flag = (st & F_RUN) || ((st & F_INCL) && __ldcg(&ws.incl[it]) != kBad &&
+                                     __ldcg(&ws.entry[it]) == cur);
+        }
+        __syncthreads();
+        const bool stop = sh.flag != 0;
+        __syncthreads();
+        if (stop) break;
+      }
+      cur = rechunk_item(g, p, ws, sh, smem_raw, it, f, it - base, cur);
+    }
+  }
+}
+
+// Sequential repair (last resort): one block per file that is still
+// inconsistent; from its first inconsistent item on, every item whose
+// recorded entry is not its predecessor's exit is re-chunked.
 __global__ void __launch_bounds__(512)
 repair_kernel(Geom g, DevParams p, WsPtrs ws) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ SegShared sh;
-  __shared__ uint32_t s_run;
   const int tid = threadIdx.x;
   for (uint64_t f = blockIdx.x; f < g.nfiles; f += gridDim.x) {
     const uint32_t fb = ws.first_bad[f];
@@ -1182,39 +1297,14 @@ repair_kernel(Geom g, DevParams p, WsPtrs ws) {
     for (uint32_t s = fb; s < nseg; ++s) {
       const uint32_t item = base + s;
       if (tid == 0) {
-        s_run = !((ws.state[item] & F_INCL) && ws.incl[item] != kBad &&
-                  ws.entry[item] == cur);
-        if (s_run) {
-          sh.gm = seg_geom(g, p, (uint32_t)f, s);
-          atomicAdd(&ws.hdr->stats[ST_RECOMPUTED], 1u);
-        }
+        sh.flag = !((ws.state[item] & F_INCL) && ws.incl[item] != kBad &&
+                    ws.entry[item] == cur);
       }
       __syncthreads();
-      if (s_run) {
-        const SegGeom gm = sh.gm;
-        const MapSmem m = carve(smem_raw, gm.W, g.L);
-        (void)seg_bitmaps(gm, g, p, m, CandRange{0, 0, 0, 0, 0, 0, false});
-        if (tid == 0) {
-          const Bits bits = bits_of(m, gm.W);
-          const int64_t B = gm.B;
-          const uint32_t end_rel = end_rel_of(gm.n_f, B);
-          const uint32_t q_rel = (uint32_t)((int64_t)gm.q_s - B);
-          uint64_t *out = ws.slot + (uint64_t)item * ws.slot_cap;
-          uint32_t nout = 0;
-          uint32_t c = (uint32_t)((int64_t)cur - B);
-          while (c < q_rel && nout < ws.slot_cap) {
-            c = chunk_step(bits, p, c, end_rel);
-            out[nout++] = (uint64_t)(B + (int64_t)c);
-          }
-          ws.count[item] = nout;
-          ws.entry[item] = cur;
-          ws.incl[item] = nout ? (uint64_t)(B + (int64_t)c) : cur;
-          ws.state[item] |= F_INCL;
-        }
-      }
+      const bool run = sh.flag != 0;
       __syncthreads();
-      cur = *((volatile uint64_t *)&ws.incl[item]);
-      __syncthreads();
+      if (run) cur = rechunk_item(g, p, ws, sh, smem_raw, item, (uint32_t)f, s, cur);
+      else cur = __ldcg(&ws.incl[item]);
     }
   }
 }
@@ -1377,6 +1467,7 @@ Layout make_layout(const seqcdc_params_t *p, uint64_t total, uint64_t nfiles,
   l.ent_term = take(l.imax * (size_t)cand_cap(L) * 4);
   l.slot = take(l.imax * (size_t)l.slot_cap * 8);
   l.itile = take(l.nitiles * 4);
+  l.runs = take(l.imax * 4);
   l.total = o;
   return l;
 }
@@ -1402,6 +1493,7 @@ WsPtrs ws_ptrs(void *d_ws, const Layout &l) {
   w.ent_term = reinterpret_cast<uint32_t *>(b + l.ent_term);
   w.slot = reinterpret_cast<uint64_t *>(b + l.slot);
   w.itile = reinterpret_cast<uint32_t *>(b + l.itile);
+  w.runs = reinterpret_cast<uint32_t *>(b + l.runs);
   w.slot_cap = l.slot_cap;
   return w;
 }
@@ -1411,8 +1503,21 @@ thread_local cudaEvent_t g_prof_end = nullptr;
 
 constexpr int kMaxDevices = 64;
 
+// Streaming multiprocessors of the current device (cached per device); 0 on
+// error.
+int sm_count() {
+  static std::mutex mu;
+  static int n[kMaxDevices] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return 0;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!n[dev] && cudaDeviceGetAttribute(&n[dev], cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    n[dev] = 0;
+  return n[dev];
+}
+
 // Allow `smem` bytes of dynamic shared memory for the map kernel of this
-// block size and for the repair kernel on the current device; remembered per
+// block size and for the repair kernels on the current device; remembered per
 // device so that the attribute is set once per size.
 bool smem_configured(uint32_t threads, size_t smem,
                      void (*map_fn)(Geom, DevParams, WsPtrs)) {
@@ -1426,6 +1531,8 @@ bool smem_configured(uint32_t threads, size_t smem,
   if (cudaFuncSetAttribute(map_fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)smem) != cudaSuccess ||
       cudaFuncSetAttribute(repair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem) != cudaSuccess ||
+      cudaFuncSetAttribute(run_repair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)smem) != cudaSuccess)
     return false;
   done[dev][k] = smem;
@@ -1457,6 +1564,8 @@ int run(const seqcdc_params_t *p, const uint8_t *d_data, uint64_t total,
       threads == 128u ? map_kernel<128, 12>
                       : threads == 512u ? map_kernel<512, 3> : map_kernel<256, 6>;
   if (smem > 48 * 1024 && !smem_configured(threads, smem, map_fn)) return SEQCDC_ECUDA;
+  const int sms = sm_count();
+  if (sms <= 0) return SEQCDC_ECUDA;
   plan_tiles_kernel<<<(unsigned)l.nftiles, 256, 0, st>>>(g, w);
   plan_scan_kernel<<<(unsigned)l.nftiles, 256, 0, st>>>(g, w, l.nftiles, l.imax);
   if (g_prof_begin) cudaEventRecord(g_prof_begin, st);
@@ -1464,7 +1573,13 @@ int run(const seqcdc_params_t *p, const uint8_t *d_data, uint64_t total,
   if (g_prof_end) cudaEventRecord(g_prof_end, st);
   resolve_kernel<<<(unsigned)l.imax, 32, 0, st>>>(g, w);
   const uint64_t vblocks = (l.imax + 255) / 256;
-  verify_kernel<<<(unsigned)(vblocks < 4096 ? vblocks : 4096), 256, 0, st>>>(g, w);
+  const unsigned vgrid = (unsigned)(vblocks < 4096 ? vblocks : 4096);
+  const unsigned rgrid = (unsigned)(l.imax < 2u * (uint64_t)sms ? l.imax : 2u * (uint64_t)sms);
+  for (uint32_t round = 0; round < kRepairRounds; ++round) {
+    verify_kernel<<<vgrid, 256, 0, st>>>(g, w, round);
+    run_repair_kernel<<<rgrid, threads, smem, st>>>(g, dp, w, round);
+  }
+  verify_kernel<<<vgrid, 256, 0, st>>>(g, w, kRepairRounds);
   const uint64_t rblocks = nfiles ? nfiles : 1;
   repair_kernel<<<(unsigned)(rblocks < 65535 ? rblocks : 65535), threads, smem, st>>>(g, dp, w);
   count_tiles_kernel<<<(unsigned)l.nitiles, kItemTile, 0, st>>>(w);
