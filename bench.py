@@ -10,9 +10,11 @@ to HBM once, and are far larger than L2 (no flush needed between steps).
 Printed: one JSON line with the metric, the device-resident throughput
 (`value`), the end-to-end throughput through host buffers (`e2e`), the
 roofline of the dominant kernel, the plain one-launch-per-file loop for
-comparison, clocks, the CPU oracle as a reported baseline, and `serve`:
-p50/p99 latency and sustained GB/s of the continuous-batching server under
-open-loop Poisson arrivals at 25, 50, 100 and 200 GB/s offered load.
+comparison, clocks, the CPU oracle as a reported baseline (all host cores and
+one thread), `serve`: p50/p99 latency and sustained GB/s of the
+continuous-batching server under open-loop Poisson arrivals at 25, 50, 100
+and 200 GB/s offered load, and `dedup`: the deduplication savings of the
+backup-like stream at the three settings in both modes.
 
 `--impl reference` times the CPU oracle (the plain single-threaded chunker,
 files spread over the host cores) on the same workload instead.
@@ -428,8 +430,14 @@ def run_gpu(args):
         "path_stats": path_stats,
         "clocks": clocks,
     }
+    backup = None
+    if not args.no_serve or not args.no_dedup:
+        from paper_2505_21194_gb300 import workloads as W
+        backup = W.backup_stream(SEED)
     if not args.no_serve:
-        line["serve"] = serve_levels(dev, p, tuning, SERVE_LOADS_GBS)
+        line["serve"] = serve_levels(dev, p, tuning, SERVE_LOADS_GBS, backup)
+    if not args.no_dedup:
+        line["dedup"] = dedup_savings(dev, backup)
     if world == 1 and not args.no_cpu:
         threads = os.cpu_count() or 1
         dt, _ = cpu_oracle_pass(data_np, offs_np, threads)
@@ -438,18 +446,65 @@ def run_gpu(args):
             d2, _ = cpu_oracle_pass(data_np, offs_np, threads)
             dt += d2
             reps += 1
+        # and the single-threaded oracle on a ~1 GB prefix of the batch
+        import oracle
+        nsamp = int(np.searchsorted(offs_np, 1 << 30))
+        t1 = time.perf_counter()
+        oracle.chunk_batch(data_np[:int(offs_np[nsamp])], offs_np[:nsamp + 1],
+                           oracle.presets(KIB, MODE))
+        dt1 = time.perf_counter() - t1
         line["cpu_baseline"] = {
             "value": round(total * reps / dt / 1e9, 3), "unit": "GB/s", "cores": threads,
             "kind": "oracle",
             "sample": "%d pass(es) over the full 10,000-file batch, files spread over "
-                      "%d host threads" % (reps, threads)}
+                      "%d host threads" % (reps, threads),
+            "single_thread": {"value": round(int(offs_np[nsamp]) / dt1 / 1e9, 3),
+                              "unit": "GB/s", "cores": 1,
+                              "sample": "the first %d files (%d bytes), one thread"
+                                        % (nsamp, int(offs_np[nsamp]))}}
     print(json.dumps(line), flush=True)
 
 
 SERVE_LOADS_GBS = (25, 50, 100, 200)
 
 
-def serve_levels(dev, p, tuning, loads, duration_s=1.0):
+def dedup_savings(dev, backup):
+    """Deduplication savings of the ~1 GiB backup-like stream (64 edited
+    versions of a 16 MiB base) chunked on the GPU at the three settings in
+    both modes: 1 - (bytes of distinct chunks) / (all bytes), chunks told
+    apart by SHA-256 on the host (Eq. 1 of the paper's background)."""
+    import hashlib
+    from concurrent.futures import ThreadPoolExecutor
+    import torch
+    from paper_2505_21194_gb300 import seqcdc
+    stream, _ = backup
+    d = torch.from_numpy(stream).to(dev)
+    mv = memoryview(stream)
+    out = []
+    with ThreadPoolExecutor(os.cpu_count() or 1) as pool:
+        for kib in (4, 8, 16):
+            for mode in (0, 1):
+                p = seqcdc.seqcdc_params(kib, mode)
+                cuts = seqcdc.chunk(d, p).cpu().numpy()
+                starts = np.concatenate([[0], cuts[:-1]])
+                digests = list(pool.map(
+                    lambda ab: hashlib.sha256(mv[ab[0]:ab[1]]).digest(),
+                    zip(starts.tolist(), cuts.tolist()), chunksize=256))
+                seen, unique = set(), 0
+                for (a, b), h in zip(zip(starts.tolist(), cuts.tolist()), digests):
+                    if h not in seen:
+                        seen.add(h)
+                        unique += b - a
+                out.append({"setting_KiB": kib, "mode": "increasing" if mode == 0 else "decreasing",
+                            "chunks": int(cuts.size),
+                            "mean_chunk_B": round(stream.size / max(cuts.size, 1), 1),
+                            "savings": round(1.0 - unique / stream.size, 4)})
+    del d
+    return {"stream": "64 versions of a 16 MiB base, Poisson(200) edits each "
+                      "(%d bytes)" % stream.size, "hash": "SHA-256 (host)", "settings": out}
+
+
+def serve_levels(dev, p, tuning, loads, backup, duration_s=1.0):
     """Open-loop serving at each offered load (GB/s): Poisson arrivals of
     requests drawn from the 64 versions (about 16 MiB each) of the backup-like
     stream, admitted under a 64 GiB HBM budget, batched continuously.  One
@@ -459,7 +514,7 @@ def serve_levels(dev, p, tuning, loads, duration_s=1.0):
     import oracle
     from paper_2505_21194_gb300 import seqcdc, workloads as W
     from paper_2505_21194_gb300.serve import Server, poisson_arrivals
-    stream, voffs = W.backup_stream(SEED)
+    stream, voffs = backup
     voffs = voffs.astype(np.int64)
     sizes = np.diff(voffs)
     pool = torch.from_numpy(stream).pin_memory()
@@ -510,6 +565,8 @@ def main():
                     help="skip the CPU-oracle baseline (profiling runs)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="library default launch tuning instead of the autotuner")
+    ap.add_argument("--no-dedup", action="store_true",
+                    help="skip the deduplication-savings report on the backup-like stream")
     ap.add_argument("--no-serve", action="store_true",
                     help="skip the serving measurement (open-loop Poisson arrivals)")
     ap.add_argument("--nfiles", type=int, default=NFILES,
