@@ -376,6 +376,41 @@ def run_gpu(args):
     # host check of the last result: CSR is consistent
     assert int(h_co[-1]) == ncuts
 
+    # Fingerprinting the batch's chunks (SHA-256 per chunk) and counting the
+    # distinct ones: the step after chunking, on the device.
+    fp = None
+    if not args.no_fingerprint:
+        dig = torch.empty((ncuts, 32), dtype=torch.uint8, device=dev)
+        fsz = torch.empty(ncuts, dtype=torch.int32, device=dev)
+        fa, fb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for _ in range(2):
+            seqcdc.seqcdc_fingerprint_batch(d_data, total, d_offs, nfiles, d_cuts, d_co,
+                                            ncuts, dig, fsz, stream)
+        reps = 5
+        fa.record(stream)
+        for _ in range(reps):
+            seqcdc.seqcdc_fingerprint_batch(d_data, total, d_offs, nfiles, d_cuts, d_co,
+                                            ncuts, dig, fsz, stream)
+        fb.record(stream)
+        torch.cuda.synchronize(dev)
+        fp_ms = fa.elapsed_time(fb) / reps
+        nd, nb = seqcdc.dedup(dig, fsz, stream)
+        # 1 % of the digests against the host's SHA-256
+        import hashlib
+        h_cuts = d_cuts[:ncuts].cpu().numpy()
+        h_co = d_co.cpu().numpy()
+        fidx = np.searchsorted(h_co, np.arange(0, ncuts, 100), side="right") - 1
+        hd = dig[::100].cpu().numpy()
+        bad = 0
+        for j, (i, f) in enumerate(zip(range(0, ncuts, 100), fidx.tolist())):
+            a = int(offs_np[f]) + (int(h_cuts[i - 1]) if i > h_co[f] else 0)
+            b = int(offs_np[f]) + int(h_cuts[i])
+            bad += hd[j].tobytes() != hashlib.sha256(memoryview(data_np)[a:b]).digest()
+        fp = {"kernel": "sha256_chunks_kernel", "chunks": ncuts,
+              "ms": round(fp_ms, 4), "value": round(total / (fp_ms * 1e-3) / 1e9, 2),
+              "unit": "GB/s", "distinct_chunks": nd, "distinct_bytes": nb,
+              "checked_vs_host_sha256": len(hd), "mismatches": int(bad)}
+        del dig, fsz
     peak, peak_kind = _measured_peaks()
     alg_bytes = total + ncuts * 8  # each input byte read once + the cut list
     achieved = alg_bytes / (seg_ms * 1e-3) / 1e9
@@ -426,6 +461,7 @@ def run_gpu(args):
         "graph_captured": ({"ms_per_step": round(graph_ms, 4),
                             "value": round(total * world / (graph_ms * 1e-3) / 1e9, 2)}
                            if graph_ms else None),
+        "fingerprint": fp,
         "gpu_launches": launches_per_step * args.steps,
         "path_stats": path_stats,
         "clocks": clocks,
@@ -470,22 +506,28 @@ SERVE_LOADS_GBS = (25, 50, 100, 200)
 
 def dedup_savings(dev, backup):
     """Deduplication savings of the ~1 GiB backup-like stream (64 edited
-    versions of a 16 MiB base) chunked on the GPU at the three settings in
-    both modes: 1 - (bytes of distinct chunks) / (all bytes), chunks told
-    apart by SHA-256 on the host (Eq. 1 of the paper's background)."""
+    versions of a 16 MiB base) chunked, fingerprinted (SHA-256) and counted
+    on the GPU at the three settings in both modes: 1 - (bytes of distinct
+    chunks) / (all bytes) (Eq. 1); the host's SHA-256 recounts the same
+    chunks as the check."""
     import hashlib
     from concurrent.futures import ThreadPoolExecutor
     import torch
     from paper_2505_21194_gb300 import seqcdc
     stream, _ = backup
     d = torch.from_numpy(stream).to(dev)
+    o = torch.tensor([0, stream.size], dtype=torch.int64, device=dev)
     mv = memoryview(stream)
     out = []
     with ThreadPoolExecutor(os.cpu_count() or 1) as pool:
         for kib in (4, 8, 16):
             for mode in (0, 1):
                 p = seqcdc.seqcdc_params(kib, mode)
-                cuts = seqcdc.chunk(d, p).cpu().numpy()
+                r = seqcdc.chunk_batch(d, o, p)
+                dig, sz = seqcdc.fingerprint(d, o, r)
+                gpu_chunks, gpu_bytes = seqcdc.dedup(dig, sz)
+                cuts = r.cuts.cpu().numpy()
+                del dig, sz, r
                 starts = np.concatenate([[0], cuts[:-1]])
                 digests = list(pool.map(
                     lambda ab: hashlib.sha256(mv[ab[0]:ab[1]]).digest(),
@@ -498,10 +540,15 @@ def dedup_savings(dev, backup):
                 out.append({"setting_KiB": kib, "mode": "increasing" if mode == 0 else "decreasing",
                             "chunks": int(cuts.size),
                             "mean_chunk_B": round(stream.size / max(cuts.size, 1), 1),
-                            "savings": round(1.0 - unique / stream.size, 4)})
+                            "savings": round(1.0 - gpu_bytes / stream.size, 4),
+                            "distinct_chunks": gpu_chunks,
+                            "host_sha256_agrees": bool(gpu_bytes == unique and
+                                                       gpu_chunks == len(seen))})
     del d
     return {"stream": "64 versions of a 16 MiB base, Poisson(200) edits each "
-                      "(%d bytes)" % stream.size, "hash": "SHA-256 (host)", "settings": out}
+                      "(%d bytes)" % stream.size,
+            "hash": "SHA-256 per chunk and distinct-chunk table on the GPU; "
+                    "host SHA-256 (hashlib) as the check", "settings": out}
 
 
 def serve_levels(dev, p, tuning, loads, backup, duration_s=1.0):
@@ -565,6 +612,8 @@ def main():
                     help="skip the CPU-oracle baseline (profiling runs)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="library default launch tuning instead of the autotuner")
+    ap.add_argument("--no-fingerprint", action="store_true",
+                    help="skip SHA-256 fingerprinting of the batch's chunks")
     ap.add_argument("--no-dedup", action="store_true",
                     help="skip the deduplication-savings report on the backup-like stream")
     ap.add_argument("--no-serve", action="store_true",

@@ -220,6 +220,43 @@ int seqcdc_stats(const void *d_ws, void *stream, uint32_t *out, uint32_t n);
  */
 int seqcdc_profile_events(void *ev_begin, void *ev_end);
 
+/*
+ * Fingerprinting and deduplication: the step after chunking (Sec. II).  These
+ * entry points take the output of seqcdc_chunk_batch() (for one stream: one
+ * file, d_offsets = {0, n}, d_cut_offsets = {0, count}).
+ *
+ * seqcdc_fingerprint_batch: SHA-256 (FIPS 180-4) of every chunk.
+ *   d_data, total_bytes, d_offsets, nfiles  as for seqcdc_chunk_batch()
+ *             (d_data 16-byte aligned, nfiles >= 1).
+ *   d_cuts, d_cut_offsets, ncuts  the chunking output; ncuts = the number of
+ *             cuts (d_cut_offsets[nfiles]); chunk i of file f is
+ *             [d_offsets[f] + previous cut of f (or 0), d_offsets[f] + d_cuts[i]).
+ *   d_digests out: 32 bytes per chunk, the digest in its standard byte order
+ *             (4-byte aligned).
+ *   d_sizes   out, optional (NULL): chunk sizes in bytes, one uint32 each.
+ * Asynchronous on `stream`.  SEQCDC_EINVAL for NULL or misaligned pointers,
+ * SEQCDC_ERANGE for 2^32 or more chunks.
+ */
+int seqcdc_fingerprint_batch(const uint8_t *d_data, uint64_t total_bytes,
+                             const uint64_t *d_offsets, uint64_t nfiles,
+                             const uint64_t *d_cuts, const uint64_t *d_cut_offsets,
+                             uint64_t ncuts, uint8_t *d_digests, uint32_t *d_sizes,
+                             void *stream);
+
+/* Bytes of the hash table seqcdc_dedup() needs for `nchunks` chunks. */
+size_t seqcdc_dedup_table_bytes(uint64_t nchunks);
+
+/*
+ * Count the distinct chunks among `nchunks` fingerprints (32-byte digests from
+ * seqcdc_fingerprint_batch, with their sizes): d_out[0] = distinct chunks,
+ * d_out[1] = their bytes (so the savings of Eq. 1 are 1 - d_out[1] / all
+ * bytes).  Chunks with equal digests are the same chunk.  d_table: caller
+ * workspace of >= seqcdc_dedup_table_bytes(nchunks) bytes (4-byte aligned),
+ * no initialisation needed.  Asynchronous on `stream`.
+ */
+int seqcdc_dedup(const uint8_t *d_digests, const uint32_t *d_sizes, uint64_t nchunks,
+                 void *d_table, size_t table_bytes, uint64_t *d_out, void *stream);
+
 /* Static, human-readable text for a status code. */
 const char *seqcdc_strerror(int status);
 

@@ -17,7 +17,7 @@ INCLUDE_DIR = os.path.join(REPO_DIR, "include")
 LIB_DIR = os.path.join(PKG_DIR, "_lib")
 LIB_PATH = os.path.join(LIB_DIR, "libseqcdc.so")
 
-SOURCES = ["seqcdc.cu"]
+SOURCES = ["seqcdc.cu", "fingerprint.cu"]
 ARCH_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -46,12 +46,27 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if not force and not is_stale():
         return LIB_PATH
     os.makedirs(LIB_DIR, exist_ok=True)
-    tmp = LIB_PATH + ".%d.tmp" % os.getpid()
-    cmd = [_nvcc(), *ARCH_FLAGS, "-O3", "-lineinfo", "-std=c++17",
-           "-I" + INCLUDE_DIR, "-shared", "-Xcompiler", "-fPIC",
-           "-o", tmp] + [os.path.join(SRC_DIR, s) for s in SOURCES]
+    nvcc = _nvcc()
+    flags = [*ARCH_FLAGS, "-O3", "-lineinfo", "-std=c++17", "-I" + INCLUDE_DIR,
+             "-Xcompiler", "-fPIC"]
     if verbose:
-        cmd.insert(1, "-Xptxas=-v")
-    subprocess.run(cmd, check=True)
-    os.replace(tmp, LIB_PATH)
+        flags.insert(0, "-Xptxas=-v")
+    # Translation units compile in parallel, then one link.
+    objs, procs = [], []
+    for s in SOURCES:
+        obj = os.path.join(LIB_DIR, s.replace(".cu", ".%d.o" % os.getpid()))
+        objs.append(obj)
+        procs.append(subprocess.Popen([nvcc, *flags, "-c", "-o", obj,
+                                       os.path.join(SRC_DIR, s)]))
+    failed = [p.wait() for p in procs]
+    try:
+        if any(failed):
+            raise subprocess.CalledProcessError(max(failed), "nvcc -c")
+        tmp = LIB_PATH + ".%d.tmp" % os.getpid()
+        subprocess.run([nvcc, *ARCH_FLAGS, "-shared", "-o", tmp, *objs], check=True)
+        os.replace(tmp, LIB_PATH)
+    finally:
+        for o in objs:
+            if os.path.exists(o):
+                os.remove(o)
     return LIB_PATH

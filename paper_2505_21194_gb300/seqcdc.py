@@ -101,6 +101,12 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
         lib.seqcdc_stats.restype = ctypes.c_int
         lib.seqcdc_profile_events.argtypes = [vp, vp]
         lib.seqcdc_profile_events.restype = ctypes.c_int
+        lib.seqcdc_fingerprint_batch.argtypes = [vp, u64, vp, u64, vp, vp, u64, vp, vp, vp]
+        lib.seqcdc_fingerprint_batch.restype = ctypes.c_int
+        lib.seqcdc_dedup_table_bytes.argtypes = [u64]
+        lib.seqcdc_dedup_table_bytes.restype = ctypes.c_size_t
+        lib.seqcdc_dedup.argtypes = [vp, vp, u64, vp, ctypes.c_size_t, vp, vp]
+        lib.seqcdc_dedup.restype = ctypes.c_int
         lib.seqcdc_strerror.argtypes = [ctypes.c_int]
         lib.seqcdc_strerror.restype = ctypes.c_char_p
         _lib = lib
@@ -293,3 +299,52 @@ def chunk_batch(data, offsets, p: Params, tuning=None, stream=None,
         _check(seqcdc_status(ws, stream), "seqcdc_chunk_batch (device)")
     total_cuts = int(cut_offsets[-1].item())
     return BatchResult(cuts[:total_cuts], cut_offsets)
+
+
+# ----------------------------------------------------------------------------
+# Fingerprinting and deduplication (the step after chunking).
+# ----------------------------------------------------------------------------
+def seqcdc_fingerprint_batch(d_data, total_bytes: int, d_offsets, nfiles: int, d_cuts,
+                             d_cut_offsets, ncuts: int, d_digests, d_sizes=None,
+                             stream=None) -> None:
+    """Raw entry point: SHA-256 of every chunk into ``d_digests`` (32 B each)."""
+    _check(load_library().seqcdc_fingerprint_batch(
+        _ptr(d_data), total_bytes, _ptr(d_offsets), nfiles, _ptr(d_cuts),
+        _ptr(d_cut_offsets), ncuts, _ptr(d_digests), _ptr(d_sizes),
+        _stream_handle(stream)), "seqcdc_fingerprint_batch")
+
+
+def seqcdc_dedup_table_bytes(nchunks: int) -> int:
+    return int(load_library().seqcdc_dedup_table_bytes(nchunks))
+
+
+def seqcdc_dedup(d_digests, d_sizes, nchunks: int, d_table, table_bytes: int, d_out,
+                 stream=None) -> None:
+    """Raw entry point: distinct chunks / bytes into ``d_out`` (2 x uint64)."""
+    _check(load_library().seqcdc_dedup(
+        _ptr(d_digests), _ptr(d_sizes), nchunks, _ptr(d_table), table_bytes,
+        _ptr(d_out), _stream_handle(stream)), "seqcdc_dedup")
+
+
+def fingerprint(data, offsets, result: "BatchResult", stream=None):
+    """SHA-256 of every chunk of a chunk_batch() result: (digests uint8 [n, 32],
+    sizes int32 [n]) on the device."""
+    import torch
+    n = result.cuts.numel()
+    dig = torch.empty((max(n, 1), 32), dtype=torch.uint8, device=data.device)
+    sizes = torch.empty(max(n, 1), dtype=torch.int32, device=data.device)
+    seqcdc_fingerprint_batch(data, data.numel(), offsets, offsets.numel() - 1,
+                             result.cuts, result.cut_offsets, n, dig, sizes, stream)
+    return dig[:n], sizes[:n]
+
+
+def dedup(digests, sizes, stream=None):
+    """(distinct chunks, distinct bytes) of fingerprinted chunks (synchronises)."""
+    import torch
+    n = digests.shape[0]
+    tb = seqcdc_dedup_table_bytes(n)
+    table = torch.empty(tb, dtype=torch.uint8, device=digests.device)
+    out = torch.empty(2, dtype=torch.int64, device=digests.device)
+    seqcdc_dedup(digests, sizes, n, table, tb, out, stream)
+    c, b = out.cpu().tolist()
+    return int(c), int(b)
