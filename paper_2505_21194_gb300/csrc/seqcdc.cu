@@ -946,25 +946,31 @@ struct ResShared {
   uint64_t p_s, q_s;
 };
 
-// Exit of `item` from entry position y (file-relative), from its table; kBad
-// when y is not a tabulated entry or its chain escapes.  One lane.
-__device__ uint64_t exit_of(const WsPtrs &ws, const ResShared &r, uint64_t y,
-                           uint32_t kMaxCand) {
-  if (y >= r.q_s) return y;
-  if (r.nc == kAbnormal || y < r.p_s) return kBad;
+// Index of the entry at y (file-relative) among the item's tabulated
+// entries (positions staged in shared memory), or -1.
+__device__ __forceinline__ int entry_index(const ResShared &r, const uint32_t *spos,
+                                           uint64_t y) {
+  if (r.nc == kAbnormal || y < r.p_s || y >= r.q_s) return -1;
   const uint32_t want = (uint32_t)(y - r.p_s);
-  const uint32_t *gpos = ws.cand_pos + (uint64_t)r.item * kMaxCand;
   uint32_t lo = 0, hi = r.nent;
   while (lo < hi) {
     const uint32_t mid = (lo + hi) >> 1;
-    const uint32_t v = gpos[mid];
-    if (v == want) {
-      const uint32_t t = ws.ent_term[(uint64_t)r.item * kMaxCand + mid];
-      return t == kEscape ? kBad : r.p_s + t;
-    }
+    const uint32_t v = spos[mid];
+    if (v == want) return (int)mid;
     if (v < want) lo = mid + 1; else hi = mid;
   }
-  return kBad;
+  return -1;
+}
+
+// Exit of `item` from entry position y (file-relative), from its table; kBad
+// when y is not a tabulated entry or its chain escapes.  One lane.
+__device__ uint64_t exit_of(const WsPtrs &ws, const ResShared &r, const uint32_t *spos,
+                           uint64_t y, uint32_t kMaxCand) {
+  if (y >= r.q_s) return y;
+  const int k = entry_index(r, spos, y);
+  if (k < 0) return kBad;
+  const uint32_t t = ws.ent_term[(uint64_t)r.item * kMaxCand + k];
+  return t == kEscape ? kBad : r.p_s + t;
 }
 
 // True entry by decoupled look-back (one warp).  Going back from item-1, each
@@ -1064,6 +1070,10 @@ __device__ uint64_t lookback(const ResShared &r, const WsPtrs &ws) {
 __global__ void __launch_bounds__(32)
 resolve_kernel(Geom g, WsPtrs ws) {
   __shared__ ResShared r;
+  // The item's candidate positions and links, staged by the warp with
+  // coalesced loads: entry lookups and the walk along the links then read
+  // shared memory instead of one dependent global load per cut.
+  extern __shared__ uint32_t rstage[];  // [cap] positions, [cap] links
   const uint32_t kMaxCand = g.cap;
   const int lane = threadIdx.x;
   uint32_t tk = 0;
@@ -1087,6 +1097,17 @@ resolve_kernel(Geom g, WsPtrs ws) {
   __syncwarp();
   const uint32_t item = r.item;
   if (item >= ws.hdr->nitems) return;
+  uint32_t *spos = rstage, *snxt = rstage + kMaxCand;
+  {
+    const uint32_t ncs = r.nc == kAbnormal ? 0u : r.nc;
+    const uint32_t *gpos = ws.cand_pos + (uint64_t)item * kMaxCand;
+    const uint32_t *gnxt = ws.cand_nxt + (uint64_t)item * kMaxCand;
+    for (uint32_t j = lane; j < ncs; j += 32) {
+      spos[j] = __ldcg(gpos + j);
+      snxt[j] = __ldcg(gnxt + j);
+    }
+    __syncwarp();
+  }
   uint64_t x = 0;
   if (r.seg > 0) {
     // The map from the predecessor's image to this item's exits.
@@ -1095,7 +1116,7 @@ resolve_kernel(Geom g, WsPtrs ws) {
     const uint32_t n = ok ? ws.img_n[item - 1] : 0u;
     if (lane < (int)n) {
       const uint64_t y = ws.img[(uint64_t)(item - 1) * kMaxImage + lane];
-      ws.agg[(uint64_t)item * kMaxImage + lane] = exit_of(ws, r, y, g.cap);
+      ws.agg[(uint64_t)item * kMaxImage + lane] = exit_of(ws, r, spos, y, g.cap);
     }
     __syncwarp();
     if (lane == 0) {
@@ -1118,30 +1139,18 @@ resolve_kernel(Geom g, WsPtrs ws) {
       exit_pos = x;  // the entry lies past the item: no cut inside it
       done = true;
     } else if (r.nc != kAbnormal) {
-      const uint32_t *gpos = ws.cand_pos + (uint64_t)item * kMaxCand;
-      const uint32_t *gnxt = ws.cand_nxt + (uint64_t)item * kMaxCand;
-      int k = -1;
-      if (x != kBad && x >= r.p_s) {
-        const uint32_t want = (uint32_t)(x - r.p_s);
-        uint32_t lo = 0, hi = r.nent;
-        while (lo < hi) {
-          const uint32_t mid = (lo + hi) >> 1;
-          const uint32_t v = gpos[mid];
-          if (v == want) { k = (int)mid; break; }
-          if (v < want) lo = mid + 1; else hi = mid;
-        }
-      }
+      int k = x != kBad ? entry_index(r, spos, x) : -1;
       const bool guess = k < 0 && r.nent > 0;
       if (guess) {
         k = 0;
-        entry = r.p_s + gpos[0];
+        entry = r.p_s + spos[0];
       }
       if (k >= 0) {
-        uint32_t code = gnxt[k];
+        uint32_t code = snxt[k];
         while (!(code & kTerminal) && nout < ws.slot_cap) {
           if (code >= r.nc) { code = kEscape; break; }  // never: codes are checked when made
-          out[nout++] = r.p_s + gpos[code];
-          code = gnxt[code];
+          out[nout++] = r.p_s + spos[code];
+          code = snxt[code];
         }
         if (code != kEscape && nout < ws.slot_cap) {
           exit_pos = r.p_s + (code & ~kTerminal);
@@ -1539,6 +1548,21 @@ bool smem_configured(uint32_t threads, size_t smem,
   return true;
 }
 
+// The same for the resolve kernel's staging area (segments over 768 KiB).
+bool resolve_smem_configured(size_t smem) {
+  static std::mutex mu;
+  static size_t done[kMaxDevices] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return false;
+  std::lock_guard<std::mutex> lock(mu);
+  if (done[dev] >= smem) return true;
+  if (cudaFuncSetAttribute(resolve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem) != cudaSuccess)
+    return false;
+  done[dev] = smem;
+  return true;
+}
+
 int run(const seqcdc_params_t *p, const uint8_t *d_data, uint64_t total,
         const uint64_t *d_offsets, uint64_t nfiles, uint64_t *d_cuts,
         uint64_t cap, uint64_t *d_cut_offsets, uint64_t *d_count, void *d_ws,
@@ -1571,7 +1595,9 @@ int run(const seqcdc_params_t *p, const uint8_t *d_data, uint64_t total,
   if (g_prof_begin) cudaEventRecord(g_prof_begin, st);
   map_fn<<<(unsigned)l.imax, threads, smem, st>>>(g, dp, w);
   if (g_prof_end) cudaEventRecord(g_prof_end, st);
-  resolve_kernel<<<(unsigned)l.imax, 32, 0, st>>>(g, w);
+  const size_t rsmem = 2 * sizeof(uint32_t) * cand_cap(L);
+  if (rsmem > 48 * 1024 && !resolve_smem_configured(rsmem)) return SEQCDC_ECUDA;
+  resolve_kernel<<<(unsigned)l.imax, 32, rsmem, st>>>(g, w);
   const uint64_t vblocks = (l.imax + 255) / 256;
   const unsigned vgrid = (unsigned)(vblocks < 4096 ? vblocks : 4096);
   const unsigned rgrid = (unsigned)(l.imax < 2u * (uint64_t)sms ? l.imax : 2u * (uint64_t)sms);
