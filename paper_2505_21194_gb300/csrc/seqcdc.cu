@@ -591,9 +591,26 @@ __device__ __forceinline__ void classify32(uint4 v0, uint4 v1, uint32_t prev_byt
 // E at position t needs T at t, t-1, ..., t-(R-2); `pt` holds the T bits of
 // the 32 positions before.
 __device__ __forceinline__ uint32_t run_ends(uint32_t pt, uint32_t T, uint32_t R) {
+  if (R == 5)  // the paper's SeqLength at every setting (Table I)
+    return T & __funnelshift_l(pt, T, 1) & __funnelshift_l(pt, T, 2) &
+           __funnelshift_l(pt, T, 3);
   uint32_t ew = T;
   for (uint32_t k = 1; k + 1 < R; ++k) ew &= __funnelshift_l(pt, T, k);
   return ew;
+}
+
+// T bits (bits 16..31) of the 16 positions of v, whose first byte's
+// predecessor is taken as equal to it (bit 16 is then 0; callers use only the
+// top SeqLength-2 bits).
+__device__ __forceinline__ uint32_t classify16_T(uint4 v, uint32_t mode) {
+  uint32_t g0, l0, g1, l1, g2, l2, g3, l3;
+  cmp_word(v.x, (v.x << 8) | (v.x & 0xffu), g0, l0);
+  cmp_word(v.y, __funnelshift_l(v.x, v.y, 8), g1, l1);
+  cmp_word(v.z, __funnelshift_l(v.y, v.z, 8), g2, l2);
+  cmp_word(v.w, __funnelshift_l(v.z, v.w, 8), g3, l3);
+  const uint32_t up = gather8(g0, g1) | (gather8(g2, g3) << 8);
+  const uint32_t dn = gather8(l0, l1) | (gather8(l2, l3) << 8);
+  return (mode == 0 ? up : dn) << 16;
 }
 
 // The natural cuts an item tabulates: run ends e in [lo, hi) give cut e + 1
@@ -642,9 +659,7 @@ __device__ __forceinline__ CandCount seg_bitmaps(const SegGeom &gm, const Geom &
     // T bits of the 16 positions before this warp's first word (only the top
     // SeqLength-2 of them matter, so the unknown byte before them is moot).
     const uint4 pv = load16(base, gwin + 32 * (int64_t)w0 - 16, g.total);
-    uint32_t Tp, Op;
-    classify32(make_uint4(0, 0, 0, 0), pv, 0, p.mode, Tp, Op);
-    carry_T = Tp;  // the top 16 bits are the 16 positions before this word
+    carry_T = classify16_T(pv, p.mode);  // top 16 bits: the 16 positions before this word
     carry_byte = pv.w >> 24;
   }
   uint32_t cE = 0;  // E bits so far in this warp's words
@@ -743,12 +758,15 @@ __device__ __forceinline__ CandCount seg_bitmaps(const SegGeom &gm, const Geom &
       if (cr.lo > bw) v &= ~0u << (cr.lo - bw);
       if (cr.hi - bw < 32) v &= (1u << (cr.hi - bw)) - 1u;
       if (v) {
+        uint32_t b = __ffs(v) - 1;
         uint32_t idx = cr.first + m.sbE[w >> 6] + m.locE[w] - cc.elo +
-                       __popc(ew & ((1u << (__ffs(v) - 1)) - 1u));
-        while (v) {
-          const uint32_t b = __ffs(v) - 1;
+                       __popc(ew & ((1u << b) - 1u));
+        m.cpos[idx] = bw + b + 1;
+        v &= v - 1;
+        while (v) {  // words with two or more run ends are the rare case
+          b = __ffs(v) - 1;
           v &= v - 1;
-          m.cpos[idx++] = bw + b + 1;
+          m.cpos[++idx] = bw + b + 1;
         }
       }
     }
