@@ -9,8 +9,10 @@
  * constants (Sec. 4.2.2, Sec. 5.3.3) are derived here from the first primes
  * with exact integer roots instead of being listed.
  *
- * One thread hashes one chunk: the 64-byte blocks of a chunk are sequential
- * by definition, and a batch holds far more chunks than the GPU has lanes.
+ * A thread hashes whole chunks (the 64-byte blocks of a chunk are sequential
+ * by definition, and a batch holds far more chunks than the GPU has lanes),
+ * several in a row, one block per iteration, so the lanes of a warp stay busy
+ * whatever the chunk sizes.
  */
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -127,57 +129,87 @@ __device__ __forceinline__ void chunk_range(const uint64_t *offsets, uint64_t nf
   b = fbase + cuts[i];
 }
 
-__global__ void __launch_bounds__(128)
-sha256_chunks_kernel(const uint8_t *data, uint64_t total, const uint64_t *offsets,
-                     uint64_t nfiles, const uint64_t *cuts, const uint64_t *cut_offsets,
-                     uint64_t ncuts, uint32_t *digests, uint32_t *sizes) {
+// Pass 1: the byte range [a, b) of every chunk, parked in the first 16 bytes
+// of the chunk's digest slot (pass 2 reads it before it writes the digest).
+__global__ void chunk_ranges_kernel(const uint64_t *offsets, uint64_t nfiles,
+                                    const uint64_t *cuts, const uint64_t *cut_offsets,
+                                    uint64_t ncuts, uint32_t *digests) {
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < ncuts;
        i += (uint64_t)gridDim.x * blockDim.x) {
     uint64_t a, b;
     chunk_range(offsets, nfiles, cuts, cut_offsets, i, a, b);
-    uint32_t h[8];
+    reinterpret_cast<ulonglong2 *>(digests)[2 * i] = make_ulonglong2(a, b);
+  }
+}
+
+// Block `off` (a multiple of 64) of the padded message of the chunk at
+// [a, a + len): data bytes, the 0x80 marker, zeros, and in the last block the
+// bit length (Sec. 5.1.1).  Whole data blocks come from 16 or 17 aligned
+// words funnel-shifted to the chunk's byte offset.
+__device__ __forceinline__ void message_block(const uint8_t *data, uint64_t total,
+                                              uint64_t a, uint64_t len, uint64_t off,
+                                              uint64_t padded, uint32_t w[16]) {
+  if (off + 64 <= len) {
+    const uint64_t q = a + off;
+    const uint64_t q4 = q & ~3ull;
+    const int sh = (int)(q & 3) * 8;
+    uint32_t v[17];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) h[j] = c_H0[j];
-    uint64_t q = a;
-    const int sh = (int)(a & 3) * 8;
-    // Whole blocks: 16 (or 17) aligned words, funnel-shifted to the chunk's
-    // byte offset.
-    while (q + 64 <= b) {
-      const uint64_t q4 = q & ~3ull;
-      uint32_t v[17];
+    for (int j = 0; j < 16; ++j) v[j] = __ldg(reinterpret_cast<const uint32_t *>(data + q4) + j);
+    v[16] = sh ? word_at(data, q4 + 64, total) : 0u;
 #pragma unroll
-      for (int j = 0; j < 16; ++j) v[j] = __ldg(reinterpret_cast<const uint32_t *>(data + q4) + j);
-      v[16] = sh ? word_at(data, q4 + 64, total) : 0u;
-      uint32_t w[16];
+    for (int j = 0; j < 16; ++j) w[j] = bswap(__funnelshift_r(v[j], v[j + 1], sh));
+    return;
+  }
 #pragma unroll
-      for (int j = 0; j < 16; ++j) w[j] = bswap(__funnelshift_r(v[j], v[j + 1], sh));
-      compress(h, w);
-      q += 64;
-    }
-    // The rest, the 0x80 marker, zeros and the bit length (Sec. 5.1.1): one
-    // block if the rest leaves room for the 9 bytes, else two.
-    const uint32_t rem = (uint32_t)(b - q);
-    const uint64_t bits = (b - a) * 8;
-    uint32_t w[16];
+  for (int j = 0; j < 16; ++j) w[j] = 0;
 #pragma unroll
-    for (int j = 0; j < 16; ++j) w[j] = 0;
-#pragma unroll
-    for (int j = 0; j < 64; ++j) {
-      const uint32_t byte = (uint32_t)j < rem ? data[q + j] : ((uint32_t)j == rem ? 0x80u : 0u);
-      w[j >> 2] |= byte << (24 - 8 * (j & 3));
-    }
-    if (rem + 9 > 64) {
-      compress(h, w);
-#pragma unroll
-      for (int j = 0; j < 16; ++j) w[j] = 0;
-    }
+  for (int j = 0; j < 64; ++j) {
+    const uint64_t pos = off + j;
+    const uint32_t byte = pos < len ? data[a + pos] : (pos == len ? 0x80u : 0u);
+    w[j >> 2] |= byte << (24 - 8 * (j & 3));
+  }
+  if (off + 64 == padded) {
+    const uint64_t bits = len * 8;
     w[14] = (uint32_t)(bits >> 32);
     w[15] = (uint32_t)bits;
-    compress(h, w);
-    uint32_t *out = digests + i * 8;
+  }
+}
+
+// Pass 2: every thread hashes the chunks t, t + G, t + 2G, ... (G threads in
+// the grid), one 64-byte block per iteration, so that a lane that finishes a
+// chunk goes on with its next one while the rest of its warp is still
+// hashing: with about ten chunks per thread the per-lane totals even out.
+__global__ void __launch_bounds__(128)
+sha256_chunks_kernel(const uint8_t *data, uint64_t total, uint64_t ncuts,
+                     uint32_t *digests, uint32_t *sizes) {
+  const uint64_t G = (uint64_t)gridDim.x * blockDim.x;
+  uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  uint64_t a = 0, len = 0, off = 0, padded = 0;
+  uint32_t h[8];
+  auto start = [&](uint64_t k) {
+    const ulonglong2 r = reinterpret_cast<const ulonglong2 *>(digests)[2 * k];
+    a = r.x;
+    len = r.y - r.x;
+    off = 0;
+    padded = ((len + 8) / 64 + 1) * 64;
 #pragma unroll
-    for (int j = 0; j < 8; ++j) out[j] = bswap(h[j]);  // bytes in digest order
-    if (sizes) sizes[i] = (uint32_t)(b - a);
+    for (int j = 0; j < 8; ++j) h[j] = c_H0[j];
+  };
+  if (i < ncuts) start(i);
+  while (i < ncuts) {
+    uint32_t w[16];
+    message_block(data, total, a, len, off, padded, w);
+    compress(h, w);
+    off += 64;
+    if (off == padded) {
+      uint32_t *out = digests + i * 8;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) out[j] = bswap(h[j]);  // bytes in digest order
+      if (sizes) sizes[i] = (uint32_t)len;
+      i += G;
+      if (i < ncuts) start(i);
+    }
   }
 }
 
@@ -232,11 +264,22 @@ int seqcdc_fingerprint_batch(const uint8_t *d_data, uint64_t total_bytes,
     return SEQCDC_EINVAL;
   if (ncuts >= 0xffffffffull) return SEQCDC_ERANGE;
   if (!constants_ready()) return SEQCDC_ECUDA;
-  const uint64_t blocks = (ncuts + 127) / 128;
-  sha256_chunks_kernel<<<(unsigned)(blocks < 65535u * 8 ? blocks : 65535u * 8), 128, 0,
-                         static_cast<cudaStream_t>(stream)>>>(
-      d_data, total_bytes, d_offsets, nfiles, d_cuts, d_cut_offsets, ncuts,
-      reinterpret_cast<uint32_t *>(d_digests), d_sizes);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  uint32_t *dig = reinterpret_cast<uint32_t *>(d_digests);
+  const uint64_t blocks = (ncuts + 255) / 256;
+  chunk_ranges_kernel<<<(unsigned)(blocks < 65535u * 8 ? blocks : 65535u * 8), 256, 0, st>>>(
+      d_offsets, nfiles, d_cuts, d_cut_offsets, ncuts, dig);
+  // Persistent grid: as many 128-thread blocks as are resident at once.
+  int dev = 0, sms = 0, per_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sha256_chunks_kernel, 128, 0) !=
+          cudaSuccess)
+    return SEQCDC_ECUDA;
+  uint64_t grid = (uint64_t)sms * (uint64_t)(per_sm > 0 ? per_sm : 1);
+  const uint64_t need = (ncuts + 127) / 128;
+  if (grid > need) grid = need;
+  sha256_chunks_kernel<<<(unsigned)grid, 128, 0, st>>>(d_data, total_bytes, ncuts, dig, d_sizes);
   return cudaGetLastError() == cudaSuccess ? SEQCDC_OK : SEQCDC_ECUDA;
 }
 

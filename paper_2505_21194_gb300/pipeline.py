@@ -1,0 +1,195 @@
+"""Chunking of host-resident data with the copies overlapped.
+
+``chunk_batch_host`` takes a CSR batch in pinned host memory, splits it into
+pieces of whole files, and pipelines each piece through a copy stream (host to
+device), a compute stream (``seqcdc_chunk_batch``) and back (cut lists to
+pinned host memory), with a few device slots in rotation: while piece k is
+chunked, piece k+1 is copied in and the cut lists of piece k-1 are copied
+out.  Files are chunked independently, so the pieces are too.
+
+``chunk_stream_host`` chunks one long stream delivered as host blocks of any
+size (more than fits on the device, if need be).  A chunk depends only on
+bytes from its start to start + max_size, so every cut of a prefix except its
+last is a cut of the whole stream (Sec. IV: a forced cut at the end of the
+input is the only cut the end decides).  Each block is chunked together with
+the bytes after the previous block's last proven cut; the final cut of the
+last block is the stream end.
+
+All chunking runs in the library's CUDA kernels; this module moves bytes and
+orders streams.
+"""
+from __future__ import annotations
+
+from typing import Iterable, Iterator, List, Optional, Tuple
+
+import numpy as np
+
+from . import seqcdc
+
+
+def split_files(offsets: np.ndarray, pieces: int) -> List[Tuple[int, int]]:
+    """File ranges [a, b) of about equal bytes; every piece has a file
+    (unless there are fewer files than pieces), a file is never split."""
+    offs = np.asarray(offsets, dtype=np.int64)
+    nfiles = offs.size - 1
+    if nfiles <= 0:
+        return []
+    pieces = max(1, min(pieces, nfiles))
+    total = int(offs[-1])
+    out, a = [], 0
+    for k in range(1, pieces + 1):
+        if a >= nfiles:
+            break
+        target = total * k // pieces
+        b = int(np.searchsorted(offs, target, side="left"))
+        b = max(a + 1, min(b, nfiles))
+        if k == pieces:
+            b = nfiles
+        out.append((a, b))
+        a = b
+    return out
+
+
+class _Slot:
+    def __init__(self, torch, dev, p, max_bytes, max_files, tuning):
+        self.max_bytes, self.max_files = max_bytes, max_files
+        self.cap = max_bytes // p.min_size + max_files
+        self.data = torch.empty(max(max_bytes, 16), dtype=torch.uint8, device=dev)
+        self.offs = torch.empty(max_files + 1, dtype=torch.int64, device=dev)
+        self.cuts = torch.empty(max(self.cap, 1), dtype=torch.int64, device=dev)
+        self.co = torch.empty(max_files + 1, dtype=torch.int64, device=dev)
+        self.ws_bytes = seqcdc.seqcdc_workspace_size(p, max_bytes, max_files, tuning)
+        self.ws = torch.empty(self.ws_bytes, dtype=torch.uint8, device=dev)
+        self.free = None  # event: the slot's last use is over
+
+
+class HostBatchPipeline:
+    """Reusable pipeline for CSR batches in pinned host memory: device slots,
+    streams and pinned staging are kept between calls (they grow when a
+    larger piece comes), so a steady stream of batches allocates nothing."""
+
+    def __init__(self, p, tuning=None, device="cuda", slots: int = 3):
+        import torch
+        self.torch = torch
+        self.p, self.tuning, self.nslots = p, tuning, max(1, slots)
+        self.dev = torch.device(device)
+        self.copy_in = torch.cuda.Stream(self.dev)
+        self.compute = torch.cuda.Stream(self.dev)
+        self.copy_out = torch.cuda.Stream(self.dev)
+        self.pool: List[_Slot] = []
+        self.h_cuts, self.h_co, self.h_rel = [], [], []
+        self.h_status = None
+
+    def _pinned(self, lst, k, n):
+        torch = self.torch
+        while len(lst) <= k:
+            lst.append(None)
+        if lst[k] is None or lst[k].numel() < n:
+            lst[k] = torch.empty(max(n, 1), dtype=torch.int64, pin_memory=True)
+        return lst[k]
+
+    def _slots(self, max_bytes, max_files, n):
+        if any(s.max_bytes < max_bytes or s.max_files < max_files for s in self.pool):
+            self.pool = []
+        while len(self.pool) < min(self.nslots, n):
+            self.pool.append(_Slot(self.torch, self.dev, self.p, max_bytes, max_files,
+                                   self.tuning))
+        for s in self.pool:
+            s.free = None
+
+    def run(self, h_data, h_offsets, pieces: int = 16):
+        """(cuts int64, cut_offsets int64) on the host, equal to
+        ``chunk_batch`` of the same batch on the device."""
+        torch, p, tuning = self.torch, self.p, self.tuning
+        offs = np.asarray(h_offsets.numpy() if hasattr(h_offsets, "numpy") else h_offsets,
+                          dtype=np.int64)
+        nfiles = offs.size - 1
+        ranges = split_files(offs, pieces)
+        if not ranges:
+            return np.empty(0, np.int64), np.zeros(max(nfiles + 1, 1), np.int64)
+        self._slots(max(int(offs[b] - offs[a]) for a, b in ranges),
+                    max(b - a for a, b in ranges), len(ranges))
+        if self.h_status is None or self.h_status.numel() < len(ranges):
+            self.h_status = torch.empty(len(ranges), dtype=torch.int32, pin_memory=True)
+        caps = []
+        for k, (a, b) in enumerate(ranges):
+            rel = self._pinned(self.h_rel, k, b - a + 1)
+            rel[:b - a + 1].copy_(torch.from_numpy(offs[a:b + 1] - offs[a]))
+            caps.append(int(offs[b] - offs[a]) // p.min_size + (b - a))
+            self._pinned(self.h_cuts, k, caps[-1])
+            self._pinned(self.h_co, k, b - a + 1)
+        done = []
+        for k, (a, b) in enumerate(ranges):
+            s = self.pool[k % len(self.pool)]
+            n = int(offs[b] - offs[a])
+            if s.free is not None:
+                self.copy_in.wait_event(s.free)
+            with torch.cuda.stream(self.copy_in):
+                s.data[:n].copy_(h_data[int(offs[a]):int(offs[b])], non_blocking=True)
+                s.offs[:b - a + 1].copy_(self.h_rel[k][:b - a + 1], non_blocking=True)
+                loaded = torch.cuda.Event()
+                loaded.record(self.copy_in)
+            self.compute.wait_event(loaded)
+            cap = caps[k]
+            seqcdc.seqcdc_chunk_batch(p, s.data, n, s.offs, b - a, s.cuts, cap, s.co,
+                                      s.ws, s.ws_bytes, tuning, self.compute)
+            chunked = torch.cuda.Event()
+            chunked.record(self.compute)
+            self.copy_out.wait_event(chunked)
+            with torch.cuda.stream(self.copy_out):
+                self.h_co[k][:b - a + 1].copy_(s.co[:b - a + 1], non_blocking=True)
+                self.h_cuts[k][:cap].copy_(s.cuts[:cap], non_blocking=True)
+                # the piece's device status word (first field of the workspace)
+                self.h_status[k:k + 1].copy_(s.ws[:4].view(torch.int32), non_blocking=True)
+                s.free = torch.cuda.Event()
+                s.free.record(self.copy_out)
+            done.append(s.free)
+        for e in done:
+            e.synchronize()
+        bad = [int(x) for x in self.h_status[:len(ranges)].numpy() if x != seqcdc.SEQCDC_OK]
+        if bad:
+            raise seqcdc.SeqCDCError(bad[0], "chunk_batch_host (device)")
+        parts, co_parts, base = [], [np.zeros(1, np.int64)], 0
+        for k, (a, b) in enumerate(ranges):
+            co = self.h_co[k][:b - a + 1].numpy()
+            parts.append(self.h_cuts[k][:int(co[-1])].numpy().copy())
+            co_parts.append(co[1:] + base)
+            base += int(co[-1])
+        return np.concatenate(parts), np.concatenate(co_parts)
+
+
+def chunk_batch_host(h_data, h_offsets, p, pieces: int = 16, slots: int = 3,
+                     tuning=None, device="cuda"):
+    """One-off use of ``HostBatchPipeline``: chunk a CSR batch held in pinned
+    host memory; returns host (cuts int64, cut_offsets int64)."""
+    return HostBatchPipeline(p, tuning, device, slots).run(h_data, h_offsets, pieces)
+
+
+def chunk_stream_host(blocks: Iterable[np.ndarray], p, tuning=None,
+                      device="cuda") -> Iterator[np.ndarray]:
+    """Chunk one stream given as host blocks (any sizes); yields the absolute
+    cut offsets block by block (their concatenation is the stream's cut
+    list).  The device holds one block plus the carried tail at a time."""
+    import torch
+    dev = torch.device(device)
+    carry = np.empty(0, dtype=np.uint8)
+    base = 0
+    for blk in blocks:
+        blk = np.asarray(blk, dtype=np.uint8)
+        buf = np.concatenate([carry, blk]) if carry.size else blk
+        if buf.size == 0:
+            continue
+        d = torch.from_numpy(buf).to(dev)
+        cuts = seqcdc.chunk(d, p, tuning).cpu().numpy()
+        del d
+        if cuts.size > 1:
+            keep = cuts[:-1]
+            yield keep + base
+            last = int(keep[-1])
+            carry = buf[last:].copy()
+            base += last
+        else:
+            carry = buf.copy()
+    if carry.size:
+        d = torch.from_numpy(carry).to(dev)
+        yield seqcdc.chunk(d, p, tuning).cpu().numpy() + base
