@@ -503,6 +503,7 @@ def run_gpu(args):
         line["serve"] = serve_levels(dev, p, tuning, SERVE_LOADS_GBS, backup)
     if not args.no_dedup:
         line["dedup"] = dedup_savings(dev, backup)
+        line["sweep"] = sweep_report(dev, backup)
     if world == 1 and not args.no_cpu:
         threads = os.cpu_count() or 1
         dt, _ = cpu_oracle_pass(data_np, offs_np, threads)
@@ -531,6 +532,30 @@ def run_gpu(args):
 
 
 SERVE_LOADS_GBS = (25, 50, 100, 200)
+
+
+def sweep_report(dev, backup):
+    """Mean chunk size at Table I's settings on uniform random bytes and on
+    the backup-like stream: as read here (a run of SeqLength bytes), with one
+    more byte per run (the other reading), and without skipping (BASE)."""
+    import torch
+    from paper_2505_21194_gb300 import workloads as W
+    from paper_2505_21194_gb300.sweep import sweep, table1_settings
+    out = {}
+    samples = (("uniform_random_256MiB", W.uniform_random(256 << 20, SEED + 7)),
+               ("backup_stream_1GiB", backup[0]))
+    for name, arr in samples:
+        d = torch.from_numpy(arr).to(dev)
+        rows = []
+        for label, sets in (("seq_length", table1_settings()),
+                            ("seq_length+1", table1_settings(extra_run_byte=True)),
+                            ("no_skipping", table1_settings(base=True))):
+            for kib, r in zip((4, 8, 16), sweep(d, sets)):
+                rows.append({"setting_KiB": kib, "variant": label,
+                             "mean_bytes": r["mean_bytes"], "at_max": r["at_max"]})
+        out[name] = rows
+        del d
+    return out
 
 
 def dedup_savings(dev, backup):
