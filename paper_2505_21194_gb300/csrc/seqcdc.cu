@@ -129,9 +129,11 @@ struct Geom {
   uint32_t cap;             // natural cuts tabulated per item (L / 64)
 };
 
-// Natural cuts tabulated per item: one per 64 bytes, twice the density of
-// uniform random or text input (about one per 126 bytes at SeqLength 5).
-__host__ __device__ inline uint32_t cand_cap(uint32_t L) { return L / 64 < 256 ? 256 : L / 64; }
+// Natural cuts tabulated per item: one per 96 bytes.  Uniform random input
+// has one per ~125 bytes at SeqLength 5 (526 +- 26 per 64 KiB; the
+// benchmark's 10,000 files reach at most 630 per 64 KiB item); an item with
+// more goes to the repair pass.
+__host__ __device__ inline uint32_t cand_cap(uint32_t L) { return L / 96 < 256 ? 256 : L / 96; }
 
 __host__ __device__ inline uint64_t file_start(const Geom &g, uint64_t f) {
   return g.offsets ? g.offsets[f] : 0;
@@ -253,39 +255,47 @@ __device__ uint32_t block_excl_scan(uint32_t v, uint32_t *scratch,
 // ---------------------------------------------------------------------------
 // Bitmaps of one item in shared memory.  Positions are relative to the window
 // base B (file-relative): rel = pos - B; word w covers rel 32w .. 32w+31.
-//   E, O   run-end and opposing-pair bits (O padded to whole 16-byte groups)
+//   E, O   run-end and opposing-pair bits
 //   nz     bit w of the mask: E[w] != 0
-//   sbE    sbE[s]: E bits in the words before step s (64 words per step)
-//   locE   locE[w]: E bits in the words of w's step before w
+//   sbE, sbO  E and O bits in the words before each step of 64 words
+//   locO   O bits in the words of w's step before w
 // A scan-region query (Sec. III.D: first set bit of the combined run mask;
-// position of the SkipTrigger-th opposing pair) is a short walk over these.
+// position of the SkipTrigger-th opposing pair) is a few lookups: the first
+// run end from the nonzero mask, the opposing pairs before it from the O
+// counts, and, when there are SkipTrigger of them, their position by a
+// binary search over the counts of the words in between.
 // ---------------------------------------------------------------------------
 struct Bits {
   const uint32_t *E;
   const uint32_t *O;
   const uint32_t *nz;
+  const uint32_t *sbO;
+  const uint16_t *locO;
   uint32_t W;
 };
+
+// O bits in the words before w.
+__device__ __forceinline__ uint32_t o_before_word(const Bits &b, uint32_t w) {
+  return b.sbO[w >> 6] + b.locO[w];
+}
+
+// O bits at rel positions before x (x < 32 W).
+__device__ __forceinline__ uint32_t o_before(const Bits &b, uint32_t x) {
+  const uint32_t w = x >> 5;
+  return o_before_word(b, w) + __popc(b.O[w] & ((1u << (x & 31)) - 1u));
+}
 
 // One scan region of the chunker (Sec. III.A-C) from scan position i with
 // chunk limit lim: returns the cut (run end + 1 when a run completes before
 // the SkipTrigger-th opposing pair; lim when the chunk reaches its maximum
 // size or the input end), or kNone after moving i past a content-defined skip.
-// The first run end e at or after i + SeqLength - 1 comes from the nonzero
-// mask; then the opposing pairs in [i + 1, e) are counted four words at a
-// time: the SkipTrigger-th of them, if any, is the skip point.  Every index
-// is clamped into the window, so lanes without work (lim = 0, result lim) run
-// the same instructions.
+// Every index is clamped into the window, so lanes without work (lim = 0,
+// result lim) run the same instructions.
 __device__ __forceinline__ uint32_t region_step(const Bits &b, const DevParams &p,
                                                 uint32_t &i, uint32_t lim) {
   const uint32_t Wm1 = b.W - 1;
   const bool open = i + 1 < lim;
-  const uint32_t x = i + 1;
-  const uint32_t w0 = min(x >> 5, Wm1);
-  uint32_t g = w0 & ~3u;
-  // First group of O words, loaded before the run-end search so that the two
-  // overlap.
-  uint4 v = *reinterpret_cast<const uint4 *>(b.O + g);
+  // e: the first E bit at or after i + SeqLength - 1, if below lim.
   uint32_t e = kNone;
   {
     const uint32_t xs = i + p.R - 1;
@@ -311,39 +321,22 @@ __device__ __forceinline__ uint32_t region_step(const Bits &b, const DevParams &
   // No run end before lim: no later region can cut either.
   if (!open || e == kNone) return lim;  // maximum size or end of input (Sec. IV)
   if (p.T == 0) return e + 1;           // skipping disabled
-  // The SkipTrigger-th O bit in [x, e), if there is one, is the skip point.
-  const uint32_t we = e >> 5;
-  const uint32_t lo_bits = ~0u << (x & 31);
-  const uint32_t hi_bits = (1u << (e & 31)) - 1u;
-  uint32_t need = p.T;
-  while (true) {
-    uint32_t m[4] = {v.x, v.y, v.z, v.w};
-    uint32_t c[4];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const uint32_t wi = g + j;
-      if (wi < w0) m[j] = 0;
-      else if (wi == w0) m[j] &= lo_bits;
-      if (wi > we) m[j] = 0;
-      else if (wi == we) m[j] &= hi_bits;
-      c[j] = __popc(m[j]);
-    }
-    const uint32_t c01 = c[0] + c[1], c012 = c01 + c[2], call = c012 + c[3];
-    if (need <= call) {
-      uint32_t mw, wj, k;
-      if (need <= c[0]) { mw = m[0]; wj = 0; k = need; }
-      else if (need <= c01) { mw = m[1]; wj = 1; k = need - c[0]; }
-      else if (need <= c012) { mw = m[2]; wj = 2; k = need - c01; }
-      else { mw = m[3]; wj = 3; k = need - c012; }
-      const uint32_t sp = ((g + wj) << 5) + nth_set_bit(mw, k);
-      i = sp + 1 + p.S;                  // content-defined skip (Sec. III.C)
-      return kNone;
-    }
-    need -= call;
-    g += 4;
-    if (g > we) return e + 1;            // boundary run ends first (Sec. III.A)
-    v = *reinterpret_cast<const uint4 *>(b.O + g);
+  // Opposing pairs in [i + 1, e): fewer than SkipTrigger means the run ends
+  // first.
+  const uint32_t x = i + 1;
+  const uint32_t rx = o_before(b, x);
+  if (o_before(b, e) - rx < p.T) return e + 1;  // boundary run (Sec. III.A)
+  // The skip point: O bit number t = rx + SkipTrigger (from 1), in the last
+  // word w of [x / 32, e / 32] whose preceding count is below t.
+  const uint32_t t = rx + p.T;
+  uint32_t lo = x >> 5, hi = e >> 5;
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi + 1) >> 1;
+    if (o_before_word(b, mid) < t) lo = mid; else hi = mid - 1;
   }
+  const uint32_t sp = (lo << 5) + nth_set_bit(b.O[lo], t - o_before_word(b, lo));
+  i = sp + 1 + p.S;                     // content-defined skip (Sec. III.C)
+  return kNone;
 }
 
 // One chunk: from chunk start c (rel) return its end (rel).  `end_rel` is the
@@ -447,15 +440,17 @@ struct SegShared {
 
 // Shared memory of the map kernel (bitmaps, query tables, candidate graph).
 struct MapSmem {
-  uint32_t *O;       // o_words(W): 16-byte groups
+  uint32_t *O;       // o_words(W)
   uint32_t *E;       // W + 1
   uint32_t *nz;      // nz_words(W)
   uint32_t *sbE;     // W / 64 + 2
+  uint32_t *sbO;     // W / 64 + 2
   uint32_t *cpos;    // cap: candidate positions (rel)
   uint32_t *cnxt;    // cap: next candidate index or terminal code
   uint32_t *ihash;   // kImgHash: distinct exits
   uint32_t *bscratch;  // 64: block helpers
-  uint16_t *locE;    // W + 2
+  uint16_t *locO;    // W + 2
+  uint16_t *erank_c; // L / 32 + 4: index of each candidate-range word's first candidate
 };
 
 // Words of the nonzero-E mask: one bit per bitmap word, whole 64-word steps.
@@ -470,19 +465,21 @@ __device__ __forceinline__ MapSmem carve(unsigned char *raw, uint32_t W, uint32_
   m.E = m.O + o_words(W);
   m.nz = m.E + W + 1;
   m.sbE = m.nz + nz_words(W);
-  m.cpos = m.sbE + (W >> 6) + 2;
+  m.sbO = m.sbE + (W >> 6) + 2;
+  m.cpos = m.sbO + (W >> 6) + 2;
   m.cnxt = m.cpos + cap;
   m.ihash = m.cnxt + cap;
   m.bscratch = m.ihash + kImgHash;
-  m.locE = reinterpret_cast<uint16_t *>(m.bscratch + 64);
+  m.locO = reinterpret_cast<uint16_t *>(m.bscratch + 64);
+  m.erank_c = m.locO + W + 2;
   return m;
 }
 
 __host__ __device__ inline size_t map_smem_bytes(uint32_t W, uint32_t L) {
   const uint32_t cap = cand_cap(L);
-  return (size_t)4 * (o_words(W) + (W + 1) + nz_words(W) + (W >> 6) + 2 +
+  return (size_t)4 * (o_words(W) + (W + 1) + nz_words(W) + 2 * ((W >> 6) + 2) +
                       2 * (size_t)cap + kImgHash + 64) +
-         (size_t)2 * (W + 2) + 16;
+         (size_t)2 * ((W + 2) + (L / 32 + 4)) + 16;
 }
 
 __device__ __forceinline__ uint32_t find_file(const uint32_t *seg_base,
@@ -541,7 +538,7 @@ __device__ __forceinline__ SegGeom seg_geom(const Geom &g, const DevParams &p,
 }
 
 __device__ __forceinline__ Bits bits_of(const MapSmem &m, uint32_t W) {
-  return Bits{m.E, m.O, m.nz, W};
+  return Bits{m.E, m.O, m.nz, m.sbO, m.locO, W};
 }
 
 // Per-byte unsigned compares of a 4-byte word x with y, the same word shifted
@@ -627,19 +624,28 @@ struct CandCount {
   uint32_t elo;       // E bits before lo
 };
 
-// E bits before rel position x (x <= 32 W) once sbE holds block-wide counts.
-__device__ __forceinline__ uint32_t erank_at(const MapSmem &m, uint32_t W,
-                                             uint32_t etot, uint32_t x) {
+// E bits before rel position x (x <= 32 W), once sbE holds block-wide
+// counts: the step's base plus a warp-wide count over the words of x's step
+// before x.  Called by all lanes of a warp; each lane gets the result.
+__device__ __forceinline__ uint32_t erank_warp(const MapSmem &m, uint32_t W, uint32_t etot,
+                                               uint32_t x) {
   const uint32_t w = x >> 5;
   if (w >= W) return etot;
-  return m.sbE[w >> 6] + m.locE[w] + __popc(m.E[w] & ((1u << (x & 31)) - 1u));
+  const uint32_t lane = threadIdx.x & 31;
+  uint32_t c = 0;
+  for (uint32_t k = (w & ~63u) + lane; k <= w; k += 32) {
+    uint32_t v = m.E[k];
+    if (k == w) v &= (1u << (x & 31)) - 1u;
+    c += __popc(v);
+  }
+  return m.sbE[w >> 6] + __reduce_add_sync(0xffffffffu, c);
 }
 
 // E and O bitmaps of the window [B, B + 32 W), their query tables and the
 // item's natural cuts.  Warp k covers the words [k per, (k + 1) per) in steps
 // of 64; per step, lane j takes words wb + j and wb + 32 + j (32 bytes each),
 // so a ballot gives the nonzero-E mask in word order and one warp scan gives
-// the E counts of both halves.  Three barriers: after the pass, after each
+// the O counts of both halves.  Three barriers: after the pass, after each
 // warp has made its step counts block-wide, after the candidate scatter.
 __device__ __forceinline__ CandCount seg_bitmaps(const SegGeom &gm, const Geom &g,
                                                  const DevParams &p, const MapSmem &m,
@@ -662,7 +668,7 @@ __device__ __forceinline__ CandCount seg_bitmaps(const SegGeom &gm, const Geom &
     carry_T = classify16_T(pv, p.mode);  // top 16 bits: the 16 positions before this word
     carry_byte = pv.w >> 24;
   }
-  uint32_t cE = 0;  // E bits so far in this warp's words
+  uint32_t cE = 0, cO = 0;  // E and O bits so far in this warp's words
   for (uint32_t wb = w0; wb < w1; wb += 64) {
     const uint32_t wa = wb + lane, wc = wa + 32;
     const bool la = wa < w1, lc = wc < w1;
@@ -708,9 +714,10 @@ __device__ __forceinline__ CandCount seg_bitmaps(const SegGeom &gm, const Geom &
     if (lc) { m.E[wc] = EC; m.O[wc] = OC; }
     const uint32_t nzA = __ballot_sync(kAll, EA != 0);
     const uint32_t nzC = __ballot_sync(kAll, EC != 0);
-    // E counts before each word within the step: first half in the low 16
+    const uint32_t stepE = __reduce_add_sync(kAll, __popc(EA) + __popc(EC));
+    // O counts before each word within the step: first half in the low 16
     // bits, second half in the high 16 bits (each at most 1024).
-    const uint32_t xv = __popc(EA) | (__popc(EC) << 16);
+    const uint32_t xv = __popc(OA) | (__popc(OC) << 16);
     uint32_t sv = xv;
     for (int d = 1; d < 32; d <<= 1) {
       const uint32_t y = __shfl_up_sync(kAll, sv, d);
@@ -719,54 +726,92 @@ __device__ __forceinline__ CandCount seg_bitmaps(const SegGeom &gm, const Geom &
     const uint32_t tv = __shfl_sync(kAll, sv, 31);
     const uint32_t ev = sv - xv;
     const uint32_t tA = tv & 0xffffu;
-    if (la) m.locE[wa] = (uint16_t)(ev & 0xffffu);
-    if (lc) m.locE[wc] = (uint16_t)(tA + (ev >> 16));
+    if (la) m.locO[wa] = (uint16_t)(ev & 0xffffu);
+    if (lc) m.locO[wc] = (uint16_t)(tA + (ev >> 16));
     if (lane == 0) {
       m.nz[wb >> 5] = nzA;
       m.nz[(wb >> 5) + 1] = nzC;
       m.sbE[wb >> 6] = cE;
+      m.sbO[wb >> 6] = cO;
     }
-    cE += tA + (tv >> 16);
+    cE += stepE;
+    cO += tA + (tv >> 16);
   }
-  if (lane == 0) m.bscratch[warp] = cE;
+  if (lane == 0) {
+    m.bscratch[warp] = cE;
+    m.bscratch[32 + warp] = cO;
+  }
   __syncthreads();
 
-  // Warp bases (exclusive scan over the warps' totals) added to the step
+  // Warp bases (exclusive scans over the warps' totals) added to the step
   // counts of this warp's words.
   const uint32_t vE = lane < nwarps ? m.bscratch[lane] : 0u;
-  uint32_t sE = vE;
+  const uint32_t vO = lane < nwarps ? m.bscratch[32 + lane] : 0u;
+  uint32_t sE = vE, sO = vO;
   for (int d = 1; d < 32; d <<= 1) {
-    const uint32_t y = __shfl_up_sync(kAll, sE, d);
-    if (lane >= d) sE += y;
+    const uint32_t yE = __shfl_up_sync(kAll, sE, d);
+    const uint32_t yO = __shfl_up_sync(kAll, sO, d);
+    if (lane >= d) { sE += yE; sO += yO; }
   }
   const uint32_t etot = __shfl_sync(kAll, sE, 31);
   const uint32_t baseE = __shfl_sync(kAll, sE - vE, warp);
-  if (w0 < w1 && baseE) {  // a warp without words owns no step
-    for (uint32_t st = (w0 >> 6) + lane; (st << 6) < w1; st += 32) m.sbE[st] += baseE;
+  const uint32_t baseO = __shfl_sync(kAll, sO - vO, warp);
+  if (w0 < w1 && (baseE | baseO)) {  // a warp without words owns no step
+    for (uint32_t st = (w0 >> 6) + lane; (st << 6) < w1; st += 32) {
+      m.sbE[st] += baseE;
+      m.sbO[st] += baseO;
+    }
   }
   __syncthreads();
 
   CandCount cc;
-  cc.elo = erank_at(m, W, etot, cr.lo);
-  cc.nc_nat = erank_at(m, W, etot, cr.hi) - cc.elo;
-  cc.nent_nat = erank_at(m, W, etot, min(max(cr.eh, cr.lo), cr.hi)) - cc.elo;
+  cc.elo = erank_warp(m, W, etot, cr.lo);
+  cc.nc_nat = erank_warp(m, W, etot, cr.hi) - cc.elo;
+  cc.nent_nat = erank_warp(m, W, etot, min(max(cr.eh, cr.lo), cr.hi)) - cc.elo;
   if (cr.want && cr.first + cc.nc_nat <= cr.cap) {
-    for (uint32_t w = (cr.lo >> 5) + tid; (w << 5) < cr.hi; w += nthreads) {
-      const uint32_t ew = m.E[w];
-      const uint32_t bw = w << 5;
-      uint32_t v = ew;
-      if (cr.lo > bw) v &= ~0u << (cr.lo - bw);
-      if (cr.hi - bw < 32) v &= (1u << (cr.hi - bw)) - 1u;
-      if (v) {
-        uint32_t b = __ffs(v) - 1;
-        uint32_t idx = cr.first + m.sbE[w >> 6] + m.locE[w] - cc.elo +
-                       __popc(ew & ((1u << b) - 1u));
-        m.cpos[idx] = bw + b + 1;
-        v &= v - 1;
-        while (v) {  // words with two or more run ends are the rare case
-          b = __ffs(v) - 1;
+    // Steps that meet [lo, hi), one per warp: a warp scan gives the run ends
+    // of the step before each word; in-range ones go to cpos by rank, and
+    // erank_c gets the index of each word's first in-range run end.
+    const uint32_t wlo = cr.lo >> 5, whi = (cr.hi + 31) >> 5;
+    for (uint32_t st = (wlo >> 6) + warp; (st << 6) < whi; st += nwarps) {
+      const uint32_t wb = st << 6;
+      const uint32_t wa = wb + lane, wc = wa + 32;
+      const uint32_t EA = wa < W ? m.E[wa] : 0u, EC = wc < W ? m.E[wc] : 0u;
+      const uint32_t xv = __popc(EA) | (__popc(EC) << 16);
+      uint32_t sv = xv;
+      for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t y = __shfl_up_sync(kAll, sv, d);
+        if (lane >= d) sv += y;
+      }
+      const uint32_t tA = __shfl_sync(kAll, sv, 31) & 0xffffu;
+      const uint32_t ev = sv - xv;
+      const uint32_t rbase = cr.first + m.sbE[st] - cc.elo;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const uint32_t w = h ? wc : wa;
+        if (w < wlo || w >= whi) continue;
+        const uint32_t ew = h ? EC : EA;
+        const uint32_t r0 = rbase + (h ? tA + (ev >> 16) : (ev & 0xffffu));
+        const uint32_t bw = w << 5;
+        uint32_t v = ew;
+        uint32_t below_lo = 0;
+        if (cr.lo > bw) {
+          const uint32_t lmask = (1u << (cr.lo - bw)) - 1u;
+          below_lo = __popc(ew & lmask);
+          v &= ~lmask;
+        }
+        if (cr.hi - bw < 32) v &= (1u << (cr.hi - bw)) - 1u;
+        m.erank_c[w - wlo] = (uint16_t)(r0 + below_lo);
+        if (v) {
+          uint32_t b = __ffs(v) - 1;
+          uint32_t idx = r0 + __popc(ew & ((1u << b) - 1u));
+          m.cpos[idx] = bw + b + 1;
           v &= v - 1;
-          m.cpos[++idx] = bw + b + 1;
+          while (v) {  // words with two or more run ends are the rare case
+            b = __ffs(v) - 1;
+            v &= v - 1;
+            m.cpos[++idx] = bw + b + 1;
+          }
         }
       }
     }
@@ -827,7 +872,6 @@ map_kernel(Geom g, DevParams p, WsPtrs ws) {
   const CandRange cr{lo, hi, ent_end - 1, first, (uint32_t)kMaxCand, ps_rel, true};
   const CandCount cc = seg_bitmaps(gm, g, p, m, cr);
   const uint32_t nc = cc.nc_nat + first;
-  const uint32_t elo = cc.elo;
   const bool abnormal = nc > (uint32_t)kMaxCand;
   if (!abnormal && tid == 0) {
     sh.nc = nc;
@@ -853,6 +897,7 @@ map_kernel(Geom g, DevParams p, WsPtrs ws) {
   const int lane = tid & 31;
   for (int j = tid; j < kImgHash; j += nthreads) m.ihash[j] = kEscape;
   const uint32_t Wm1 = gm.W - 1;
+  const uint32_t wlo = lo >> 5, lo_keep = ~((1u << (lo & 31)) - 1u);
   // Only as many warps as give each lane about kCandPerLane candidates take
   // part: a lane then runs through several chunks, so fewer lanes idle in
   // the tail of the longest chunk; the other warps wait at the barrier
@@ -890,8 +935,8 @@ map_kernel(Geom g, DevParams p, WsPtrs ws) {
     const uint32_t bit = 1u << (ye & 31);
     uint32_t code = kEscape;
     if (y >= q_rel) code = kTerminal | (y - ps_rel);
-    else if (ye >= lo && (ew & bit))
-      code = first + m.sbE[w >> 6] + m.locE[w] + __popc(ew & (bit - 1u)) - elo;
+    else if (ye >= lo && ye < hi && (ew & bit))  // also keeps lanes without a cut in range
+      code = m.erank_c[w - wlo] + __popc(ew & (bit - 1u) & (w == wlo ? lo_keep : ~0u));
     if (k != kNone && y != kNone) {
       // A candidate's next cut lies after it: a candidate code must be a
       // later index (anything else would be a table fault; escaping sends the
