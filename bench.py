@@ -125,6 +125,18 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(inside)}
 
 
+def max_over_ranks(x: float, device) -> float:
+    """The largest value of x over all ranks (the job is as slow as its
+    slowest rank); x itself without a process group."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def make_workload(rank: int, nfiles: int = NFILES):
     from paper_2505_21194_gb300 import workloads as W
     return W.file_batch(nfiles, seed=SEED + rank)
@@ -284,9 +296,7 @@ def run_gpu(args):
     ms_step = t_begin.elapsed_time(t_end) / args.steps
     seg_ms = sum(kb[i].elapsed_time(ke[i]) for i in range(args.steps)) / args.steps
     if world > 1:
-        t = torch.tensor([ms_step], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_step = float(t.item())
+        ms_step = max_over_ranks(ms_step, dev)
     gbs = total * world / (ms_step * 1e-3) / 1e9
 
     # CUDA-graph-captured step (same work, one graph launch per step).
