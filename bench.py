@@ -234,7 +234,7 @@ def run_gpu(args):
         # Launch tuning from the autotuner, timed on the first 1,000 files of
         # the same workload (cached per GPU model / parameters / file sizes).
         from paper_2505_21194_gb300 import autotune
-        nsamp = min(1000, offs_np.size - 1)
+        nsamp = min(2000, offs_np.size - 1)
         d_s = torch.from_numpy(data_np[:int(offs_np[nsamp])]).to(dev)
         o_s = torch.from_numpy(offs_np[:nsamp + 1].astype(np.int64)).to(dev)
         args.segment_bytes, args.threads = autotune.autotune(p, d_s, o_s)

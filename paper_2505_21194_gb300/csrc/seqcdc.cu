@@ -518,6 +518,24 @@ __device__ __forceinline__ uint32_t end_rel_of(uint64_t n_f, int64_t B) {
   return r >= (int64_t)0xffffffffLL ? 0xffffffffu : (uint32_t)r;
 }
 
+// Ask L2 for the input bytes [lo, hi) (global byte indices, clamped to the
+// input and to 16-byte boundaries) with bulk prefetches of up to 64 KiB, one
+// per lane of the calling warp: the block's loads that follow then find them
+// in L2 instead of each load step waiting for HBM.
+__device__ __forceinline__ void prefetch_l2(const uint8_t *base, int64_t lo, int64_t hi,
+                                            uint64_t total) {
+  if (lo < 0) lo = 0;
+  if (hi > (int64_t)total) hi = (int64_t)total;
+  lo = (lo + 15) & ~(int64_t)15;
+  hi &= ~(int64_t)15;
+  const int64_t lane = threadIdx.x & 31;
+  for (int64_t a = lo + lane * 65536; a < hi; a += 32 * 65536) {
+    const uint32_t n = (uint32_t)(hi - a < 65536 ? hi - a : 65536);
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(base + a), "r"(n)
+                 : "memory");
+  }
+}
+
 // Geometry of segment `seg` of `file`.
 __device__ __forceinline__ SegGeom seg_geom(const Geom &g, const DevParams &p,
                                             uint32_t file, uint32_t seg) {
@@ -849,6 +867,10 @@ map_kernel(Geom g, DevParams p, WsPtrs ws) {
   // the bitmap pass.
   const uint32_t f = find_file_warp(ws.seg_base, g.nfiles, item);
   const SegGeom gm = seg_geom(g, p, f, item - ws.seg_base[f]);
+  if (tid < 32) {
+    const int64_t gwin = (int64_t)gm.gbase + gm.B;
+    prefetch_l2(g.data, gwin, gwin + 32 * (int64_t)gm.W, g.total);
+  }
   if (tid == 0) {
     sh.nc = 0;
     sh.nent = 0;

@@ -35,6 +35,11 @@ def test_workload_key_separates_shapes(seqcdc_lib):
 def test_pick_best_and_ties():
     t = {(65536, 256): 2.0, (32768, 128): 1.5, (131072, 512): 1.5}
     assert A.pick_best(t) == (32768, 128)
+    assert A.pick_best(t, default=(65536, 256)) == (32768, 128)     # default too slow
+    t2 = {(65536, 256): 1.005, (131072, 512): 1.0, (32768, 128): 1.3}
+    assert A.pick_best(t2, default=(65536, 256)) == (65536, 256)    # within 1 %
+    assert A.pick_best(t2) == (65536, 256)                          # smaller segment
+    assert A.pick_best(t2, tol=0.0) == (131072, 512)
 
 
 def test_cache_roundtrip(tmp_path):
