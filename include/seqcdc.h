@@ -168,7 +168,7 @@ int seqcdc_chunk_batch(const seqcdc_params_t *p, const uint8_t *d_data,
  *             library image: every GPU that loads the library holds these
  *             bytes until the process exits.  The input may be at most as
  *             large as fits: seqcdc_workspace_size(p, n, 1, tuning) must not
- *             exceed it (about 64 MiB of input for the paper's parameter
+ *             exceed it (about 112 MiB of input for the paper's parameter
  *             sets), else SEQCDC_ERANGE is returned before anything runs.
  *   d_in, n, d_cuts, cap, d_count, tuning, stream  as for seqcdc_chunk().
  *   d_status  optional (may be NULL): one uint32 on the device that receives
