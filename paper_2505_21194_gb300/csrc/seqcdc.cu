@@ -1152,15 +1152,20 @@ __device__ uint64_t lookback(const ResShared &r, const WsPtrs &ws) {
   return x;
 }
 
-__global__ void __launch_bounds__(32)
+// Each warp of a block resolves its own item (blocks hold up to
+// kResolveWarps warps so that more items are in flight per SM).
+constexpr int kResolveWarps = 4;
+
+__global__ void __launch_bounds__(32 * kResolveWarps)
 resolve_kernel(Geom g, WsPtrs ws) {
-  __shared__ ResShared r;
+  __shared__ ResShared rs[kResolveWarps];
   // The item's candidate positions and links, staged by the warp with
   // coalesced loads: entry lookups and the walk along the links then read
   // shared memory instead of one dependent global load per cut.
-  extern __shared__ uint32_t rstage[];  // [cap] positions, [cap] links
+  extern __shared__ uint32_t rstage[];  // per warp: [cap] positions, [cap] links
   const uint32_t kMaxCand = g.cap;
-  const int lane = threadIdx.x;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  ResShared &r = rs[wid];
   uint32_t tk = 0;
   if (lane == 0) tk = atomicAdd(&ws.hdr->ticket, 1u);
   tk = __shfl_sync(0xffffffffu, tk, 0);
@@ -1182,7 +1187,7 @@ resolve_kernel(Geom g, WsPtrs ws) {
   __syncwarp();
   const uint32_t item = r.item;
   if (item >= ws.hdr->nitems) return;
-  uint32_t *spos = rstage, *snxt = rstage + kMaxCand;
+  uint32_t *spos = rstage + (size_t)wid * 2 * kMaxCand, *snxt = spos + kMaxCand;
   {
     const uint32_t ncs = r.nc == kAbnormal ? 0u : r.nc;
     const uint32_t *gpos = ws.cand_pos + (uint64_t)item * kMaxCand;
@@ -1680,9 +1685,14 @@ int run(const seqcdc_params_t *p, const uint8_t *d_data, uint64_t total,
   if (g_prof_begin) cudaEventRecord(g_prof_begin, st);
   map_fn<<<(unsigned)l.imax, threads, smem, st>>>(g, dp, w);
   if (g_prof_end) cudaEventRecord(g_prof_end, st);
-  const size_t rsmem = 2 * sizeof(uint32_t) * cand_cap(L);
+  // Warps per resolve block: up to kResolveWarps while their staging areas
+  // stay within 96 KiB.
+  const size_t rper = 2 * sizeof(uint32_t) * cand_cap(L);
+  uint32_t rwarps = (uint32_t)((96 * 1024) / rper);
+  rwarps = rwarps < 1 ? 1 : (rwarps > (uint32_t)kResolveWarps ? (uint32_t)kResolveWarps : rwarps);
+  const size_t rsmem = rper * rwarps;
   if (rsmem > 48 * 1024 && !resolve_smem_configured(rsmem)) return SEQCDC_ECUDA;
-  resolve_kernel<<<(unsigned)l.imax, 32, rsmem, st>>>(g, w);
+  resolve_kernel<<<(unsigned)((l.imax + rwarps - 1) / rwarps), 32 * rwarps, rsmem, st>>>(g, w);
   const uint64_t vblocks = (l.imax + 255) / 256;
   const unsigned vgrid = (unsigned)(vblocks < 4096 ? vblocks : 4096);
   const unsigned rgrid = (unsigned)(l.imax < 2u * (uint64_t)sms ? l.imax : 2u * (uint64_t)sms);
