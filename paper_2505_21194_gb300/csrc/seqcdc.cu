@@ -112,7 +112,8 @@ enum : uint32_t {
 
 struct Layout {
   size_t hdr, seg_base, ftile, state, incl, entry, first_bad, count, img_n,
-      img, agg, cand_n, ent_n, cand_pos, cand_nxt, ent_term, slot, itile, runs, total;
+      img, agg, cand_n, ent_n, cand_pos, cand_nxt, ent_term, slot, itile, runs, item_file,
+      total;
   uint64_t imax;     // upper bound on items
   uint64_t nftiles;  // plan tiles
   uint64_t nitiles;  // compaction tiles
@@ -162,6 +163,7 @@ struct WsPtrs {
   uint64_t *slot;       // per item x slot_cap (file-relative cuts)
   uint32_t *itile;      // per compaction tile
   uint32_t *runs;       // per item: first items of runs to repair (verify rounds)
+  uint32_t *item_file;  // per item: its file (written by the map kernel)
   uint32_t slot_cap;
 };
 
@@ -482,18 +484,8 @@ __host__ __device__ inline size_t map_smem_bytes(uint32_t W, uint32_t L) {
          (size_t)2 * ((W + 2) + (L / 32 + 4)) + 16;
 }
 
-__device__ __forceinline__ uint32_t find_file(const uint32_t *seg_base,
-                                              uint64_t nfiles, uint32_t item) {
-  // largest f < nfiles with seg_base[f] <= item (then seg_base[f+1] > item)
-  uint64_t lo = 0, hi = nfiles;
-  while (hi - lo > 1) {
-    const uint64_t mid = (lo + hi) >> 1;
-    if (seg_base[mid] <= item) lo = mid; else hi = mid;
-  }
-  return (uint32_t)lo;
-}
-
-// find_file by one warp: a 32-ary search (three rounds cover 32768 files).
+// The file of an item (largest f with seg_base[f] <= item), by one warp: a
+// 32-ary search (three rounds cover 32768 files).
 __device__ uint32_t find_file_warp(const uint32_t *seg_base, uint64_t nfiles,
                                    uint32_t item) {
   const int lane = threadIdx.x & 31;
@@ -872,6 +864,7 @@ map_kernel(Geom g, DevParams p, WsPtrs ws) {
     prefetch_l2(g.data, gwin, gwin + 32 * (int64_t)gm.W, g.total);
   }
   if (tid == 0) {
+    ws.item_file[item] = f;
     sh.nc = 0;
     sh.nent = 0;
     sh.ninvalid = 0;
@@ -1283,7 +1276,7 @@ __global__ void verify_kernel(Geom g, WsPtrs ws, uint32_t round) {
   const uint32_t nitems = ws.hdr->nitems;
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nitems;
        i += (uint64_t)gridDim.x * blockDim.x) {
-    const uint32_t f = find_file(ws.seg_base, g.nfiles, (uint32_t)i);
+    const uint32_t f = ws.item_file[i];
     const uint32_t s = (uint32_t)i - ws.seg_base[f];
     const bool ok = item_consistent(ws, i, s);
     if (round < kRepairRounds) {
@@ -1359,7 +1352,7 @@ run_repair_kernel(Geom g, DevParams p, WsPtrs ws, uint32_t round) {
     __syncthreads();
     if (r >= nruns) return;
     const uint32_t i0 = ws.runs[r];
-    const uint32_t f = find_file(ws.seg_base, g.nfiles, i0);
+    const uint32_t f = ws.item_file[i0];
     const uint32_t base = ws.seg_base[f], end = ws.seg_base[f + 1];
     uint64_t cur = (i0 == base) ? 0ull : __ldcg(&ws.incl[i0 - 1]);
     for (uint32_t it = i0; it < end; ++it) {
@@ -1567,6 +1560,7 @@ Layout make_layout(const seqcdc_params_t *p, uint64_t total, uint64_t nfiles,
   l.slot = take(l.imax * (size_t)l.slot_cap * 8);
   l.itile = take(l.nitiles * 4);
   l.runs = take(l.imax * 4);
+  l.item_file = take(l.imax * 4);
   l.total = o;
   return l;
 }
@@ -1593,6 +1587,7 @@ WsPtrs ws_ptrs(void *d_ws, const Layout &l) {
   w.slot = reinterpret_cast<uint64_t *>(b + l.slot);
   w.itile = reinterpret_cast<uint32_t *>(b + l.itile);
   w.runs = reinterpret_cast<uint32_t *>(b + l.runs);
+  w.item_file = reinterpret_cast<uint32_t *>(b + l.item_file);
   w.slot_cap = l.slot_cap;
   return w;
 }
@@ -1701,8 +1696,11 @@ int run(const seqcdc_params_t *p, const uint8_t *d_data, uint64_t total,
     run_repair_kernel<<<rgrid, threads, smem, st>>>(g, dp, w, round);
   }
   verify_kernel<<<vgrid, 256, 0, st>>>(g, w, kRepairRounds);
+  // One block per still-inconsistent file, over a grid of at most 4 per SM
+  // (files are taken in strides; almost all have nothing to do).
   const uint64_t rblocks = nfiles ? nfiles : 1;
-  repair_kernel<<<(unsigned)(rblocks < 65535 ? rblocks : 65535), threads, smem, st>>>(g, dp, w);
+  const uint64_t rcap = 4u * (uint64_t)sms;
+  repair_kernel<<<(unsigned)(rblocks < rcap ? rblocks : rcap), threads, smem, st>>>(g, dp, w);
   count_tiles_kernel<<<(unsigned)l.nitiles, kItemTile, 0, st>>>(w);
   emit_kernel<<<(unsigned)l.nitiles, kItemTile, 0, st>>>(g, w, d_cuts, cap,
                                                           d_cut_offsets, d_count);
