@@ -125,6 +125,34 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(inside)}
 
 
+def bind_to_gpu_numa(gpu_index: int):
+    """Run this process on the CPUs local to the GPU (the GPU's PCI device
+    lists them in sysfs), so that pinned host buffers are allocated in memory
+    next to it: host<->device copies from the other socket's memory are much
+    slower.  Returns the CPUs bound to, or None when unknown."""
+    try:
+        bus = subprocess.run(["nvidia-smi", "--query-gpu=pci.bus_id", "--format=csv,noheader",
+                              "-i", str(gpu_index)], capture_output=True, text=True,
+                             timeout=30).stdout.strip().lower()
+        dom, rest = bus.split(":", 1)
+        path = "/sys/bus/pci/devices/%s:%s/local_cpulist" % (dom[-4:], rest)
+        cpus = set()
+        with open(path) as f:
+            for part in f.read().strip().split(","):
+                if "-" in part:
+                    a, b = part.split("-")
+                    cpus.update(range(int(a), int(b) + 1))
+                elif part:
+                    cpus.add(int(part))
+        cpus &= set(os.sched_getaffinity(0))
+        if cpus:
+            os.sched_setaffinity(0, cpus)
+            return sorted(cpus)
+    except Exception:
+        pass
+    return None
+
+
 def max_over_ranks(x: float, device) -> float:
     """The largest value of x over all ranks (the job is as slow as its
     slowest rank); x itself without a process group."""
@@ -221,6 +249,7 @@ def run_gpu(args):
         dist.init_process_group("nccl")
     dev = torch.device("cuda", local if world > 1 else 0)
     torch.cuda.set_device(dev)
+    numa_cpus = bind_to_gpu_numa(dev.index)
     seqcdc.load_library()
 
     data_np, offs_np = make_workload(rank, args.nfiles)
@@ -488,7 +517,9 @@ def run_gpu(args):
                 "serial": {"value": round(total * world / e2e_serial_s / 1e9, 2),
                            "d2h_bytes_per_step": int(d2h),
                            "api": "one host-to-device copy, seqcdc_chunk_batch, copies back"},
-                "h2d_copy_GBs": round(h2d_gbs, 1)},
+                "h2d_copy_GBs": round(h2d_gbs, 1),
+                "host_cpus": ("%d CPUs local to the GPU" % len(numa_cpus)) if numa_cpus
+                             else "not bound"},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
                      "unit": "GB/s", "frac": round(achieved / peak, 4),
                      "traffic": traffic, "kernel": "map_kernel",

@@ -37,18 +37,18 @@ class Request:
 
 
 def form_batch(queue: Sequence[Request], inflight_bytes: int, budget: int,
-               max_batch_bytes: int) -> int:
+               max_batch_bytes: int, max_files: int = 1 << 30) -> int:
     """How many requests at the head of ``queue`` form the next batch.
 
     First come, first served: requests are taken in order while the batch
     stays within ``max_batch_bytes`` (a request larger than that forms a batch
-    alone) and the bytes in flight stay within ``budget``.  The head request
-    is never skipped, so the order of completion follows the order of
-    arrival batch by batch.
+    alone) and ``max_files`` requests, and the bytes in flight stay within
+    ``budget``.  The head request is never skipped, so the order of
+    completion follows the order of arrival batch by batch.
     """
     take, total = 0, 0
     for r in queue:
-        if take and total + r.nbytes > max_batch_bytes:
+        if take and (total + r.nbytes > max_batch_bytes or take >= max_files):
             break
         if inflight_bytes + total + r.nbytes > budget:
             break
@@ -89,6 +89,7 @@ class _Batch:
     keep: tuple           # device tensors alive until the batch is done
     h_cuts: object        # pinned host int64
     h_co: object          # pinned host int64
+    slot: int             # staging slot
 
 
 @dataclasses.dataclass
@@ -109,7 +110,7 @@ class Server:
 
     def __init__(self, p, pool, pool_offsets, budget_bytes: int = 64 * GIB,
                  max_batch_bytes: int = 4 * GIB, max_inflight: int = 3,
-                 tuning=None, device: str = "cuda"):
+                 tuning=None, device: str = "cuda", max_batch_files: int = 4096):
         import torch
         if not pool.is_pinned():
             raise ValueError("the payload pool must be pinned host memory")
@@ -127,7 +128,18 @@ class Server:
         self.device = torch.device(device)
         self.copy = torch.cuda.Stream(self.device)
         self.compute = torch.cuda.Stream(self.device)
+        self.max_files = int(max_batch_files)
         seqcdc.load_library()
+        # Pinned staging for each pipeline slot, allocated once: offsets in,
+        # cut lists and CSR index out (a batch's cut list is bounded by its
+        # bytes / min_size + its files).
+        big = max(self.max_batch, int(self.sizes.max(initial=0)))
+        cap = big // p.min_size + self.max_files
+        self._stage = [(torch.empty(self.max_files + 1, dtype=torch.int64, pin_memory=True),
+                        torch.empty(cap, dtype=torch.int64, pin_memory=True),
+                        torch.empty(self.max_files + 1, dtype=torch.int64, pin_memory=True))
+                       for _ in range(self.max_inflight)]
+        self._free_stage = list(range(self.max_inflight))
 
     # -- one batch ---------------------------------------------------------
     def _launch(self, reqs: List[Request]) -> _Batch:
@@ -138,7 +150,10 @@ class Server:
         total = int(offs[-1])
         nfiles = len(reqs)
         cap = total // self.p.min_size + nfiles
-        h_offs = torch.from_numpy(offs).pin_memory()
+        slot = self._free_stage.pop()
+        h_offs_all, h_cuts_all, h_co_all = self._stage[slot]
+        h_offs = h_offs_all[:nfiles + 1]
+        h_offs.copy_(torch.from_numpy(offs))
         with torch.cuda.stream(self.copy):
             d_data = torch.empty(max(total, 16), dtype=torch.uint8, device=self.device)
             for r, o in zip(reqs, offs[:-1].tolist()):
@@ -159,14 +174,14 @@ class Server:
             seqcdc.seqcdc_chunk_batch(self.p, d_data, total, d_offs, nfiles, d_cuts,
                                       cap, d_co, d_ws, ws_bytes, self.tuning,
                                       self.compute)
-            h_cuts = torch.empty(max(cap, 1), dtype=torch.int64, pin_memory=True)
-            h_co = torch.empty(nfiles + 1, dtype=torch.int64, pin_memory=True)
+            h_cuts = h_cuts_all[:max(cap, 1)]
+            h_co = h_co_all[:nfiles + 1]
             h_cuts.copy_(d_cuts, non_blocking=True)
             h_co.copy_(d_co, non_blocking=True)
             done = torch.cuda.Event(enable_timing=True)
             done.record(self.compute)
         return _Batch(reqs, total, done, (d_data, d_offs, d_cuts, d_co, d_ws, h_offs),
-                      h_cuts, h_co)
+                      h_cuts, h_co, slot)
 
     # -- the serving loop --------------------------------------------------
     def run(self, arrivals: Iterable[Request], keep: Optional[set] = None,
@@ -205,9 +220,11 @@ class Server:
                         results[r.rid] = cuts[co[j]:co[j + 1]].copy()
                 inflight_bytes -= b.nbytes
                 nbytes += b.nbytes
+                self._free_stage.append(b.slot)
                 progressed = True
             if queue and len(inflight) < self.max_inflight:
-                k = form_batch(queue, inflight_bytes, self.budget, self.max_batch)
+                k = form_batch(queue, inflight_bytes, self.budget, self.max_batch,
+                               self.max_files)
                 if k:
                     reqs = [queue.popleft() for _ in range(k)]
                     b = self._launch(reqs)

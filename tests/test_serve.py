@@ -28,6 +28,8 @@ def test_form_batch_fifo_and_limits():
     assert form_batch(q, 995, budget=1000, max_batch_bytes=1000) == 0  # head does not fit
     assert form_batch(_reqs([5, 500, 5]), 0, budget=100, max_batch_bytes=1000) == 1
     assert form_batch([], 0, 10, 10) == 0
+    assert form_batch(q, 0, budget=1000, max_batch_bytes=1000, max_files=2) == 2
+    assert form_batch(q, 0, budget=1000, max_batch_bytes=1000, max_files=1) == 1
 
 
 def test_latency_stats_percentiles():
