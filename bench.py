@@ -170,25 +170,47 @@ def make_workload(rank: int, nfiles: int = NFILES):
     return W.file_batch(nfiles, seed=SEED + rank)
 
 
-def _traffic_record(kernel_src_hash: str):
-    """DRAM bytes per launch from the committed ncu summary, if still current."""
-    path = os.path.join(ROOT, "profiles", "map_kernel_traffic.json")
+# Source files each dominant kernel is built from: a DRAM-traffic record
+# under profiles/ is used only while their hash still matches.
+KERNEL_SOURCES = {
+    "spec_kernel": ("paper_2505_21194_gb300/csrc/walk.cu",
+                    "paper_2505_21194_gb300/csrc/common.cuh", "include/seqcdc.h"),
+    "map_kernel": ("paper_2505_21194_gb300/csrc/seqcdc.cu",
+                   "paper_2505_21194_gb300/csrc/common.cuh", "include/seqcdc.h"),
+}
+
+
+def _traffic_record(kernel: str):
+    """DRAM bytes per unit from the committed ncu summary, if still current."""
+    path = os.path.join(ROOT, "profiles", "%s_traffic.json" % kernel)
     try:
         with open(path) as f:
             d = json.load(f)
     except Exception:
-        return None, None
-    if d.get("source_sha256") != kernel_src_hash:
-        return None, d
-    return d, d
+        return None
+    return d if d.get("source_sha256") == _source_hash(kernel) else None
 
 
-def _source_hash():
+def _source_hash(kernel: str):
     h = hashlib.sha256()
-    for rel in ("paper_2505_21194_gb300/csrc/seqcdc.cu", "include/seqcdc.h"):
+    for rel in KERNEL_SOURCES[kernel]:
         with open(os.path.join(ROOT, rel), "rb") as f:
             h.update(f.read())
     return h.hexdigest()
+
+
+def scan_span_bytes(d_cuts, d_co, ncuts, p):
+    """Bytes the chunk chain scans: for every chunk, from its scan start
+    (min_size - SeqLength bytes in, Sec. III.B) to its end."""
+    import torch
+    cuts = d_cuts[:ncuts]
+    starts = torch.zeros_like(cuts)
+    if ncuts > 1:
+        starts[1:] = cuts[:-1]
+    first = d_co[:-1][d_co[:-1] < d_co[1:]]  # first cut of every non-empty file
+    starts[first] = 0
+    skip = max(int(p.min_size) - int(p.seq_length), 0)
+    return int(torch.clamp(cuts - starts - skip, min=0).sum().item())
 
 
 def cpu_oracle_pass(data, offs, threads):
@@ -256,26 +278,28 @@ def run_gpu(args):
     total = int(data_np.size)
     nfiles = offs_np.size - 1
     p = seqcdc.seqcdc_params(KIB, MODE)
+    d_data = torch.from_numpy(data_np).to(dev)
+    d_offs = torch.from_numpy(offs_np.astype(np.int64)).to(dev)
     tune_src = "library default"
-    if args.segment_bytes or args.threads:
+    algos = {"auto": seqcdc.ALGO_AUTO, "map": seqcdc.ALGO_MAP, "walk": seqcdc.ALGO_WALK}
+    if args.segment_bytes or args.threads or args.algorithm != "auto" or args.piece_bytes:
+        best = (args.segment_bytes, args.threads, algos[args.algorithm], args.piece_bytes)
         tune_src = "command line"
     elif not args.no_autotune:
-        # Launch tuning from the autotuner, timed on the first 1,000 files of
-        # the same workload (cached per GPU model / parameters / file sizes).
+        # Path and sizes from the autotuner, timed on this device-resident
+        # batch (cached per GPU model / parameters / workload shape).
         from paper_2505_21194_gb300 import autotune
-        nsamp = min(2000, offs_np.size - 1)
-        d_s = torch.from_numpy(data_np[:int(offs_np[nsamp])]).to(dev)
-        o_s = torch.from_numpy(offs_np[:nsamp + 1].astype(np.int64)).to(dev)
-        args.segment_bytes, args.threads = autotune.autotune(p, d_s, o_s)
-        tune_src = "autotuned on the first %d files" % nsamp
-        del d_s, o_s
-    tuning = seqcdc.Tuning(args.segment_bytes, args.threads)
+        best = autotune.autotune(p, d_data, d_offs)
+        tune_src = "autotuned on this batch"
+    else:
+        best = (0, 0, seqcdc.ALGO_AUTO, 0)
+    tuning = seqcdc.Tuning(*best)
     eff = seqcdc.seqcdc_resolve_tuning(p, tuning)
+    walk = best[2] == seqcdc.ALGO_WALK or (best[2] == seqcdc.ALGO_AUTO and
+                                          nfiles >= seqcdc.WALK_MIN_FILES)
     cap = total // p.min_size + nfiles
     ws_bytes = seqcdc.seqcdc_workspace_size(p, total, nfiles, tuning)
 
-    d_data = torch.from_numpy(data_np).to(dev)
-    d_offs = torch.from_numpy(offs_np.astype(np.int64)).to(dev)
     d_cuts = torch.empty(cap, dtype=torch.int64, device=dev)
     d_co = torch.empty(nfiles + 1, dtype=torch.int64, device=dev)
     d_ws = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
@@ -362,7 +386,8 @@ def run_gpu(args):
     if not args.skip_plain:
         offs64 = offs_np.astype(np.int64)
         cnt = torch.empty(1, dtype=torch.int64, device=dev)
-        ws1 = seqcdc.seqcdc_workspace_size(p, int(np.diff(offs64).max()), 1, tuning)
+        # one file per call: the library's defaults for a single stream
+        ws1 = seqcdc.seqcdc_workspace_size(p, int(np.diff(offs64).max()), 1, None)
         d_ws1 = torch.empty(ws1, dtype=torch.uint8, device=dev)
         # Each file gets its own 16-byte-aligned device buffer (the ABI's
         # alignment rule); file starts inside the CSR batch are arbitrary.
@@ -376,7 +401,7 @@ def run_gpu(args):
         def plain_pass():
             for f in range(nfiles):
                 seqcdc.seqcdc_chunk(p, views[f], views[f].numel(), d_cuts, cap, cnt,
-                                    d_ws1, ws1, tuning, stream)
+                                    d_ws1, ws1, None, stream)
 
         plain_pass()
         torch.cuda.synchronize(dev)
@@ -474,15 +499,53 @@ def run_gpu(args):
               "checked_vs_host_sha256": len(hd), "mismatches": int(bad)}
         del dig, fsz
     peak, peak_kind = _measured_peaks()
-    alg_bytes = total + ncuts * 8  # each input byte read once + the cut list
+    if walk:
+        # The chain walk reads only the scan windows: its algorithmic bytes
+        # are the bytes the chain scans (Sec. III.B leaves the rest unread)
+        # plus its 4-byte cut records.
+        kernel = "spec_kernel"
+        span = scan_span_bytes(d_cuts, d_co, ncuts, p)
+        alg_bytes = span + ncuts * 4
+        # plan_tiles, plan_scan, fill, spec, junction, verify, repair, count, emit
+        launches_per_step = 9
+    else:
+        kernel = "map_kernel"
+        span = None
+        alg_bytes = total + ncuts * 8  # each input byte read once + the cut list
+        # plan_tiles, plan_scan, map, resolve, 2 x (verify, run_repair), verify,
+        # repair, count_tiles, emit
+        launches_per_step = 12
     achieved = alg_bytes / (seg_ms * 1e-3) / 1e9
-    rec, _ = _traffic_record(_source_hash())
+    rec = _traffic_record(kernel)
     traffic = None
     if rec is not None:
         traffic = float(rec["dram_bytes_per_byte"]) * total
-    # plan_tiles, plan_scan, map, resolve, 2 x (verify, run_repair), verify,
-    # repair, count_tiles, emit
-    launches_per_step = 12
+    # The other path on the same batch, for comparison (library defaults).
+    other = None
+    if not args.no_compare:
+        alt = seqcdc.Tuning(0, 0, seqcdc.ALGO_MAP if walk else seqcdc.ALGO_WALK, 0)
+        ws_alt = seqcdc.seqcdc_workspace_size(p, total, nfiles, alt)
+        d_ws_alt = torch.empty(ws_alt, dtype=torch.uint8, device=dev)
+        for _ in range(3):
+            seqcdc.seqcdc_chunk_batch(p, d_data, total, d_offs, nfiles, d_cuts, cap,
+                                      d_co, d_ws_alt, ws_alt, alt, stream)
+        oa, ob = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 5
+        oa.record(stream)
+        for _ in range(reps):
+            seqcdc.seqcdc_chunk_batch(p, d_data, total, d_offs, nfiles, d_cuts, cap,
+                                      d_co, d_ws_alt, ws_alt, alt, stream)
+        ob.record(stream)
+        torch.cuda.synchronize(dev)
+        o_ms = oa.elapsed_time(ob) / reps
+        same = (seqcdc.seqcdc_status(d_ws_alt, stream) == 0 and int(d_co[-1].item()) == ncuts)
+        other = {"path": "segment map" if walk else "chain walk", "ms_per_step": round(o_ms, 4),
+                 "value": round(total / (o_ms * 1e-3) / 1e9, 2), "unit": "GB/s",
+                 "same_cut_count": bool(same)}
+        del d_ws_alt
+        # restore this path's output for anything below that reads it
+        step()
+        torch.cuda.synchronize(dev)
     if rank != 0:
         return
     line = {
@@ -503,8 +566,10 @@ def run_gpu(args):
                         "4 KiB..64 MiB), half random / half Markov text, CSR; "
                         "8 KiB setting, increasing mode" % nfiles,
             "total_bytes": total, "nfiles": nfiles, "cuts": ncuts,
-            "segment_bytes": eff.segment_bytes,
-            "block_threads": eff.block_threads,
+            "path": "chain walk" if walk else "segment map",
+            "piece_bytes": eff.piece_bytes if walk else None,
+            "segment_bytes": None if walk else eff.segment_bytes,
+            "block_threads": None if walk else eff.block_threads,
             "tuning": tune_src,
             "l2": "inputs (%.1f GiB) far larger than L2; no flush" % (total / 2**30),
             "parallelism": "1 GPU per rank, independent batches (weak scaling)",
@@ -522,9 +587,15 @@ def run_gpu(args):
                              else "not bound"},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
                      "unit": "GB/s", "frac": round(achieved / peak, 4),
-                     "traffic": traffic, "kernel": "map_kernel",
+                     "traffic": traffic, "kernel": kernel,
                      "peak_source": peak_kind,
-                     "kernel_ms": round(seg_ms, 4)},
+                     "kernel_ms": round(seg_ms, 4),
+                     "algorithmic_bytes": int(alg_bytes),
+                     "algorithmic": ("scan spans (%d B, %.3f of the input) + 4 B per cut"
+                                     % (span, span / max(total, 1))) if walk else
+                                    "every input byte once + 8 B per cut",
+                     "input_GBs": round(total / (seg_ms * 1e-3) / 1e9, 1)},
+        "other_path": other,
         "plain_one_launch_per_file": (
             {"value": round(total / (plain_ms * 1e-3) / 1e9, 3), "unit": "GB/s",
              "ms_per_pass": round(plain_ms, 2)} if plain_ms else None),
@@ -541,7 +612,8 @@ def run_gpu(args):
         from paper_2505_21194_gb300 import workloads as W
         backup = W.backup_stream(SEED)
     if not args.no_serve:
-        line["serve"] = serve_levels(dev, p, tuning, SERVE_LOADS_GBS, backup)
+        # batches of a few ~16 MiB requests: the library's own choice per batch
+        line["serve"] = serve_levels(dev, p, None, SERVE_LOADS_GBS, backup)
     if not args.no_dedup:
         line["dedup"] = dedup_savings(dev, backup)
         line["sweep"] = sweep_report(dev, backup)
@@ -702,7 +774,13 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--segment-bytes", type=int, default=0)
     ap.add_argument("--threads", type=int, default=0)
+    ap.add_argument("--algorithm", default="auto", choices=["auto", "map", "walk"],
+                    help="chunking path (default: autotuned, else the library's AUTO rule)")
+    ap.add_argument("--piece-bytes", type=int, default=0,
+                    help="chain walk: bytes per piece (0 = library default)")
     ap.add_argument("--skip-plain", action="store_true")
+    ap.add_argument("--no-compare", action="store_true",
+                    help="skip timing the other chunking path on the same batch")
     ap.add_argument("--no-cpu", action="store_true",
                     help="skip the CPU-oracle baseline (profiling runs)")
     ap.add_argument("--no-autotune", action="store_true",

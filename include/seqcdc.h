@@ -10,6 +10,11 @@
  * Sec. III.C.  A chunk is cut at max_size when no run completes first,
  * Sec. IV and Sec. VI.  This library computes exactly the boundary list a
  * sequential scan produces, with CUDA kernels over device-resident bytes.
+ * It has two paths with the same output (see seqcdc_tuning_t.algorithm):
+ * a segment map that classifies every byte and resolves the chunk chain
+ * across segments, and a chain walk that follows the chain one chunk after
+ * the other, many chains at once, reading only the scan windows (the bytes
+ * Sec. III.B and III.C leave unread are never loaded).
  *
  * Conventions for every entry point:
  *   - "d_" pointers are CUDA device pointers (or managed memory) that the
@@ -75,25 +80,42 @@ typedef struct {
 
 /*
  * Launch tuning (all fields 0 = library default).
- *   segment_bytes  bytes of input one thread block owns (rounded up to a
- *                  multiple of 1024; at least 4096 and at least max_size;
- *                  lowered if the block's shared memory would not fit).
- *                  Larger segments mean fewer junctions but more shared
- *                  memory per block.
- *   block_threads  threads per block of the segment kernel (128, 256, 512;
- *                  any other value means the default).
+ *   segment_bytes  segment map: bytes of input one thread block owns
+ *                  (rounded up to a multiple of 1024; at least 4096 and at
+ *                  least max_size; lowered if the block's shared memory would
+ *                  not fit).  Larger segments mean fewer junctions but more
+ *                  shared memory per block.
+ *   block_threads  segment map: threads per block of the segment kernel
+ *                  (128, 256, 512; any other value means the default).
+ *   algorithm      SEQCDC_ALGO_AUTO (0), SEQCDC_ALGO_MAP or SEQCDC_ALGO_WALK.
+ *                  AUTO takes the chain walk for batches of at least
+ *                  SEQCDC_WALK_MIN_FILES files and the segment map otherwise.
+ *                  The chain walk needs many chains (pieces) at once to be
+ *                  fast, and walks stretches without run ends (long runs of
+ *                  equal bytes, where every cut is forced at max_size) one
+ *                  file at a time; the segment map has neither limit.
+ *   piece_bytes    chain walk: bytes of a piece, the unit one warp walks
+ *                  (rounded up to a multiple of 64 KiB; at least
+ *                  4 x max_size, at most 64 MiB; default 1 MiB).
  */
+#define SEQCDC_ALGO_AUTO 0u
+#define SEQCDC_ALGO_MAP  1u
+#define SEQCDC_ALGO_WALK 2u
+#define SEQCDC_WALK_MIN_FILES 256u
 typedef struct {
     uint32_t segment_bytes;
     uint32_t block_threads;
+    uint32_t algorithm;
+    uint32_t piece_bytes;
 } seqcdc_tuning_t;
 
 /*
- * Fill *out with the segment size and block size that a chunking call with
- * these parameters and this tuning (NULL or zero fields: library defaults)
- * runs with.  The defaults are 256 threads and 64 KiB segments (max_size if
- * larger).  Returns SEQCDC_EINVAL
- * for an invalid parameter set or a NULL out.
+ * Fill *out with the segment size, block size and piece size that a chunking
+ * call with these parameters and this tuning (NULL or zero fields: library
+ * defaults) runs with; out->algorithm is copied from the tuning (AUTO is
+ * decided per call, from the number of files).  The defaults are 256 threads,
+ * 64 KiB segments (max_size if larger) and 1 MiB pieces.  Returns
+ * SEQCDC_EINVAL for an invalid parameter set or a NULL out.
  */
 int seqcdc_resolve_tuning(const seqcdc_params_t *p, const seqcdc_tuning_t *tuning,
                           seqcdc_tuning_t *out);
@@ -198,23 +220,28 @@ int seqcdc_status(const void *d_ws, void *stream);
 
 /*
  * Synchronise `stream` and copy up to `n` (<= 8) path counters of the last
- * call that used d_ws into out[]: [0] segments processed, [1] segments whose
- * natural entries could not all be walked, [2] segments with more distinct
- * exits than the library publishes, [3] look-backs that had to wait for a
- * predecessor's true exit, [4] segments found inconsistent by the verify
- * pass, [5] segments re-chunked by the repair passes, [6] segments the
- * resolve pass emitted from a guessed entry (or could not emit) because their
- * true entry was unknown or not one of their natural cuts, [7] total
- * look-back depth.  The counters describe which code paths ran; the output is
- * exact either way.
+ * call that used d_ws into out[].  Segment map: [0] segments processed,
+ * [1] segments whose natural entries could not all be walked, [2] segments
+ * with more distinct exits than the library publishes, [3] look-backs that
+ * had to wait for a predecessor's true exit, [4] segments found inconsistent
+ * by the verify pass, [5] segments re-chunked by the repair passes,
+ * [6] segments the resolve pass emitted from a guessed entry (or could not
+ * emit) because their true entry was unknown or not one of their natural
+ * cuts, [7] total look-back depth.  Chain walk: [0] pieces walked, [1] chunks
+ * found by the piece walks, [2] junction walks, [3] chunks the junction walks
+ * took before meeting their piece's walk, [4] junction walks that left their
+ * piece without meeting it, [5] pieces found inconsistent, [6] junction walks
+ * redone by the repair pass, [7] 1 KiB windows the piece walks loaded.  The
+ * counters describe which code paths ran; the output is exact either way.
  */
 int seqcdc_stats(const void *d_ws, void *stream, uint32_t *out, uint32_t n);
 
 /*
  * Measurement hook: record the CUDA events `ev_begin` / `ev_end` (cudaEvent_t
  * passed as void*) on the call's stream immediately before and after the
- * segment kernel of every later seqcdc_chunk / seqcdc_chunk_batch call made
- * from this host thread, so that its device time can be read with
+ * dominant kernel (the segment kernel of the segment map, the piece-walk
+ * kernel of the chain walk) of every later seqcdc_chunk / seqcdc_chunk_batch
+ * call made from this host thread, so that its device time can be read with
  * cudaEventElapsedTime.  Pass NULL, NULL to stop.  The events are owned by the
  * caller.  Always returns SEQCDC_OK.
  */

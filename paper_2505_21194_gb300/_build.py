@@ -17,7 +17,8 @@ INCLUDE_DIR = os.path.join(REPO_DIR, "include")
 LIB_DIR = os.path.join(PKG_DIR, "_lib")
 LIB_PATH = os.path.join(LIB_DIR, "libseqcdc.so")
 
-SOURCES = ["seqcdc.cu", "fingerprint.cu"]
+SOURCES = ["seqcdc.cu", "walk.cu", "fingerprint.cu"]
+HEADERS = ["common.cuh", "walk.h"]
 ARCH_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -29,7 +30,7 @@ def _nvcc() -> str:
 
 
 def _inputs():
-    files = [os.path.join(SRC_DIR, s) for s in SOURCES]
+    files = [os.path.join(SRC_DIR, s) for s in SOURCES + HEADERS]
     files.append(os.path.join(INCLUDE_DIR, "seqcdc.h"))
     return files
 

@@ -1,17 +1,20 @@
-"""Launch tuning: segment size x block size, chosen by timing and cached.
+"""Launch tuning: which path, and its sizes, chosen by timing and cached.
 
-Each candidate (segment bytes, threads per block) is timed on a sample of the
-caller's workload: the whole chunking call (all of its kernels) with CUDA
-events on the launching stream, after warm-up, median of a few runs.  The
-fastest (the library default when it is within 1 %, i.e. within the
-timing noise) is stored in a JSON cache keyed by the GPU model and SM count, the
-parameter set and the shape of the workload (single stream or batch, and the
-median file size in powers of two), so a later process on the same kind of GPU
-reuses it without timing.
+Candidates are (segment bytes, threads, algorithm, piece bytes) tuples, the
+fields of ``seqcdc_tuning_t``: the segment map with each segment size x block
+size, and the chain walk with each piece size.  Each candidate is timed on
+the caller's (device-resident) workload: the whole chunking call (all of its
+kernels) with CUDA events on the launching stream, after warm-up, median of a
+few runs.  The fastest (the library default when it is within 1 %, i.e.
+within the timing noise) is stored in a JSON cache keyed by the GPU model and
+SM count, the parameter set and the shape of the workload (single stream or
+batch, the number of files and the median file size in powers of two), so a
+later process on the same kind of GPU reuses it without timing.
 
 Segments must be at least max_size bytes and the block's shared memory must
-fit (the library lowers an oversized segment; a candidate it would change is
-skipped).  Timing runs only the library's CUDA kernels.
+fit; pieces must be at least 4 x max_size (the library adjusts other values;
+a candidate it would change is skipped).  Timing runs only the library's
+CUDA kernels.
 """
 from __future__ import annotations
 
@@ -28,6 +31,8 @@ from . import seqcdc
 
 SEGMENTS = (32768, 49152, 65536, 98304, 131072, 196608, 262144)
 THREADS = (128, 256, 512)
+PIECES = (262144, 524288, 1048576, 2097152, 4194304)
+CACHE_VERSION = "v2"
 _lock = threading.Lock()
 
 
@@ -45,23 +50,39 @@ def workload_key(gpu_name: str, sm_count: int, p, sizes: Sequence[int]) -> str:
     kind = "stream" if sizes.size <= 1 else "batch"
     med = int(np.median(sizes)) if sizes.size else 0
     bucket = int(math.log2(med)) if med > 0 else 0
+    nbucket = int(math.log2(sizes.size)) if sizes.size > 0 else 0
     params = "%d-%d-%d-%d-%d-%d" % (p.mode, p.seq_length, p.skip_trigger, p.skip_size,
                                     p.min_size, p.max_size)
-    return "%s|sm%d|%s|%s|2^%d" % (gpu_name, sm_count, params, kind, bucket)
+    return "%s|%s|sm%d|%s|%s|2^%d files|2^%d" % (CACHE_VERSION, gpu_name, sm_count, params,
+                                                 kind, nbucket, bucket)
 
 
-def candidates(p, segments: Iterable[int] = SEGMENTS,
-               threads: Iterable[int] = THREADS) -> List[Tuple[int, int]]:
-    """(segment, threads) pairs the library runs as given."""
+def candidates(p, segments: Iterable[int] = SEGMENTS, threads: Iterable[int] = THREADS,
+               pieces: Iterable[int] = PIECES) -> List[Tuple[int, int, int, int]]:
+    """Tuning tuples the library runs as given: segment-map (segment, threads)
+    pairs, then chain-walk piece sizes."""
     out = []
     for L in segments:
         if L < p.max_size:
             continue
         for t in threads:
-            eff = seqcdc.seqcdc_resolve_tuning(p, (L, t))
+            eff = seqcdc.seqcdc_resolve_tuning(p, (L, t, seqcdc.ALGO_MAP, 0))
             if (eff.segment_bytes, eff.block_threads) == (L, t):
-                out.append((L, t))
+                out.append((L, t, seqcdc.ALGO_MAP, 0))
+    for P in pieces:
+        eff = seqcdc.seqcdc_resolve_tuning(p, (0, 0, seqcdc.ALGO_WALK, P))
+        if eff.piece_bytes == P:
+            out.append((0, 0, seqcdc.ALGO_WALK, P))
     return out
+
+
+def default_candidate(p, nfiles: int, batch: bool = True) -> Tuple[int, int, int, int]:
+    """The tuple a call with the library defaults runs as (AUTO resolved:
+    the chain walk for batches of at least SEQCDC_WALK_MIN_FILES files)."""
+    eff = seqcdc.seqcdc_resolve_tuning(p)
+    if batch and nfiles >= seqcdc.WALK_MIN_FILES:
+        return (0, 0, seqcdc.ALGO_WALK, eff.piece_bytes)
+    return (eff.segment_bytes, eff.block_threads, seqcdc.ALGO_MAP, 0)
 
 
 def load_cache(path: str) -> Dict[str, dict]:
@@ -84,19 +105,19 @@ def store_cache(path: str, key: str, entry: dict) -> None:
         os.replace(tmp, path)
 
 
-def pick_best(times: Dict[Tuple[int, int], float],
-              default: Optional[Tuple[int, int]] = None, tol: float = 0.01) -> Tuple[int, int]:
+def pick_best(times: Dict[tuple, float], default: Optional[tuple] = None,
+              tol: float = 0.01) -> tuple:
     """Fastest candidate.  Within ``tol`` of the fastest (timing noise), the
-    library default wins if it is among them, else the smaller segment, then
-    fewer threads."""
+    library default wins if it is among them, else the smallest tuple (smaller
+    segment, then fewer threads)."""
     best = min(times.values())
     near = [c for c in times if times[c] <= best * (1.0 + tol)]
     if default is not None and default in near:
         return default
-    return min(near, key=lambda c: (c[0], c[1], times[c]))
+    return min(near, key=lambda c: (tuple(c), times[c]))
 
 
-def time_candidate(p, d_data, d_offsets, tuning: Tuple[int, int], reps: int = 5,
+def time_candidate(p, d_data, d_offsets, tuning: tuple, reps: int = 5,
                    warmup: int = 3, stream=None) -> float:
     """Median milliseconds of one chunking call (all kernels) on the sample."""
     import torch
@@ -130,13 +151,14 @@ def time_candidate(p, d_data, d_offsets, tuning: Tuple[int, int], reps: int = 5,
 
 
 def autotune(p, d_data, d_offsets, cache_path: Optional[str] = None,
-             cands: Optional[List[Tuple[int, int]]] = None,
-             timer: Optional[Callable] = None, force: bool = False) -> Tuple[int, int]:
-    """Best (segment bytes, threads) for this kind of workload on this GPU.
+             cands: Optional[List[tuple]] = None,
+             timer: Optional[Callable] = None, force: bool = False) -> tuple:
+    """Best tuning tuple (segment bytes, threads, algorithm, piece bytes) for
+    this kind of workload on this GPU.
 
-    ``d_data`` (uint8) and ``d_offsets`` (int64, CSR) are a device-resident
-    sample of the workload; a single stream is ``offsets = [0, n]``.  The
-    result is cached at ``cache_path`` (default: ``default_cache_path()``).
+    ``d_data`` (uint8) and ``d_offsets`` (int64, CSR) are the device-resident
+    workload (or a sample of it); a single stream is ``offsets = [0, n]``.
+    The result is cached at ``cache_path`` (default: ``default_cache_path()``).
     """
     import torch
     path = cache_path or default_cache_path()
@@ -145,14 +167,14 @@ def autotune(p, d_data, d_offsets, cache_path: Optional[str] = None,
     key = workload_key(props.name, props.multi_processor_count, p, sizes)
     if not force:
         hit = load_cache(path).get(key)
-        if hit:
-            return int(hit["segment_bytes"]), int(hit["block_threads"])
+        if hit and "tuning" in hit:
+            return tuple(int(v) for v in hit["tuning"])
     cands = cands or candidates(p)
     timer = timer or time_candidate
-    times = {c: timer(p, d_data, d_offsets, c) for c in cands}
-    eff = seqcdc.seqcdc_resolve_tuning(p)
-    best = pick_best(times, (eff.segment_bytes, eff.block_threads))
-    store_cache(path, key, {"segment_bytes": best[0], "block_threads": best[1],
-                            "ms": times[best], "sample_bytes": int(d_data.numel()),
-                            "timed": {"%dx%d" % c: round(t, 4) for c, t in times.items()}})
+    times = {tuple(c): timer(p, d_data, d_offsets, tuple(c)) for c in cands}
+    best = pick_best(times, default_candidate(p, int(sizes.size)))
+    store_cache(path, key, {"tuning": list(best), "ms": times[best],
+                            "sample_bytes": int(d_data.numel()),
+                            "timed": {"x".join(str(v) for v in c): round(t, 4)
+                                      for c, t in times.items()}})
     return best

@@ -48,6 +48,8 @@
 #include <mutex>
 
 #include "seqcdc.h"
+#include "common.cuh"
+#include "walk.h"
 
 namespace {
 
@@ -78,15 +80,6 @@ constexpr uint32_t kTerminal = 0x80000000u;  // candidate next: first cut >= ite
 constexpr uint32_t kEscape = 0xFFFFFFFFu;    // candidate next: forced cut inside item
 constexpr uint32_t kAbnormal = 0xFFFFFFFFu;  // cand_n: too many natural cuts
 constexpr uint64_t kBad = ~0ull;             // unknown exit / entry
-
-struct DevParams {
-  uint32_t mode;
-  uint32_t R;   // seq_length
-  uint32_t T;   // skip_trigger (0 = never)
-  uint32_t S;   // skip_size
-  uint32_t mn;  // min_size
-  uint32_t mx;  // max_size
-};
 
 // Workspace header (first 256 bytes of the workspace).
 struct WsHeader {
@@ -170,17 +163,6 @@ struct WsPtrs {
 // ---------------------------------------------------------------------------
 // Small device helpers.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ uint64_t global_ns() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-__device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p) {
-  uint32_t v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
 
 // Wait until (*flag & mask) != 0, at most kWaitNs.  Returns the flag value, or
 // 0 after recording SEQCDC_ETIMEOUT in the workspace status.
@@ -198,60 +180,6 @@ __device__ uint32_t wait_any(const uint32_t *flag, uint32_t mask, WsHeader *hdr)
   }
   atomicExch(&hdr->status, (uint32_t)SEQCDC_ETIMEOUT);
   return 0;
-}
-
-// Position (0..31) of the k-th set bit (1 <= k <= popc(x)); a branch-free
-// binary descent over halves, quarters, ... of the word.
-__device__ __forceinline__ uint32_t nth_set_bit(uint32_t x, uint32_t k) {
-  uint32_t pos = 0, c, t;
-  c = __popc(x & 0xffffu); t = k > c; k -= t ? c : 0u; x >>= t ? 16 : 0; pos += t ? 16 : 0;
-  c = __popc(x & 0xffu);   t = k > c; k -= t ? c : 0u; x >>= t ? 8 : 0;  pos += t ? 8 : 0;
-  c = __popc(x & 0xfu);    t = k > c; k -= t ? c : 0u; x >>= t ? 4 : 0;  pos += t ? 4 : 0;
-  c = __popc(x & 0x3u);    t = k > c; k -= t ? c : 0u; x >>= t ? 2 : 0;  pos += t ? 2 : 0;
-  c = x & 1u;              t = k > c;                                    pos += t ? 1 : 0;
-  return pos;
-}
-
-// 16 input bytes at global byte index gi (16-aligned); bytes outside
-// [0, total) read as zero.
-__device__ __forceinline__ uint4 load16(const uint8_t *data, int64_t gi,
-                                        uint64_t total) {
-  if (gi >= 0 && (uint64_t)gi + 16 <= total) {
-    return __ldg(reinterpret_cast<const uint4 *>(data + gi));
-  }
-  uint32_t w[4] = {0, 0, 0, 0};
-  for (int t = 0; t < 16; ++t) {
-    const int64_t a = gi + t;
-    if (a >= 0 && (uint64_t)a < total) w[t >> 2] |= (uint32_t)data[a] << (8 * (t & 3));
-  }
-  return make_uint4(w[0], w[1], w[2], w[3]);
-}
-
-// Exclusive block scan of one value per thread (blockDim <= 1024).
-__device__ uint32_t block_excl_scan(uint32_t v, uint32_t *scratch,
-                                    uint32_t *total) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int nwarps = (blockDim.x + 31) >> 5;
-  uint32_t x = v;
-  for (int d = 1; d < 32; d <<= 1) {
-    const uint32_t y = __shfl_up_sync(0xffffffffu, x, d);
-    if (lane >= d) x += y;
-  }
-  if (lane == 31) scratch[warp] = x;
-  __syncthreads();
-  if (warp == 0) {
-    uint32_t s = lane < nwarps ? scratch[lane] : 0u;
-    for (int d = 1; d < 32; d <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xffffffffu, s, d);
-      if (lane >= d) s += y;
-    }
-    if (lane < nwarps) scratch[lane] = s;
-  }
-  __syncthreads();
-  const uint32_t warp_off = warp ? scratch[warp - 1] : 0u;
-  *total = scratch[nwarps - 1];
-  __syncthreads();
-  return warp_off + x - v;
 }
 
 // ---------------------------------------------------------------------------
@@ -352,7 +280,6 @@ __device__ uint32_t chunk_step(const Bits &b, const DevParams &p, uint32_t c,
     if (y != kNone) return y;
   }
 }
-
 
 // ---------------------------------------------------------------------------
 // Plan: seg_base[f] = sum of ceil(n_g / L) over g < f; item count.
@@ -549,61 +476,6 @@ __device__ __forceinline__ SegGeom seg_geom(const Geom &g, const DevParams &p,
 
 __device__ __forceinline__ Bits bits_of(const MapSmem &m, uint32_t W) {
   return Bits{m.E, m.O, m.nz, m.sbO, m.locO, W};
-}
-
-// Per-byte unsigned compares of a 4-byte word x with y, the same word shifted
-// by one byte (y's byte k is the byte before x's byte k), answers in bit 7 of
-// each byte.  Both come from one borrow-free subtraction: with
-// z1 = (x | 0x80) - (y & 0x7f) - 1 per byte (0..0xfe), bit 7 of z1 is
-// [x_low7 > y_low7] and z2 = 0xfe - z1 = (y | 0x80) - (x & 0x7f) - 1 gives
-// [y_low7 > x_low7]; where the top bits differ they decide.
-__device__ __forceinline__ void cmp_word(uint32_t x, uint32_t y, uint32_t &gt,
-                                         uint32_t &lt) {
-  const uint32_t z1 = (x | 0x80808080u) - (y & 0x7f7f7f7fu) - 0x01010101u;
-  const uint32_t z2 = 0xfefefefeu - z1;
-  gt = ((x & ~y) | (~(x ^ y) & z1)) & 0x80808080u;   // x > y per byte
-  lt = ((y & ~x) | (~(x ^ y) & z2)) & 0x80808080u;   // x < y per byte
-}
-
-// Bit 7 of the 8 bytes of two words (a = bytes 0..3, b = bytes 4..7) -> bits
-// 0..7 in byte order.  With a's bits moved to 3, 11, 19, 27 and b's at 7, 15,
-// 23, 31, one multiplication by 1 + 2^7 + 2^14 + 2^21 lands them at 24..31 in
-// order; the other partial products stay below bit 24 without overlapping.
-__device__ __forceinline__ uint32_t gather8(uint32_t a, uint32_t b) {
-  return (((a >> 4) | b) * 0x00204081u) >> 24;
-}
-
-// 32 bytes (two 16-byte vectors) with the byte before them -> T and O bits
-// of the 32 positions (bit t = pair (byte t-1, byte t)).
-__device__ __forceinline__ void classify32(uint4 v0, uint4 v1, uint32_t prev_byte,
-                                           uint32_t mode, uint32_t &T,
-                                           uint32_t &Ow) {
-  uint32_t g0, l0, g1, l1, g2, l2, g3, l3, g4, l4, g5, l5, g6, l6, g7, l7;
-  cmp_word(v0.x, (v0.x << 8) | (prev_byte & 0xffu), g0, l0);
-  cmp_word(v0.y, __funnelshift_l(v0.x, v0.y, 8), g1, l1);
-  cmp_word(v0.z, __funnelshift_l(v0.y, v0.z, 8), g2, l2);
-  cmp_word(v0.w, __funnelshift_l(v0.z, v0.w, 8), g3, l3);
-  cmp_word(v1.x, __funnelshift_l(v0.w, v1.x, 8), g4, l4);
-  cmp_word(v1.y, __funnelshift_l(v1.x, v1.y, 8), g5, l5);
-  cmp_word(v1.z, __funnelshift_l(v1.y, v1.z, 8), g6, l6);
-  cmp_word(v1.w, __funnelshift_l(v1.z, v1.w, 8), g7, l7);
-  const uint32_t up = gather8(g0, g1) | (gather8(g2, g3) << 8) |
-                      (gather8(g4, g5) << 16) | (gather8(g6, g7) << 24);
-  const uint32_t dn = gather8(l0, l1) | (gather8(l2, l3) << 8) |
-                      (gather8(l4, l5) << 16) | (gather8(l6, l7) << 24);
-  T = mode == 0 ? up : dn;
-  Ow = mode == 0 ? dn : up;
-}
-
-// E at position t needs T at t, t-1, ..., t-(R-2); `pt` holds the T bits of
-// the 32 positions before.
-__device__ __forceinline__ uint32_t run_ends(uint32_t pt, uint32_t T, uint32_t R) {
-  if (R == 5)  // the paper's SeqLength at every setting (Table I)
-    return T & __funnelshift_l(pt, T, 1) & __funnelshift_l(pt, T, 2) &
-           __funnelshift_l(pt, T, 3);
-  uint32_t ew = T;
-  for (uint32_t k = 1; k + 1 < R; ++k) ew &= __funnelshift_l(pt, T, k);
-  return ew;
 }
 
 // T bits (bits 16..31) of the 16 positions of v, whose first byte's
@@ -1520,6 +1392,20 @@ uint32_t pick_segment(const seqcdc_params_t *p, const seqcdc_tuning_t *t) {
   return L;
 }
 
+// Which path a call takes: the tuning's choice, else the chain walk for
+// batches of many files (each piece is a chain one warp walks; a batch of
+// few large files or one stream gives too few of them at once) and the
+// segment map otherwise.
+bool use_walk(const seqcdc_tuning_t *t, uint64_t nfiles, bool batch) {
+  const uint32_t a = t ? t->algorithm : SEQCDC_ALGO_AUTO;
+  if (a == SEQCDC_ALGO_WALK) return true;
+  if (a == SEQCDC_ALGO_MAP) return false;
+  return batch && nfiles >= SEQCDC_WALK_MIN_FILES;
+}
+
+size_t workspace_for(const seqcdc_params_t *p, uint64_t total, uint64_t nfiles,
+                     const seqcdc_tuning_t *t, bool batch);
+
 uint32_t pick_threads(const seqcdc_tuning_t *t) {
   uint32_t n = (t && t->block_threads) ? t->block_threads : 256u;
   if (n != 128u && n != 256u && n != 512u) n = 256u;
@@ -1592,6 +1478,13 @@ WsPtrs ws_ptrs(void *d_ws, const Layout &l) {
   return w;
 }
 
+size_t workspace_for(const seqcdc_params_t *p, uint64_t total, uint64_t nfiles,
+                     const seqcdc_tuning_t *t, bool batch) {
+  if (use_walk(t, nfiles, batch))
+    return seqcdc_walk::workspace_bytes(p, total, nfiles, seqcdc_walk::pick_piece(p, t));
+  return make_layout(p, total, nfiles, pick_segment(p, t)).total;
+}
+
 thread_local cudaEvent_t g_prof_begin = nullptr;
 thread_local cudaEvent_t g_prof_end = nullptr;
 
@@ -1656,6 +1549,15 @@ int run(const seqcdc_params_t *p, const uint8_t *d_data, uint64_t total,
   if (!d_ws || ((uintptr_t)d_ws & 255u)) return SEQCDC_EINVAL;
   if (total > 0 && (!d_data || ((uintptr_t)d_data & 15u))) return SEQCDC_EINVAL;
   if (total > 0 && !d_cuts) return SEQCDC_EINVAL;
+  if (use_walk(tuning, nfiles, d_offsets != nullptr)) {
+    if (cap < total / p->min_size + nfiles) return SEQCDC_ECAPACITY;
+    const int sms_w = sm_count();
+    if (sms_w <= 0) return SEQCDC_ECUDA;
+    return seqcdc_walk::run(p, d_data, total, d_offsets, nfiles, d_cuts, cap,
+                            d_cut_offsets, d_count, d_ws, ws_bytes,
+                            seqcdc_walk::pick_piece(p, tuning), sms_w, stream,
+                            g_prof_begin, g_prof_end);
+  }
   const uint32_t L = pick_segment(p, tuning);
   const uint32_t threads = pick_threads(tuning);
   const Layout l = make_layout(p, total, nfiles, L);
@@ -1719,7 +1621,6 @@ __global__ void copy_status_kernel(const WsHeader *hdr, uint32_t *out) {
   *out = hdr->status;
 }
 
-
 // Device address of g_noalloc_scratch on the current device (set-up on first
 // use per device, with that device current).  nullptr on failure.
 void *noalloc_scratch_address() {
@@ -1772,13 +1673,20 @@ int seqcdc_resolve_tuning(const seqcdc_params_t *p, const seqcdc_tuning_t *tunin
   if (!params_ok(p) || !out) return SEQCDC_EINVAL;
   out->segment_bytes = pick_segment(p, tuning);
   out->block_threads = pick_threads(tuning);
+  out->algorithm = tuning ? tuning->algorithm : SEQCDC_ALGO_AUTO;
+  out->piece_bytes = seqcdc_walk::pick_piece(p, tuning);
   return SEQCDC_OK;
 }
 
 size_t seqcdc_workspace_size(const seqcdc_params_t *p, uint64_t total_bytes,
                              uint64_t nfiles, const seqcdc_tuning_t *tuning) {
   if (!params_ok(p)) return 0;
-  return make_layout(p, total_bytes, nfiles, pick_segment(p, tuning)).total;
+  // The path seqcdc_chunk_batch() takes for these sizes; for one file,
+  // which seqcdc_chunk() may chunk too, whichever path needs more.
+  const size_t as_batch = workspace_for(p, total_bytes, nfiles, tuning, true);
+  if (nfiles != 1) return as_batch;
+  const size_t as_stream = workspace_for(p, total_bytes, nfiles, tuning, false);
+  return as_batch > as_stream ? as_batch : as_stream;
 }
 
 int seqcdc_chunk(const seqcdc_params_t *p, const uint8_t *d_in, uint64_t n,
@@ -1805,7 +1713,7 @@ int seqcdc_chunk_noalloc(const seqcdc_params_t *p, const uint8_t *d_in,
                          uint64_t *d_count, uint32_t *d_status,
                          const seqcdc_tuning_t *tuning, void *stream) {
   if (!d_count || !params_ok(p)) return SEQCDC_EINVAL;
-  const size_t need = make_layout(p, n, 1, pick_segment(p, tuning)).total;
+  const size_t need = workspace_for(p, n, 1, tuning, false);
   if (need > (size_t)SEQCDC_NOALLOC_SCRATCH_BYTES) return SEQCDC_ERANGE;
   void *ws = noalloc_scratch_address();
   if (!ws) return SEQCDC_ECUDA;

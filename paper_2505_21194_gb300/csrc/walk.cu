@@ -1,0 +1,864 @@
+// walk.cu -- SeqCDC by walking the chunk chain, reading only what it scans.
+//
+// The sequential chunker of Sec. III looks at few of the input bytes: the
+// first min_size - SeqLength bytes of every chunk are never scanned
+// (Sec. III.B) and SkipSize bytes are passed over after each skip
+// (Sec. III.C).  This path follows the chain the way the paper's scan does,
+// one chunk after the other, with a whole warp per scan step: the warp loads
+// a 1 KiB window of the scan region (32 bytes per lane), classifies its byte
+// pairs into the T, O and E bits of Sec. III.D, and finds the first run end
+// and the SkipTrigger-th opposing pair with a ballot and a warp prefix sum.
+// Only the windows the chain scans are read from memory.
+//
+// The chain is sequential, so parallelism comes from many chains at once:
+//   plan      split every file into pieces of P bytes (P >= 4 max_size).
+//   spec      one warp per piece walks the chain from the piece start as if
+//             a chunk began there, up to the first cut at or after the piece
+//             end (the piece's exit).  For a file's first piece this is the
+//             true chain.
+//   junction  one warp per later piece: from the exit of the previous
+//             piece's walk, walk the chain until it reaches a cut of this
+//             piece's own walk.  The chunk after a cut depends only on that
+//             cut, so from the meeting cut on the two chains are the same.
+//   verify    a piece's junction started from the exit its predecessor's
+//             spec walk computed; where the predecessor's final exit differs
+//             (its own junction never met its walk) the piece is
+//             inconsistent.  A file without inconsistent pieces is exact by
+//             induction from its start.
+//   repair    one warp per file with an inconsistent piece redoes the
+//             junctions in order from the first such piece.
+//   compact   count each piece's cuts, exclusive scan, copy to the caller's
+//             CSR output.
+// Chains started at different positions meet after a few dozen chunks on
+// ordinary data, well within a piece.  In long stretches with no run ends
+// (constant bytes, where every cut is forced at max_size) they never meet,
+// and the repair pass walks those stretches one file at a time.
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <mutex>
+
+#include "common.cuh"
+#include "seqcdc.h"
+#include "walk.h"
+
+namespace {
+
+constexpr uint32_t kWin = 1024;        // bytes per warp window (32 per lane)
+constexpr int kWalkThreads = 128;      // walk kernels: four warps per block
+// Blocks of the walk kernels resident per SM that the register budget is
+// sized for (the walks are latency-bound: more warps, more chains in flight).
+#ifndef SEQCDC_WALK_MIN_BLOCKS
+#define SEQCDC_WALK_MIN_BLOCKS 1
+#endif
+constexpr int kWalkMinBlocks = SEQCDC_WALK_MIN_BLOCKS;
+constexpr int kFileTile = 1024;        // files per plan block
+constexpr int kPieceTile = 256;        // pieces per compaction block
+constexpr uint32_t kUnmerged = 0xFFFFFFFFu;
+constexpr uint32_t kNoBad = 0xFFFFFFFFu;
+constexpr uint32_t kFull = 0xFFFFFFFFu;
+constexpr uint32_t kDefaultPiece = 1u << 20;
+// L2 prefetch ahead of each chunk: the next chunk's scan starts at least
+// min_size bytes after this chunk's scan start.
+#ifndef SEQCDC_WALK_PREFETCH
+#define SEQCDC_WALK_PREFETCH 2048
+#endif
+constexpr uint32_t kPrefetch = SEQCDC_WALK_PREFETCH;
+
+// Workspace header: status and statistics at the offsets seqcdc_status and
+// seqcdc_stats read.
+struct WalkHeader {
+  uint32_t status;         // 0 or a SEQCDC_* error code
+  uint32_t ticket;         // spec-walk queue head
+  uint32_t npieces;
+  uint32_t stats[8];
+  uint32_t jticket;        // junction queue head
+  uint32_t nlong, nshort;  // walk-order fill counters
+  uint32_t pad[50];
+};
+static_assert(sizeof(WalkHeader) == 256, "walk header is 256 bytes");
+
+enum : uint32_t {
+  WS_PIECES = 0,        // pieces walked
+  WS_SPEC_CHUNKS = 1,   // chunks found by the spec walks
+  WS_JUNCTIONS = 2,     // junction walks
+  WS_JCHUNKS = 3,       // chunks the junction walks took before meeting
+  WS_UNMERGED = 4,      // junction walks that left their piece without meeting
+  WS_INCONSISTENT = 5,  // pieces whose junction input was wrong
+  WS_REPAIRED = 6,      // junction walks redone by the repair pass
+  WS_WINDOWS = 7,       // 1 KiB windows loaded by the spec walks
+};
+
+struct WGeom {
+  const uint8_t *data;
+  uint64_t total;
+  const uint64_t *offsets;  // nullptr: one stream of `total` bytes
+  uint64_t nfiles;
+  uint32_t P;               // piece bytes
+  uint32_t fullcap;         // list entries of a full piece (P / min_size + 3)
+};
+
+struct WPtrs {
+  WalkHeader *hdr;
+  uint32_t *piece_base;  // nfiles + 1: first piece of each file
+  uint64_t *list_base;   // nfiles + 1: first list entry of each file
+  uint32_t *ftile;       // per plan tile: pieces of its files
+  uint64_t *ftile_l;     // per plan tile: list entries of its files
+  uint32_t *piece_file;  // per piece
+  uint32_t *order;       // per piece: walk order (long pieces first)
+  uint32_t *spec_n;      // per piece: cuts of its spec walk (the exit last)
+  uint32_t *spec;        // list entries: spec-walk cuts, relative to the piece start
+  uint32_t *jin;         // per piece: where its junction walk started (relative)
+  uint32_t *jn;          // per piece: junction cuts before the meeting cut
+  uint32_t *jm;          // per piece: index of the meeting cut in spec, or kUnmerged
+  uint32_t *jexit;       // per piece: exit of a junction walk that did not meet
+  uint32_t *jcut;        // list entries: junction cuts, relative to the piece start
+  uint32_t *first_bad;   // per file: first inconsistent piece
+  uint32_t *count;       // per piece: cuts it owns (c with start < c <= end)
+  uint32_t *ctile;       // per compaction tile: their sum
+};
+
+__device__ __forceinline__ uint64_t wfile_start(const WGeom &g, uint64_t f) {
+  return g.offsets ? g.offsets[f] : 0;
+}
+__device__ __forceinline__ uint64_t wfile_end(const WGeom &g, uint64_t f) {
+  return g.offsets ? g.offsets[f + 1] : g.total;
+}
+
+// List entries a piece of `len` bytes reserves: its cuts in (start, end] are
+// at least min_size apart except the file's last, plus the exit.
+__host__ __device__ __forceinline__ uint32_t list_cap(uint32_t len, uint32_t mn) {
+  return len / mn + 3;
+}
+
+__device__ __forceinline__ uint64_t file_lists(uint64_t n, uint32_t P, uint32_t fullcap,
+                                               uint32_t mn) {
+  const uint64_t tail = n % P;
+  return (n / P) * fullcap + (tail ? list_cap((uint32_t)tail, mn) : 0u);
+}
+
+struct Piece {
+  uint64_t ps;    // absolute start
+  uint64_t fend;  // absolute end of its file
+  uint64_t lb;    // first list entry
+  uint32_t len;   // bytes
+  uint32_t kl;    // index within its file
+  uint32_t cap;   // list entries
+  uint32_t file;
+};
+
+__device__ __forceinline__ Piece piece_of(const WGeom &g, const WPtrs &w, const DevParams &p,
+                                          uint32_t k) {
+  Piece pc;
+  pc.file = w.piece_file[k];
+  pc.kl = k - w.piece_base[pc.file];
+  const uint64_t fs = wfile_start(g, pc.file);
+  pc.fend = wfile_end(g, pc.file);
+  pc.ps = fs + (uint64_t)pc.kl * g.P;
+  const uint64_t rest = pc.fend - pc.ps;
+  pc.len = (uint32_t)(rest < g.P ? rest : g.P);
+  pc.lb = w.list_base[pc.file] + (uint64_t)pc.kl * g.fullcap;
+  pc.cap = list_cap(pc.len, p.mn);
+  return pc;
+}
+
+__device__ __forceinline__ void set_status(WalkHeader *h, uint32_t code) {
+  atomicCAS(&h->status, 0u, code);
+}
+
+// ---------------------------------------------------------------------------
+// Plan: pieces and list entries per file, their prefix sums, walk order.
+// ---------------------------------------------------------------------------
+__global__ void wplan_tiles_kernel(WGeom g, DevParams p, WPtrs w) {
+  __shared__ uint32_t red[32];
+  __shared__ uint64_t red_l[32];
+  const uint64_t f0 = (uint64_t)blockIdx.x * kFileTile;
+  uint32_t sum = 0;
+  uint64_t sum_l = 0;
+  for (uint64_t f = f0 + threadIdx.x; f < f0 + kFileTile && f < g.nfiles; f += blockDim.x) {
+    const uint64_t n = wfile_end(g, f) - wfile_start(g, f);
+    sum += (uint32_t)((n + g.P - 1) / g.P);
+    sum_l += file_lists(n, g.P, g.fullcap, p.mn);
+  }
+  for (int d = 16; d; d >>= 1) {
+    sum += __shfl_down_sync(kFull, sum, d);
+    sum_l += __shfl_down_sync(kFull, sum_l, d);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[threadIdx.x >> 5] = sum;
+    red_l[threadIdx.x >> 5] = sum_l;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t s = 0;
+    uint64_t s_l = 0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+      s += red[k];
+      s_l += red_l[k];
+    }
+    w.ftile[blockIdx.x] = s;
+    w.ftile_l[blockIdx.x] = s_l;
+  }
+}
+
+// Exclusive block scan of one 64-bit value per thread.
+__device__ uint64_t block_excl_scan64(uint64_t v, uint64_t *scratch, uint64_t *total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nwarps = (blockDim.x + 31) >> 5;
+  uint64_t x = v;
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint64_t y = __shfl_up_sync(kFull, x, d);
+    if (lane >= d) x += y;
+  }
+  if (lane == 31) scratch[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    uint64_t s = lane < nwarps ? scratch[lane] : 0ull;
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint64_t y = __shfl_up_sync(kFull, s, d);
+      if (lane >= d) s += y;
+    }
+    if (lane < nwarps) scratch[lane] = s;
+  }
+  __syncthreads();
+  const uint64_t warp_off = warp ? scratch[warp - 1] : 0ull;
+  *total = scratch[nwarps - 1];
+  __syncthreads();
+  return warp_off + x - v;
+}
+
+__global__ void wplan_scan_kernel(WGeom g, DevParams p, WPtrs w, uint64_t nftiles) {
+  __shared__ uint32_t scratch[32];
+  __shared__ uint64_t scratch_l[32];
+  __shared__ uint32_t s_prefix;
+  __shared__ uint64_t s_prefix_l;
+  uint32_t part = 0;
+  uint64_t part_l = 0;
+  for (uint64_t t = threadIdx.x; t < blockIdx.x; t += blockDim.x) {
+    part += w.ftile[t];
+    part_l += w.ftile_l[t];
+  }
+  for (int d = 16; d; d >>= 1) {
+    part += __shfl_down_sync(kFull, part, d);
+    part_l += __shfl_down_sync(kFull, part_l, d);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    scratch[threadIdx.x >> 5] = part;
+    scratch_l[threadIdx.x >> 5] = part_l;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t s = 0;
+    uint64_t s_l = 0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+      s += scratch[k];
+      s_l += scratch_l[k];
+    }
+    s_prefix = s;
+    s_prefix_l = s_l;
+  }
+  __syncthreads();
+  uint32_t running = s_prefix;
+  uint64_t running_l = s_prefix_l;
+  const uint64_t f0 = (uint64_t)blockIdx.x * kFileTile;
+  for (uint64_t c0 = f0; c0 < f0 + kFileTile; c0 += blockDim.x) {
+    const uint64_t f = c0 + threadIdx.x;
+    const bool live = f < g.nfiles && f < f0 + kFileTile;
+    const uint64_t n = live ? wfile_end(g, f) - wfile_start(g, f) : 0;
+    const uint32_t v = live ? (uint32_t)((n + g.P - 1) / g.P) : 0u;
+    const uint64_t v_l = live ? file_lists(n, g.P, g.fullcap, p.mn) : 0ull;
+    uint32_t tot;
+    uint64_t tot_l;
+    const uint32_t ex = block_excl_scan(v, scratch, &tot);
+    const uint64_t ex_l = block_excl_scan64(v_l, scratch_l, &tot_l);
+    if (live) {
+      w.piece_base[f] = running + ex;
+      w.list_base[f] = running_l + ex_l;
+    }
+    running += tot;
+    running_l += tot_l;
+  }
+  if (blockIdx.x == nftiles - 1 && threadIdx.x == 0) {
+    w.piece_base[g.nfiles] = running;
+    w.list_base[g.nfiles] = running_l;
+    WalkHeader *h = w.hdr;
+    h->status = 0;
+    h->ticket = 0;
+    h->jticket = 0;
+    h->npieces = running;
+    h->nlong = 0;
+    h->nshort = 0;
+    for (int k = 0; k < 8; ++k) h->stats[k] = 0;
+  }
+  for (uint64_t f = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; f < g.nfiles;
+       f += (uint64_t)gridDim.x * blockDim.x)
+    w.first_bad[f] = kNoBad;
+}
+
+// piece_file of every piece, and the walk order: pieces of at least P/2
+// bytes first (filled from the front), shorter ones after them (filled from
+// the back), so the longest walks start in the first wave.
+__global__ void wfill_kernel(WGeom g, WPtrs w) {
+  const uint32_t np = w.hdr->npieces;
+  const uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool live = k < np;
+  bool longp = false;
+  if (live) {
+    // The last file whose first piece is at or before k holds it (an empty
+    // file shares its first-piece index with the next file).
+    uint64_t a = 0, b = g.nfiles - 1;
+    while (a < b) {
+      const uint64_t mid = (a + b + 1) >> 1;
+      if (w.piece_base[mid] <= k) a = mid; else b = mid - 1;
+    }
+    w.piece_file[k] = (uint32_t)a;
+    const uint64_t ps = wfile_start(g, a) + (k - w.piece_base[a]) * (uint64_t)g.P;
+    longp = wfile_end(g, a) - ps >= (uint64_t)(g.P >> 1);
+  }
+  const int lane = threadIdx.x & 31;
+  const uint32_t bl = __ballot_sync(kFull, live && longp);
+  const uint32_t bs = __ballot_sync(kFull, live && !longp);
+  uint32_t base_l = 0, base_s = 0;
+  if (lane == 0) {
+    if (bl) base_l = atomicAdd(&w.hdr->nlong, (uint32_t)__popc(bl));
+    if (bs) base_s = atomicAdd(&w.hdr->nshort, (uint32_t)__popc(bs));
+  }
+  base_l = __shfl_sync(kFull, base_l, 0);
+  base_s = __shfl_sync(kFull, base_s, 0);
+  const uint32_t below = (1u << lane) - 1u;
+  if (live) {
+    if (longp) w.order[base_l + __popc(bl & below)] = (uint32_t)k;
+    else w.order[np - 1u - (base_s + __popc(bs & below))] = (uint32_t)k;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// One chunk, one warp.
+// ---------------------------------------------------------------------------
+// Bits [a, b) of a 32-bit lane word (a, b relative to the lane's first bit).
+__device__ __forceinline__ uint32_t bit_range(int32_t a, int32_t b) {
+  a = a < 0 ? 0 : a;
+  b = b > 32 ? 32 : b;
+  if (a >= b) return 0u;
+  const uint32_t hi = b >= 32 ? kFull : ((1u << b) - 1u);
+  return hi & ~((1u << a) - 1u);
+}
+
+// End of the chunk that starts at absolute byte c of a file ending at fend
+// (Sec. III.A-C, Sec. IV): the chunk limit is c + max_size (or the file end);
+// the scan starts min_size - SeqLength bytes in; a region ends at its first
+// run end (cut right after it) or at its SkipTrigger-th opposing pair, after
+// which SkipSize bytes are passed over and a new region starts.  All lanes
+// of the warp call this together and get the same result.
+__device__ uint64_t chunk_end_warp(const WGeom &g, const DevParams &p, uint64_t c,
+                                   uint64_t fend, uint32_t &wins, bool &ok) {
+  const int lane = threadIdx.x & 31;
+  const uint64_t lim = (fend - c > p.mx) ? c + p.mx : fend;
+  uint64_t r = c + (p.mn > p.R ? p.mn - p.R : 0u);
+  if (r + 1 >= lim) return lim;
+  if (kPrefetch && lane == 0) {
+    const uint64_t a = (r + p.mn + 15) & ~15ull;
+    if (a + kPrefetch <= g.total)
+      asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(g.data + a),
+                   "r"(kPrefetch) : "memory");
+  }
+  uint32_t opp = 0;  // opposing pairs counted in the current region
+  uint64_t w0 = r & ~15ull;
+  uint32_t carry_b = 0, carry_t = 0;  // byte and T bits before w0 (continued region)
+  // Every window either ends the chunk, starts a region at least
+  // SkipSize + 2 bytes further on, or moves 1 KiB ahead, so a chunk of at
+  // most max_size bytes needs fewer windows than this bound.
+  const uint32_t max_windows = p.mx + 8u;
+  for (uint32_t it = 0; it < max_windows; ++it) {
+    ++wins;
+    const int64_t gb = (int64_t)w0 + 32 * lane;
+    const uint4 v0 = load16(g.data, gb, g.total);
+    const uint4 v1 = load16(g.data, gb + 16, g.total);
+    uint32_t prev = __shfl_up_sync(kFull, v1.w >> 24, 1);
+    if (lane == 0) prev = carry_b;
+    uint32_t Tw, Ow;
+    classify32(v0, v1, prev, p.mode, Tw, Ow);
+    uint32_t pt = __shfl_up_sync(kFull, Tw, 1);
+    if (lane == 0) pt = carry_t;
+    const uint32_t Ew = run_ends(pt, Tw, p.R);
+    const int32_t lb = 32 * lane;  // position of the lane's bit 0, relative to w0
+    const uint64_t span = lim - w0;
+    const int32_t hi = (int32_t)(span < (uint64_t)(kWin + 32) ? span : (uint64_t)(kWin + 32));
+    for (;;) {
+      // Region from r: run ends at j >= r + SeqLength - 1 (the whole run
+      // after r), opposing pairs (j-1, j) with j >= r + 1, all below lim.
+      const int32_t rr = (int32_t)((int64_t)r - (int64_t)w0);
+      const uint32_t em = Ew & bit_range(rr + (int32_t)p.R - 1 - lb, hi - lb);
+      const uint32_t eb = __ballot_sync(kFull, em != 0u);
+      int32_t epos = INT32_MAX;
+      if (eb) {
+        const int el = __ffs(eb) - 1;
+        const uint32_t x = __shfl_sync(kFull, em, el);
+        epos = 32 * el + __ffs(x) - 1;
+      }
+      int32_t opos = INT32_MAX;
+      uint32_t tot = 0;
+      if (p.T) {
+        const uint32_t om = Ow & bit_range(rr + 1 - lb, hi - lb);
+        const uint32_t cnt = __popc(om);
+        uint32_t s = cnt;
+        for (int d = 1; d < 32; d <<= 1) {
+          const uint32_t y = __shfl_up_sync(kFull, s, d);
+          if (lane >= d) s += y;
+        }
+        tot = __shfl_sync(kFull, s, 31);
+        const uint32_t need = p.T - opp;
+        if (tot >= need) {
+          const uint32_t ob = __ballot_sync(kFull, s >= need);
+          const int ol = __ffs(ob) - 1;
+          uint32_t bp = 0;
+          if (lane == ol) bp = nth_set_bit(om, need - (s - cnt));
+          bp = __shfl_sync(kFull, bp, ol);
+          opos = 32 * ol + (int32_t)bp;
+        }
+      }
+      if (epos < opos) return w0 + (uint64_t)epos + 1u;
+      if (opos != INT32_MAX) {
+        // Skip: the pair at opos fires; bytes opos+1 .. opos+SkipSize are
+        // passed over and the next region starts right after them.
+        r = w0 + (uint64_t)opos + 1u + p.S;
+        opp = 0;
+        if (r + 1 >= lim) return lim;
+        if (r + 1 < w0 + kWin) continue;
+        w0 = r & ~15ull;
+        carry_b = 0;
+        carry_t = 0;
+        break;
+      }
+      opp += tot;
+      if (w0 + kWin >= lim) return lim;
+      carry_b = __shfl_sync(kFull, v1.w >> 24, 31);
+      carry_t = __shfl_sync(kFull, Tw, 31);
+      w0 += kWin;
+      break;
+    }
+  }
+  ok = false;
+  return lim;
+}
+
+// ---------------------------------------------------------------------------
+// Spec walks.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kWalkThreads, kWalkMinBlocks)
+spec_kernel(WGeom g, DevParams p, WPtrs w) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t np = w.hdr->npieces;
+  uint32_t pieces = 0, chunks = 0, wins = 0;
+  bool ok = true;
+  for (;;) {
+    uint32_t t = 0;
+    if (lane == 0) t = atomicAdd(&w.hdr->ticket, 1u);
+    t = __shfl_sync(kFull, t, 0);
+    if (t >= np) break;
+    const uint32_t k = w.order[t];
+    const Piece pc = piece_of(g, w, p, k);
+    const uint64_t pe = pc.ps + pc.len;
+    uint32_t *out = w.spec + pc.lb;
+    uint64_t c = pc.ps;
+    uint32_t n = 0;
+    do {
+      c = chunk_end_warp(g, p, c, pc.fend, wins, ok);
+      if (n < pc.cap) {
+        if (lane == 0) out[n] = (uint32_t)(c - pc.ps);
+        ++n;
+      } else {
+        ok = false;
+        break;
+      }
+    } while (c < pe);
+    if (lane == 0) w.spec_n[k] = n;
+    ++pieces;
+    chunks += n;
+  }
+  if (lane == 0) {
+    atomicAdd(&w.hdr->stats[WS_PIECES], pieces);
+    atomicAdd(&w.hdr->stats[WS_SPEC_CHUNKS], chunks);
+    atomicAdd(&w.hdr->stats[WS_WINDOWS], wins);
+    if (!ok) set_status(w.hdr, SEQCDC_ECAPACITY);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Junction walks.
+// ---------------------------------------------------------------------------
+// Exit of piece k as its current results give it: the last cut of its spec
+// walk if its junction met that walk, else the junction walk's exit.
+__device__ __forceinline__ uint32_t exit_of(const WPtrs &w, uint32_t k, uint64_t lb) {
+  return w.jm[k] != kUnmerged ? w.spec[lb + w.spec_n[k] - 1u] : w.jexit[k];
+}
+
+// Walk piece k's chain from x (relative to the piece start) until it reaches
+// a cut of the piece's spec walk or leaves the piece; record where it
+// started, the cuts before the meeting cut, the meeting index or the exit.
+// Returns whether the walk met the spec walk.
+__device__ bool junction_walk(const WGeom &g, const DevParams &p, const WPtrs &w,
+                              uint32_t k, const Piece &pc, uint32_t x, uint32_t &chunks,
+                              uint32_t &wins, bool &ok) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t ns = w.spec_n[k];
+  const uint32_t *sp = w.spec + pc.lb;
+  uint32_t *jc = w.jcut + pc.lb;
+  uint32_t q = 0, n = 0, jm = kUnmerged, jexit = 0;
+  uint32_t rel = x;
+  if (x == 0) {
+    jm = 0;  // the spec walk starts at the input itself
+  } else {
+    bool done = false;
+    for (uint32_t it = 0; it <= pc.cap && !done; ++it) {
+      // First spec cut >= rel: both lists increase, so q only moves on.
+      for (uint32_t s = 0; s <= ns / 32u + 1u; ++s) {
+        const uint32_t v = q + lane < ns ? sp[q + lane] : kFull;
+        const uint32_t below = __ballot_sync(kFull, v < rel);
+        q += __popc(below);
+        if (below != kFull) break;
+      }
+      const uint32_t at = q < ns ? sp[q] : kFull;
+      if (at == rel) {
+        jm = q;
+        done = true;
+      } else if (rel >= pc.len) {
+        jexit = rel;
+        if (rel == pc.len) {  // a cut exactly at the piece end belongs to it
+          if (n < pc.cap) { if (lane == 0) jc[n] = rel; ++n; } else ok = false;
+        }
+        done = true;
+      } else {
+        if (n < pc.cap) { if (lane == 0) jc[n] = rel; ++n; } else { ok = false; done = true; }
+        if (!done) {
+          rel = (uint32_t)(chunk_end_warp(g, p, pc.ps + rel, pc.fend, wins, ok) - pc.ps);
+          ++chunks;
+        }
+      }
+    }
+    if (!done) ok = false;
+  }
+  if (lane == 0) {
+    w.jin[k] = x;
+    w.jn[k] = n;
+    w.jm[k] = jm;
+    w.jexit[k] = jexit;
+  }
+  __syncwarp();
+  return jm != kUnmerged;
+}
+
+__global__ void __launch_bounds__(kWalkThreads, kWalkMinBlocks)
+junction_kernel(WGeom g, DevParams p, WPtrs w) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t np = w.hdr->npieces;
+  uint32_t walks = 0, chunks = 0, unmerged = 0, wins = 0;
+  bool ok = true;
+  for (;;) {
+    uint32_t t = 0;
+    if (lane == 0) t = atomicAdd(&w.hdr->jticket, 1u);
+    t = __shfl_sync(kFull, t, 0);
+    if (t >= np) break;
+    const uint32_t k = w.order[t];
+    const Piece pc = piece_of(g, w, p, k);
+    if (pc.kl == 0) {  // a file's first piece: its spec walk is its chain
+      if (lane == 0) {
+        w.jin[k] = 0;
+        w.jn[k] = 0;
+        w.jm[k] = 0;
+        w.jexit[k] = 0;
+      }
+      continue;
+    }
+    // The previous piece is a full piece of the same file; its exit is at
+    // or after this piece's start.
+    const uint64_t lb_prev = pc.lb - g.fullcap;
+    const uint32_t x = w.spec[lb_prev + w.spec_n[k - 1] - 1u] - g.P;
+    const bool met = junction_walk(g, p, w, k, pc, x, chunks, wins, ok);
+    ++walks;
+    unmerged += met ? 0u : 1u;
+  }
+  if (lane == 0) {
+    atomicAdd(&w.hdr->stats[WS_JUNCTIONS], walks);
+    atomicAdd(&w.hdr->stats[WS_JCHUNKS], chunks);
+    atomicAdd(&w.hdr->stats[WS_UNMERGED], unmerged);
+    if (!ok) set_status(w.hdr, SEQCDC_ECAPACITY);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Verify and repair.
+// ---------------------------------------------------------------------------
+__global__ void wverify_kernel(WGeom g, DevParams p, WPtrs w) {
+  const uint32_t np = w.hdr->npieces;
+  uint32_t bad = 0;
+  for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < np;
+       k += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t f = w.piece_file[k];
+    const uint32_t kl = (uint32_t)k - w.piece_base[f];
+    if (kl == 0) continue;
+    const uint64_t lb_prev = w.list_base[f] + (uint64_t)(kl - 1u) * g.fullcap;
+    const uint32_t x = exit_of(w, (uint32_t)k - 1u, lb_prev) - g.P;
+    if (x != w.jin[k]) {
+      atomicMin(&w.first_bad[f], (uint32_t)k);
+      ++bad;
+    }
+  }
+  for (int d = 16; d; d >>= 1) bad += __shfl_down_sync(kFull, bad, d);
+  if ((threadIdx.x & 31) == 0 && bad) atomicAdd(&w.hdr->stats[WS_INCONSISTENT], bad);
+}
+
+// One warp per file (files taken in strides): from the first inconsistent
+// piece on, every piece whose junction input differs from its predecessor's
+// exit walks again from that exit.  Pieces are taken in order, so each input
+// is the true exit of the piece before.
+__global__ void __launch_bounds__(kWalkThreads)
+wrepair_kernel(WGeom g, DevParams p, WPtrs w) {
+  const int lane = threadIdx.x & 31;
+  const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  uint32_t redone = 0, chunks = 0, wins = 0;
+  bool ok = true;
+  for (uint64_t f = warp; f < g.nfiles; f += nwarps) {
+    const uint32_t kb = w.first_bad[f];
+    if (kb == kNoBad) continue;
+    const uint32_t kend = w.piece_base[f + 1];
+    for (uint32_t k = kb; k < kend; ++k) {
+      const Piece pc = piece_of(g, w, p, k);
+      const uint32_t x = exit_of(w, k - 1u, pc.lb - g.fullcap) - g.P;
+      if (x == w.jin[k]) continue;
+      junction_walk(g, p, w, k, pc, x, chunks, wins, ok);
+      ++redone;
+    }
+  }
+  if (lane == 0) {
+    if (redone) atomicAdd(&w.hdr->stats[WS_REPAIRED], redone);
+    if (!ok) set_status(w.hdr, SEQCDC_ECAPACITY);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Compaction.
+// ---------------------------------------------------------------------------
+// Cuts piece k owns: its junction cuts, then its spec cuts from the meeting
+// cut on that lie at or before the piece end.
+__device__ __forceinline__ uint32_t owned_cuts(const WPtrs &w, uint32_t k, const Piece &pc) {
+  const uint32_t n = w.jn[k], jm = w.jm[k];
+  if (jm == kUnmerged) return n;
+  const uint32_t ns = w.spec_n[k];
+  const uint32_t nle = ns - (w.spec[pc.lb + ns - 1u] > pc.len ? 1u : 0u);
+  return n + (nle > jm ? nle - jm : 0u);
+}
+
+__global__ void wcount_kernel(WGeom g, DevParams p, WPtrs w) {
+  __shared__ uint32_t red[32];
+  const uint32_t np = w.hdr->npieces;
+  const uint64_t k = (uint64_t)blockIdx.x * kPieceTile + threadIdx.x;
+  uint32_t v = 0;
+  if (threadIdx.x < kPieceTile && k < np) {
+    const Piece pc = piece_of(g, w, p, (uint32_t)k);
+    v = owned_cuts(w, (uint32_t)k, pc);
+    w.count[k] = v;
+  }
+  for (int d = 16; d; d >>= 1) v += __shfl_down_sync(kFull, v, d);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t s = 0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) s += red[q];
+    w.ctile[blockIdx.x] = s;
+  }
+}
+
+__global__ void wemit_kernel(WGeom g, DevParams p, WPtrs w, uint64_t *d_cuts, uint64_t cap,
+                             uint64_t *d_cut_offsets, uint64_t *d_count) {
+  __shared__ uint32_t scratch[32];
+  __shared__ uint64_t red64[32];
+  __shared__ uint64_t s_prefix;
+  __shared__ uint32_t offs[kPieceTile + 1];
+  const uint32_t np = w.hdr->npieces;
+  const uint64_t lo = (uint64_t)blockIdx.x * kPieceTile;
+  uint64_t part = 0;
+  for (uint64_t t = threadIdx.x; t < blockIdx.x; t += blockDim.x) part += w.ctile[t];
+  for (int d = 16; d; d >>= 1) part += __shfl_down_sync(kFull, part, d);
+  if ((threadIdx.x & 31) == 0) red64[threadIdx.x >> 5] = part;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint64_t s = 0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) s += red64[q];
+    s_prefix = s;
+  }
+  __syncthreads();
+  const uint64_t i = lo + threadIdx.x;
+  const uint32_t c = i < np ? w.count[i] : 0u;
+  uint32_t tot;
+  const uint32_t ex = block_excl_scan(c, scratch, &tot);
+  offs[threadIdx.x] = ex;
+  if (threadIdx.x == 0) offs[kPieceTile] = tot;
+  __syncthreads();
+  const uint64_t prefix = s_prefix;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int it = warp; it < kPieceTile; it += blockDim.x >> 5) {
+    const uint64_t k = lo + it;
+    if (k >= np) break;
+    const uint32_t n = w.count[k];
+    const uint64_t at = prefix + offs[it];
+    if (at + n > cap) {  // cannot happen for a correct cut list; never write past cap
+      if (lane == 0) set_status(w.hdr, SEQCDC_ECAPACITY);
+      continue;
+    }
+    const Piece pc = piece_of(g, w, p, (uint32_t)k);
+    const uint64_t fbase = (uint64_t)pc.kl * g.P;  // piece start, file-relative
+    const uint32_t nj = w.jn[k], jm = w.jm[k];
+    const uint32_t *jc = w.jcut + pc.lb;
+    const uint32_t *sp = w.spec + pc.lb + (jm == kUnmerged ? 0u : jm);
+    uint64_t *dst = d_cuts + at;
+    for (uint32_t j = lane; j < n; j += 32)
+      dst[j] = fbase + (j < nj ? jc[j] : sp[j - nj]);
+  }
+  // CSR offsets of the files whose first piece index falls in [lo, lo+tile).
+  const uint64_t hi = lo + kPieceTile;
+  if (lo <= np) {
+    uint64_t a = 0, b = g.nfiles + 1;  // lower_bound(piece_base, lo)
+    while (a < b) {
+      const uint64_t mid = (a + b) >> 1;
+      if (w.piece_base[mid] < lo) a = mid + 1; else b = mid;
+    }
+    for (uint64_t f = a + threadIdx.x; f <= g.nfiles; f += blockDim.x) {
+      const uint32_t sb = w.piece_base[f];
+      if (sb >= hi) break;
+      const uint64_t v = prefix + offs[sb - lo];
+      if (d_cut_offsets) d_cut_offsets[f] = v;
+      if (d_count && f == g.nfiles) *d_count = v;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host side.
+// ---------------------------------------------------------------------------
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+struct WLayout {
+  size_t hdr, piece_base, list_base, ftile, ftile_l, piece_file, order, spec_n, spec, jin,
+      jn, jm, jexit, jcut, first_bad, count, ctile, total;
+  uint64_t npmax, nlist, nftiles, nctiles;
+  uint32_t P, fullcap;
+};
+
+WLayout make_wlayout(const seqcdc_params_t *p, uint64_t total, uint64_t nfiles, uint32_t P) {
+  WLayout l{};
+  l.P = P;
+  l.fullcap = list_cap(P, (uint32_t)p->min_size);
+  l.npmax = total / P + nfiles + 1;
+  // Per file: (n / P) full lists plus one for the tail; summed over files at
+  // most total / min_size + 3 (total / P + nfiles).
+  l.nlist = total / p->min_size + 3 * l.npmax;
+  l.nftiles = (nfiles + kFileTile - 1) / kFileTile;
+  if (l.nftiles == 0) l.nftiles = 1;
+  l.nctiles = (l.npmax + 1 + kPieceTile - 1) / kPieceTile;
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    const size_t at = o;
+    o = align_up(o + bytes, 256);
+    return at;
+  };
+  l.hdr = take(sizeof(WalkHeader));
+  l.piece_base = take((nfiles + 1) * 4);
+  l.list_base = take((nfiles + 1) * 8);
+  l.ftile = take(l.nftiles * 4);
+  l.ftile_l = take(l.nftiles * 8);
+  l.piece_file = take(l.npmax * 4);
+  l.order = take(l.npmax * 4);
+  l.spec_n = take(l.npmax * 4);
+  l.spec = take(l.nlist * 4);
+  l.jin = take(l.npmax * 4);
+  l.jn = take(l.npmax * 4);
+  l.jm = take(l.npmax * 4);
+  l.jexit = take(l.npmax * 4);
+  l.jcut = take(l.nlist * 4);
+  l.first_bad = take((nfiles + 1) * 4);
+  l.count = take(l.npmax * 4);
+  l.ctile = take(l.nctiles * 4);
+  l.total = o;
+  return l;
+}
+
+WPtrs wptrs(void *d_ws, const WLayout &l) {
+  char *b = static_cast<char *>(d_ws);
+  WPtrs w;
+  w.hdr = reinterpret_cast<WalkHeader *>(b + l.hdr);
+  w.piece_base = reinterpret_cast<uint32_t *>(b + l.piece_base);
+  w.list_base = reinterpret_cast<uint64_t *>(b + l.list_base);
+  w.ftile = reinterpret_cast<uint32_t *>(b + l.ftile);
+  w.ftile_l = reinterpret_cast<uint64_t *>(b + l.ftile_l);
+  w.piece_file = reinterpret_cast<uint32_t *>(b + l.piece_file);
+  w.order = reinterpret_cast<uint32_t *>(b + l.order);
+  w.spec_n = reinterpret_cast<uint32_t *>(b + l.spec_n);
+  w.spec = reinterpret_cast<uint32_t *>(b + l.spec);
+  w.jin = reinterpret_cast<uint32_t *>(b + l.jin);
+  w.jn = reinterpret_cast<uint32_t *>(b + l.jn);
+  w.jm = reinterpret_cast<uint32_t *>(b + l.jm);
+  w.jexit = reinterpret_cast<uint32_t *>(b + l.jexit);
+  w.jcut = reinterpret_cast<uint32_t *>(b + l.jcut);
+  w.first_bad = reinterpret_cast<uint32_t *>(b + l.first_bad);
+  w.count = reinterpret_cast<uint32_t *>(b + l.count);
+  w.ctile = reinterpret_cast<uint32_t *>(b + l.ctile);
+  return w;
+}
+
+}  // namespace
+
+namespace seqcdc_walk {
+
+uint32_t pick_piece(const seqcdc_params_t *p, const seqcdc_tuning_t *t) {
+  uint64_t P = (t && t->piece_bytes) ? t->piece_bytes : kDefaultPiece;
+  const uint64_t floor = p ? 4u * p->max_size : 0u;
+  if (P < floor) P = floor;
+  P = (P + 65535u) & ~(uint64_t)65535u;
+  if (P > (64u << 20)) P = 64u << 20;
+  return (uint32_t)P;
+}
+
+size_t workspace_bytes(const seqcdc_params_t *p, uint64_t total, uint64_t nfiles,
+                       uint32_t piece) {
+  return make_wlayout(p, total, nfiles, piece).total;
+}
+
+int run(const seqcdc_params_t *p, const uint8_t *d_data, uint64_t total,
+        const uint64_t *d_offsets, uint64_t nfiles, uint64_t *d_cuts, uint64_t cap,
+        uint64_t *d_cut_offsets, uint64_t *d_count, void *d_ws, size_t ws_bytes,
+        uint32_t piece, int sms, void *stream, void *prof_begin, void *prof_end) {
+  const WLayout l = make_wlayout(p, total, nfiles, piece);
+  if (l.npmax >= 0xffffffffull || nfiles >= 0xffffffffull) return SEQCDC_ERANGE;
+  if (ws_bytes < l.total) return SEQCDC_ECAPACITY;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const WPtrs w = wptrs(d_ws, l);
+  const WGeom g{d_data, total, d_offsets, nfiles, l.P, l.fullcap};
+  const DevParams dp{p->mode, p->seq_length, p->skip_trigger, p->skip_size,
+                     (uint32_t)p->min_size, (uint32_t)p->max_size};
+  wplan_tiles_kernel<<<(unsigned)l.nftiles, 256, 0, st>>>(g, dp, w);
+  wplan_scan_kernel<<<(unsigned)l.nftiles, 256, 0, st>>>(g, dp, w, l.nftiles);
+  wfill_kernel<<<(unsigned)((l.npmax + 255) / 256), 256, 0, st>>>(g, w);
+  // Persistent walk grids: up to 16 blocks of four warps per SM; warps take
+  // pieces from a queue, so blocks that do not fit only find it empty.
+  const uint64_t want = (l.npmax + 3) / 4;
+  const uint64_t most = 16u * (uint64_t)sms;
+  const unsigned wgrid = (unsigned)(want < most ? want : most);
+  if (prof_begin) cudaEventRecord(static_cast<cudaEvent_t>(prof_begin), st);
+  spec_kernel<<<wgrid, kWalkThreads, 0, st>>>(g, dp, w);
+  if (prof_end) cudaEventRecord(static_cast<cudaEvent_t>(prof_end), st);
+  junction_kernel<<<wgrid, kWalkThreads, 0, st>>>(g, dp, w);
+  const uint64_t vb = (l.npmax + 255) / 256;
+  wverify_kernel<<<(unsigned)(vb < 4096 ? vb : 4096), 256, 0, st>>>(g, dp, w);
+  const uint64_t rb = (nfiles + 3) / 4;
+  const uint64_t rcap = 4u * (uint64_t)sms;
+  wrepair_kernel<<<(unsigned)(rb < rcap ? (rb ? rb : 1) : rcap), kWalkThreads, 0, st>>>(g, dp, w);
+  wcount_kernel<<<(unsigned)l.nctiles, kPieceTile, 0, st>>>(g, dp, w);
+  wemit_kernel<<<(unsigned)l.nctiles, kPieceTile, 0, st>>>(g, dp, w, d_cuts, cap,
+                                                           d_cut_offsets, d_count);
+  return cudaGetLastError() == cudaSuccess ? SEQCDC_OK : SEQCDC_ECUDA;
+}
+
+}  // namespace seqcdc_walk

@@ -55,11 +55,21 @@ class Params(ctypes.Structure):
                 "min_size=%d, max_size=%d)" % self.astuple())
 
 
+ALGO_AUTO = 0
+ALGO_MAP = 1
+ALGO_WALK = 2
+WALK_MIN_FILES = 256   # SEQCDC_WALK_MIN_FILES: AUTO takes the chain walk from here
+
+
 class Tuning(ctypes.Structure):
-    """``seqcdc_tuning_t``: segment_bytes, block_threads (0 = default)."""
+    """``seqcdc_tuning_t``: segment_bytes, block_threads (segment map),
+    algorithm (ALGO_AUTO / ALGO_MAP / ALGO_WALK), piece_bytes (chain walk);
+    0 = default."""
 
     _fields_ = [("segment_bytes", ctypes.c_uint32),
-                ("block_threads", ctypes.c_uint32)]
+                ("block_threads", ctypes.c_uint32),
+                ("algorithm", ctypes.c_uint32),
+                ("piece_bytes", ctypes.c_uint32)]
 
 
 _lib = None
@@ -123,8 +133,8 @@ def _tuning(tuning):
         return None
     if isinstance(tuning, Tuning):
         return ctypes.byref(tuning)
-    seg, thr = tuning
-    return ctypes.byref(Tuning(int(seg), int(thr)))
+    # (segment_bytes, block_threads[, algorithm[, piece_bytes]])
+    return ctypes.byref(Tuning(*(int(v) for v in tuning)))
 
 
 def _stream_handle(stream) -> int:
@@ -161,7 +171,8 @@ def seqcdc_validate(p: Params) -> int:
 
 
 def seqcdc_resolve_tuning(p: Params, tuning=None) -> Tuning:
-    """Segment size and block size a call with this tuning runs with."""
+    """Segment size, block size and piece size a call with this tuning runs
+    with (the algorithm as given)."""
     out = Tuning()
     _check(load_library().seqcdc_resolve_tuning(ctypes.byref(p), _tuning(tuning),
                                                 ctypes.byref(out)),

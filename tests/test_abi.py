@@ -62,11 +62,14 @@ def test_validate_rejects(seqcdc_lib, bad):
 
 
 def test_workspace_size_grows(seqcdc_lib):
-    p = seqcdc_lib.seqcdc_params(8, 0)
-    a = seqcdc_lib.seqcdc_workspace_size(p, 1 << 20, 1)
-    b = seqcdc_lib.seqcdc_workspace_size(p, 1 << 30, 1)
-    c = seqcdc_lib.seqcdc_workspace_size(p, 1 << 30, 10000)
-    assert 0 < a < b < c
+    s = seqcdc_lib
+    p = s.seqcdc_params(8, 0)
+    for algo in (s.ALGO_MAP, s.ALGO_WALK):
+        t = (0, 0, algo, 0)
+        a = s.seqcdc_workspace_size(p, 1 << 20, 1, t)
+        b = s.seqcdc_workspace_size(p, 1 << 30, 1, t)
+        c = s.seqcdc_workspace_size(p, 1 << 30, 10000, t)
+        assert 0 < a < b < c
 
 
 def test_host_side_errors_before_launch(seqcdc_lib):
@@ -113,3 +116,35 @@ def test_resolve_tuning_defaults_and_rules(seqcdc_lib):
     assert t.segment_bytes <= 1 << 20 and t.segment_bytes % 1024 == 0
     with pytest.raises(s.SeqCDCError):
         s.seqcdc_resolve_tuning(s.Params(2, 5, 50, 256, 4096, 16384))
+
+
+def test_resolve_tuning_piece_rules(seqcdc_lib):
+    """Chain-walk piece size: default 1 MiB; rounded up to 64 KiB; at least
+    4 x max_size; at most 64 MiB.  The algorithm field is passed through."""
+    s = seqcdc_lib
+    p8, p16 = s.seqcdc_params(8, 0), s.seqcdc_params(16, 0)
+    t = s.seqcdc_resolve_tuning(p8)
+    assert t.piece_bytes == 1 << 20 and t.algorithm == s.ALGO_AUTO
+    t = s.seqcdc_resolve_tuning(p8, (0, 0, s.ALGO_WALK, 100000))
+    assert t.piece_bytes == 131072 and t.algorithm == s.ALGO_WALK
+    assert s.seqcdc_resolve_tuning(p8, (0, 0, 2, 65536)).piece_bytes == 65536
+    assert s.seqcdc_resolve_tuning(p16, (0, 0, 2, 65536)).piece_bytes == 131072
+    assert s.seqcdc_resolve_tuning(p8, (0, 0, 2, 1 << 30)).piece_bytes == 64 << 20
+    assert s.seqcdc_resolve_tuning(p8, (0, 0, s.ALGO_MAP, 0)).algorithm == s.ALGO_MAP
+
+
+def test_workspace_follows_the_path(seqcdc_lib):
+    """A batch of at least SEQCDC_WALK_MIN_FILES files takes the chain walk by
+    default and sizes its workspace for it; forcing either path sizes for
+    that path; a single stream is sized for the path it may take."""
+    s = seqcdc_lib
+    p = s.seqcdc_params(8, 0)
+    total, many, few = 8 << 30, s.WALK_MIN_FILES, s.WALK_MIN_FILES - 1
+    walk = s.seqcdc_workspace_size(p, total, many, (0, 0, s.ALGO_WALK, 0))
+    smap = s.seqcdc_workspace_size(p, total, many, (0, 0, s.ALGO_MAP, 0))
+    assert walk < smap
+    assert s.seqcdc_workspace_size(p, total, many) == walk
+    assert s.seqcdc_workspace_size(p, total, few) == \
+        s.seqcdc_workspace_size(p, total, few, (0, 0, s.ALGO_MAP, 0))
+    # 8 GiB in 1 MiB pieces: the walk's lists take a few bytes per input KiB
+    assert walk < total // 64

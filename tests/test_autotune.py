@@ -13,13 +13,28 @@ def test_candidates_respect_max_size_and_library_rules(seqcdc_lib):
     s = seqcdc_lib
     p = s.seqcdc_params(16, 0)                    # max_size 32 KiB
     c = A.candidates(p)
-    assert c and all(L >= p.max_size for L, _ in c)
-    assert {t for _, t in c} == {128, 256, 512}
-    for L, t in c:
-        e = s.seqcdc_resolve_tuning(p, (L, t))
+    maps = [x for x in c if x[2] == s.ALGO_MAP]
+    walks = [x for x in c if x[2] == s.ALGO_WALK]
+    assert maps and all(L >= p.max_size for L, _, _, _ in maps)
+    assert {t for _, t, _, _ in maps} == {128, 256, 512}
+    for L, t, a, P in maps:
+        e = s.seqcdc_resolve_tuning(p, (L, t, a, P))
         assert (e.segment_bytes, e.block_threads) == (L, t)
+    # pieces below 4 x max_size (128 KiB here) are not candidates
+    assert walks and all(P >= 4 * p.max_size for _, _, _, P in walks)
+    for x in walks:
+        assert s.seqcdc_resolve_tuning(p, x).piece_bytes == x[3]
     p4 = s.seqcdc_params(4, 0)
-    assert (32768, 256) in A.candidates(p4)
+    assert (32768, 256, s.ALGO_MAP, 0) in A.candidates(p4)
+    assert (0, 0, s.ALGO_WALK, 262144) in A.candidates(p4)
+
+
+def test_default_candidate_follows_auto_rule(seqcdc_lib):
+    s = seqcdc_lib
+    p = s.seqcdc_params(8, 0)
+    assert A.default_candidate(p, s.WALK_MIN_FILES) == (0, 0, s.ALGO_WALK, 1 << 20)
+    assert A.default_candidate(p, s.WALK_MIN_FILES - 1) == (65536, 256, s.ALGO_MAP, 0)
+    assert A.default_candidate(p, 1000, batch=False)[2] == s.ALGO_MAP
 
 
 def test_workload_key_separates_shapes(seqcdc_lib):
@@ -28,12 +43,17 @@ def test_workload_key_separates_shapes(seqcdc_lib):
     k2 = A.workload_key("GPU", 152, p, [1 << 18] * 9)
     k3 = A.workload_key("GPU", 148, p, [1 << 20])
     k4 = A.workload_key("GPU", 152, seqcdc_lib.seqcdc_params(8, 1), [1 << 20])
-    assert len({k1, k2, k3, k4}) == 4
+    k5 = A.workload_key("GPU", 152, p, [1 << 18] * 900)
+    assert len({k1, k2, k3, k4, k5}) == 5
     assert A.workload_key("GPU", 152, p, [300000] * 5) == A.workload_key("GPU", 152, p, [270000] * 7)
+    assert A.workload_key("GPU", 152, p, [1 << 18]).startswith(A.CACHE_VERSION + "|")
 
 
 def test_pick_best_and_ties():
     t = {(65536, 256): 2.0, (32768, 128): 1.5, (131072, 512): 1.5}
+    w = {(65536, 256, 1, 0): 2.0, (0, 0, 2, 1 << 20): 1.0, (0, 0, 2, 1 << 19): 1.002}
+    assert A.pick_best(w, default=(0, 0, 2, 1 << 20)) == (0, 0, 2, 1 << 20)
+    assert A.pick_best(w) == (0, 0, 2, 1 << 19)
     assert A.pick_best(t) == (32768, 128)
     assert A.pick_best(t, default=(65536, 256)) == (32768, 128)     # default too slow
     t2 = {(65536, 256): 1.005, (131072, 512): 1.0, (32768, 128): 1.3}
@@ -45,10 +65,10 @@ def test_pick_best_and_ties():
 def test_cache_roundtrip(tmp_path):
     path = str(tmp_path / "sub" / "tuning.json")
     assert A.load_cache(path) == {}
-    A.store_cache(path, "k1", {"segment_bytes": 65536, "block_threads": 256})
-    A.store_cache(path, "k2", {"segment_bytes": 131072, "block_threads": 512})
+    A.store_cache(path, "k1", {"tuning": [65536, 256, 1, 0]})
+    A.store_cache(path, "k2", {"tuning": [0, 0, 2, 1 << 20]})
     d = json.load(open(path))
-    assert d["k1"]["segment_bytes"] == 65536 and d["k2"]["block_threads"] == 512
+    assert d["k1"]["tuning"] == [65536, 256, 1, 0] and d["k2"]["tuning"][3] == 1 << 20
     (tmp_path / "bad.json").write_text("not json")
     assert A.load_cache(str(tmp_path / "bad.json")) == {}
 
@@ -63,7 +83,7 @@ def test_autotune_times_once_then_hits_cache(gpu, tmp_path):
     d = torch.from_numpy(data).cuda()
     o = torch.from_numpy(offs.astype(np.int64)).cuda()
     path = str(tmp_path / "t.json")
-    cands = [(65536, 256), (131072, 512), (32768, 128)]
+    cands = [(65536, 256, 1, 0), (131072, 512, 1, 0), (0, 0, 2, 1 << 18)]
     calls = []
 
     def timer(p_, d_, o_, c):
