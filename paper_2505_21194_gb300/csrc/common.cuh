@@ -134,6 +134,21 @@ __device__ __forceinline__ void classify32(uint4 v0, uint4 v1, uint32_t prev_byt
   Ow = mode == 0 ? dn : up;
 }
 
+// 16 bytes with the byte before them -> T and O bits of the 16 positions
+// (bits 0..15; bit t = pair (byte t-1, byte t)).
+__device__ __forceinline__ void classify16(uint4 v, uint32_t prev_byte, uint32_t mode,
+                                           uint32_t &T, uint32_t &Ow) {
+  uint32_t g0, l0, g1, l1, g2, l2, g3, l3;
+  cmp_word(v.x, (v.x << 8) | (prev_byte & 0xffu), g0, l0);
+  cmp_word(v.y, __funnelshift_l(v.x, v.y, 8), g1, l1);
+  cmp_word(v.z, __funnelshift_l(v.y, v.z, 8), g2, l2);
+  cmp_word(v.w, __funnelshift_l(v.z, v.w, 8), g3, l3);
+  const uint32_t up = gather8(g0, g1) | (gather8(g2, g3) << 8);
+  const uint32_t dn = gather8(l0, l1) | (gather8(l2, l3) << 8);
+  T = mode == 0 ? up : dn;
+  Ow = mode == 0 ? dn : up;
+}
+
 // E at position t needs T at t, t-1, ..., t-(R-2); `pt` holds the T bits of
 // the 32 positions before.
 __device__ __forceinline__ uint32_t run_ends(uint32_t pt, uint32_t T, uint32_t R) {

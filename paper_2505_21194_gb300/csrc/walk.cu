@@ -12,19 +12,19 @@
 //
 // The chain is sequential, so parallelism comes from many chains at once:
 //   plan      split every file into pieces of P bytes (P >= 4 max_size).
-//   spec      one warp per piece walks the chain from the piece start as if
-//             a chunk began there, up to the first cut at or after the piece
-//             end (the piece's exit).  For a file's first piece this is the
-//             true chain.
-//   junction  one warp per later piece: from the exit of the previous
-//             piece's walk, walk the chain until it reaches a cut of this
-//             piece's own walk.  The chunk after a cut depends only on that
-//             cut, so from the meeting cut on the two chains are the same.
+//   walk      one warp per piece (longest first) walks the chain from the
+//             piece start as if a chunk began there, up to the first cut at
+//             or after the piece end (the piece's exit); for a file's first
+//             piece this is the true chain.  The warp then walks on from that
+//             exit into the file's next piece (the next piece's junction
+//             walk) until it reaches a cut of that piece's own walk: the
+//             chunk after a cut depends only on the cut, so from the meeting
+//             cut on the two chains are the same.
 //   verify    a piece's junction started from the exit its predecessor's
-//             spec walk computed; where the predecessor's final exit differs
-//             (its own junction never met its walk) the piece is
-//             inconsistent.  A file without inconsistent pieces is exact by
-//             induction from its start.
+//             walk computed; where the predecessor's final exit differs (its
+//             own junction never met its walk) the piece is inconsistent.  A
+//             file without inconsistent pieces is exact by induction from its
+//             start.
 //   repair    one warp per file with an inconsistent piece redoes the
 //             junctions in order from the first such piece.
 //   compact   count each piece's cuts, exclusive scan, copy to the caller's
@@ -48,9 +48,10 @@ namespace {
 constexpr uint32_t kWin = 1024;        // bytes per warp window (32 per lane)
 constexpr int kWalkThreads = 128;      // walk kernels: four warps per block
 // Blocks of the walk kernels resident per SM that the register budget is
-// sized for (the walks are latency-bound: more warps, more chains in flight).
+// sized for: 8 blocks of 4 warps (the walks are bound by latency and issue;
+// this keeps 32 chains in flight per SM without spilling).
 #ifndef SEQCDC_WALK_MIN_BLOCKS
-#define SEQCDC_WALK_MIN_BLOCKS 1
+#define SEQCDC_WALK_MIN_BLOCKS 8
 #endif
 constexpr int kWalkMinBlocks = SEQCDC_WALK_MIN_BLOCKS;
 constexpr int kFileTile = 1024;        // files per plan block
@@ -59,23 +60,17 @@ constexpr uint32_t kUnmerged = 0xFFFFFFFFu;
 constexpr uint32_t kNoBad = 0xFFFFFFFFu;
 constexpr uint32_t kFull = 0xFFFFFFFFu;
 constexpr uint32_t kDefaultPiece = 1u << 20;
-// L2 prefetch ahead of each chunk: the next chunk's scan starts at least
-// min_size bytes after this chunk's scan start.
-#ifndef SEQCDC_WALK_PREFETCH
-#define SEQCDC_WALK_PREFETCH 2048
-#endif
-constexpr uint32_t kPrefetch = SEQCDC_WALK_PREFETCH;
+constexpr uint32_t kPrefetch = 2048;   // bytes asked of L2 for the next chunk's scan
 
 // Workspace header: status and statistics at the offsets seqcdc_status and
 // seqcdc_stats read.
 struct WalkHeader {
   uint32_t status;         // 0 or a SEQCDC_* error code
-  uint32_t ticket;         // spec-walk queue head
+  uint32_t ticket;         // piece-walk queue head
   uint32_t npieces;
   uint32_t stats[8];
-  uint32_t jticket;        // junction queue head
   uint32_t nlong, nshort;  // walk-order fill counters
-  uint32_t pad[50];
+  uint32_t pad[51];
 };
 static_assert(sizeof(WalkHeader) == 256, "walk header is 256 bytes");
 
@@ -87,7 +82,7 @@ enum : uint32_t {
   WS_UNMERGED = 4,      // junction walks that left their piece without meeting
   WS_INCONSISTENT = 5,  // pieces whose junction input was wrong
   WS_REPAIRED = 6,      // junction walks redone by the repair pass
-  WS_WINDOWS = 7,       // 1 KiB windows loaded by the spec walks
+  WS_WINDOWS = 7,       // 1 KiB windows the walks loaded
 };
 
 struct WGeom {
@@ -108,6 +103,7 @@ struct WPtrs {
   uint32_t *piece_file;  // per piece
   uint32_t *order;       // per piece: walk order (long pieces first)
   uint32_t *spec_n;      // per piece: cuts of its spec walk (the exit last)
+  uint32_t *sdone;       // per piece: 1 once its spec walk's cuts are published
   uint32_t *spec;        // list entries: spec-walk cuts, relative to the piece start
   uint32_t *jin;         // per piece: where its junction walk started (relative)
   uint32_t *jn;          // per piece: junction cuts before the meeting cut
@@ -285,7 +281,6 @@ __global__ void wplan_scan_kernel(WGeom g, DevParams p, WPtrs w, uint64_t nftile
     WalkHeader *h = w.hdr;
     h->status = 0;
     h->ticket = 0;
-    h->jticket = 0;
     h->npieces = running;
     h->nlong = 0;
     h->nshort = 0;
@@ -296,9 +291,12 @@ __global__ void wplan_scan_kernel(WGeom g, DevParams p, WPtrs w, uint64_t nftile
     w.first_bad[f] = kNoBad;
 }
 
-// piece_file of every piece, and the walk order: pieces of at least P/2
-// bytes first (filled from the front), shorter ones after them (filled from
-// the back), so the longest walks start in the first wave.
+// piece_file of every piece, and the walk order: first (filled from the
+// front) every piece of a file with several pieces and every piece of at
+// least P/2 bytes, then the short single-piece files (filled from the back).
+// The longest walks thus start in the first wave, and a piece's successor
+// is walked alongside it, so that its cuts are there when this piece's warp
+// walks on into it.
 __global__ void wfill_kernel(WGeom g, WPtrs w) {
   const uint32_t np = w.hdr->npieces;
   const uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -313,8 +311,10 @@ __global__ void wfill_kernel(WGeom g, WPtrs w) {
       if (w.piece_base[mid] <= k) a = mid; else b = mid - 1;
     }
     w.piece_file[k] = (uint32_t)a;
+    w.sdone[k] = 0u;
     const uint64_t ps = wfile_start(g, a) + (k - w.piece_base[a]) * (uint64_t)g.P;
-    longp = wfile_end(g, a) - ps >= (uint64_t)(g.P >> 1);
+    longp = w.piece_base[a + 1] - w.piece_base[a] > 1u ||
+            wfile_end(g, a) - ps >= (uint64_t)(g.P >> 1);
   }
   const int lane = threadIdx.x & 31;
   const uint32_t bl = __ballot_sync(kFull, live && longp);
@@ -336,13 +336,29 @@ __global__ void wfill_kernel(WGeom g, WPtrs w) {
 // ---------------------------------------------------------------------------
 // One chunk, one warp.
 // ---------------------------------------------------------------------------
-// Bits [a, b) of a 32-bit lane word (a, b relative to the lane's first bit).
-__device__ __forceinline__ uint32_t bit_range(int32_t a, int32_t b) {
-  a = a < 0 ? 0 : a;
-  b = b > 32 ? 32 : b;
-  if (a >= b) return 0u;
-  const uint32_t hi = b >= 32 ? kFull : ((1u << b) - 1u);
-  return hi & ~((1u << a) - 1u);
+// Bits 0 .. n-1 set (n >= 0; 32 and more: all).
+__device__ __forceinline__ uint32_t low_bits(int32_t n) {
+  return __funnelshift_lc(0xffffffffu, 0u, (uint32_t)(n < 0 ? 0 : n));
+}
+
+// A 1 KiB window of input held in registers: 16 bytes per lane in each of
+// its two 512-byte halves, starting at the 16-aligned absolute byte `base`.
+struct Win {
+  uint4 a, b;
+};
+
+__device__ __forceinline__ Win load_win(const WGeom &g, uint64_t base) {
+  const int lane = threadIdx.x & 31;
+  const uint64_t off = base + 16u * lane;
+  Win w;
+  if (off + 528u <= g.total) {
+    w.a = __ldg(reinterpret_cast<const uint4 *>(g.data + off));
+    w.b = __ldg(reinterpret_cast<const uint4 *>(g.data + off + 512u));
+  } else {
+    w.a = load16(g.data, (int64_t)off, g.total);
+    w.b = load16(g.data, (int64_t)(off + 512u), g.total);
+  }
+  return w;
 }
 
 // End of the chunk that starts at absolute byte c of a file ending at fend
@@ -351,106 +367,243 @@ __device__ __forceinline__ uint32_t bit_range(int32_t a, int32_t b) {
 // run end (cut right after it) or at its SkipTrigger-th opposing pair, after
 // which SkipSize bytes are passed over and a new region starts.  All lanes
 // of the warp call this together and get the same result.
+//
+// A window is 1 KiB loaded at once; a 512-byte half is classified only when
+// the scan reaches it.  Lane l's word of a half holds the half's positions
+// 16 l .. 16 l + 15 in bits 0..15.  Positions are 32-bit offsets from the
+// first window's start.  While the chunk is scanned, L2 is asked for the
+// 2 KiB where the next chunk's scan can start at the earliest (min_size
+// after this scan's start), where it does start for most chunks.
 __device__ uint64_t chunk_end_warp(const WGeom &g, const DevParams &p, uint64_t c,
                                    uint64_t fend, uint32_t &wins, bool &ok) {
   const int lane = threadIdx.x & 31;
-  const uint64_t lim = (fend - c > p.mx) ? c + p.mx : fend;
-  uint64_t r = c + (p.mn > p.R ? p.mn - p.R : 0u);
-  if (r + 1 >= lim) return lim;
-  if (kPrefetch && lane == 0) {
-    const uint64_t a = (r + p.mn + 15) & ~15ull;
+  const uint64_t rest = fend - c;
+  const uint64_t lim_abs = c + (rest > p.mx ? p.mx : rest);
+  const uint64_t r_abs = c + (p.mn > p.R ? p.mn - p.R : 0u);
+  if (r_abs + 1 >= lim_abs) return lim_abs;
+  if (lane == 0) {
+    const uint64_t a = (r_abs + p.mn + 15) & ~15ull;
     if (a + kPrefetch <= g.total)
       asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(g.data + a),
                    "r"(kPrefetch) : "memory");
   }
-  uint32_t opp = 0;  // opposing pairs counted in the current region
-  uint64_t w0 = r & ~15ull;
-  uint32_t carry_b = 0, carry_t = 0;  // byte and T bits before w0 (continued region)
+  const uint64_t cb = r_abs & ~15ull;
+  Win cur = load_win(g, cb);
+  ++wins;
+  const uint32_t lim = (uint32_t)(lim_abs - cb);
+  uint32_t r = (uint32_t)(r_abs - cb);
+  const int32_t lb = 16 * lane;     // the lane's first position in a half
+  uint32_t opp = 0;                 // opposing pairs counted in the current region
+  uint32_t w0 = 0;                  // window start
+  uint32_t carry_b = 0, carry_t = 0;  // byte and T bits before the half (continued region)
   // Every window either ends the chunk, starts a region at least
   // SkipSize + 2 bytes further on, or moves 1 KiB ahead, so a chunk of at
   // most max_size bytes needs fewer windows than this bound.
   const uint32_t max_windows = p.mx + 8u;
   for (uint32_t it = 0; it < max_windows; ++it) {
-    ++wins;
-    const int64_t gb = (int64_t)w0 + 32 * lane;
-    const uint4 v0 = load16(g.data, gb, g.total);
-    const uint4 v1 = load16(g.data, gb + 16, g.total);
-    uint32_t prev = __shfl_up_sync(kFull, v1.w >> 24, 1);
-    if (lane == 0) prev = carry_b;
-    uint32_t Tw, Ow;
-    classify32(v0, v1, prev, p.mode, Tw, Ow);
-    uint32_t pt = __shfl_up_sync(kFull, Tw, 1);
-    if (lane == 0) pt = carry_t;
-    const uint32_t Ew = run_ends(pt, Tw, p.R);
-    const int32_t lb = 32 * lane;  // position of the lane's bit 0, relative to w0
-    const uint64_t span = lim - w0;
-    const int32_t hi = (int32_t)(span < (uint64_t)(kWin + 32) ? span : (uint64_t)(kWin + 32));
-    for (;;) {
-      // Region from r: run ends at j >= r + SeqLength - 1 (the whole run
-      // after r), opposing pairs (j-1, j) with j >= r + 1, all below lim.
-      const int32_t rr = (int32_t)((int64_t)r - (int64_t)w0);
-      const uint32_t em = Ew & bit_range(rr + (int32_t)p.R - 1 - lb, hi - lb);
-      const uint32_t eb = __ballot_sync(kFull, em != 0u);
-      int32_t epos = INT32_MAX;
-      if (eb) {
-        const int el = __ffs(eb) - 1;
-        const uint32_t x = __shfl_sync(kFull, em, el);
-        epos = 32 * el + __ffs(x) - 1;
-      }
-      int32_t opos = INT32_MAX;
-      uint32_t tot = 0;
-      if (p.T) {
-        const uint32_t om = Ow & bit_range(rr + 1 - lb, hi - lb);
+    if (it) {
+      cur = load_win(g, cb + w0);
+      ++wins;
+    }
+    bool fresh = false;  // the next window starts a new region at r
+    // A region that starts inside the second half skips classifying the
+    // first (its first pair, (r, r + 1), then lies wholly in the second).
+    for (int h = (r >= w0 + 512u) ? 1 : 0; h < 2; ++h) {
+      const uint4 v = h ? cur.b : cur.a;
+      const uint32_t hb = w0 + 512u * h;  // half start (< lim)
+      uint32_t prev = __shfl_up_sync(kFull, v.w >> 24, 1);
+      if (lane == 0) prev = carry_b;
+      uint32_t Tw, Ow;
+      classify16(v, prev, p.mode, Tw, Ow);
+      uint32_t pt = __shfl_up_sync(kFull, Tw, 1);
+      if (lane == 0) pt = carry_t;
+      // The run ends of this lane's 16 positions look back into the 16 before.
+      const uint32_t Ew = run_ends(0u, (Tw << 16) | (pt & 0xffffu), p.R) >> 16;
+      carry_b = __shfl_sync(kFull, v.w >> 24, 31);
+      carry_t = __shfl_sync(kFull, Tw, 31);
+      const uint32_t span = lim - hb;
+      const uint32_t hmask = low_bits((int32_t)(span < 1024u ? span : 1024u) - lb);  // pairs j < lim
+      bool moved = false;  // a skip moved r past this half
+      for (;;) {
+        // Region from r: run ends at j >= r + SeqLength - 1 (the whole run
+        // after r), opposing pairs (j-1, j) with j >= r + 1, all below lim.
+        const int32_t rr = (int32_t)(r - hb);
+        const uint32_t em = Ew & hmask & ~low_bits(rr + (int32_t)p.R - 1 - lb);
+        const uint32_t om = Ow & hmask & ~low_bits(rr + 1 - lb);
+        const uint32_t eb = __ballot_sync(kFull, em != 0u);
+        uint32_t need = 0;  // nonzero: the need-th opposing pair here fires a skip
+        if (eb) {
+          const int el = __ffs(eb) - 1;
+          const uint32_t ebit = __ffs(__shfl_sync(kFull, em, el)) - 1;
+          if (p.T) {
+            const uint32_t ob = lane < el ? om : (lane == el ? (om & ((1u << ebit) - 1u)) : 0u);
+            const uint32_t before = __reduce_add_sync(kFull, (uint32_t)__popc(ob));
+            if (opp + before >= p.T) need = p.T - opp;
+          }
+          if (!need) return cb + hb + 16u * el + ebit + 1u;
+        } else if (p.T) {
+          const uint32_t tot = __reduce_add_sync(kFull, (uint32_t)__popc(om));
+          if (opp + tot >= p.T) need = p.T - opp;
+          else opp += tot;
+        }
+        if (!need) break;  // the region goes on past this half
+        // Skip: the need-th opposing pair fires; bytes after it up to
+        // SkipSize are passed over and the next region starts after them.
         const uint32_t cnt = __popc(om);
-        uint32_t s = cnt;
+        uint32_t sc = cnt;
         for (int d = 1; d < 32; d <<= 1) {
-          const uint32_t y = __shfl_up_sync(kFull, s, d);
-          if (lane >= d) s += y;
+          const uint32_t y = __shfl_up_sync(kFull, sc, d);
+          if (lane >= d) sc += y;
         }
-        tot = __shfl_sync(kFull, s, 31);
-        const uint32_t need = p.T - opp;
-        if (tot >= need) {
-          const uint32_t ob = __ballot_sync(kFull, s >= need);
-          const int ol = __ffs(ob) - 1;
-          uint32_t bp = 0;
-          if (lane == ol) bp = nth_set_bit(om, need - (s - cnt));
-          bp = __shfl_sync(kFull, bp, ol);
-          opos = 32 * ol + (int32_t)bp;
-        }
-      }
-      if (epos < opos) return w0 + (uint64_t)epos + 1u;
-      if (opos != INT32_MAX) {
-        // Skip: the pair at opos fires; bytes opos+1 .. opos+SkipSize are
-        // passed over and the next region starts right after them.
-        r = w0 + (uint64_t)opos + 1u + p.S;
+        const int ol = __ffs(__ballot_sync(kFull, sc >= need)) - 1;
+        uint32_t bp = 0;
+        if (lane == ol) bp = nth_set_bit(om, need - (sc - cnt));
+        bp = __shfl_sync(kFull, bp, ol);
+        const uint64_t rn = (uint64_t)hb + 16u * ol + bp + 1u + p.S;
         opp = 0;
-        if (r + 1 >= lim) return lim;
-        if (r + 1 < w0 + kWin) continue;
-        w0 = r & ~15ull;
-        carry_b = 0;
-        carry_t = 0;
+        if (rn + 1 >= lim) return cb + lim;
+        r = (uint32_t)rn;
+        if (r + 1 < hb + 512u) continue;  // the next region starts in this half
+        moved = true;
         break;
       }
-      opp += tot;
-      if (w0 + kWin >= lim) return lim;
-      carry_b = __shfl_sync(kFull, v1.w >> 24, 31);
-      carry_t = __shfl_sync(kFull, Tw, 31);
-      w0 += kWin;
+      if (!moved) {
+        // No event: the region continues into the bytes after this half.
+        if (hb + 512u >= lim) return cb + lim;
+        continue;  // next half, or (after half 1) the next window
+      }
+      if (h == 0 && r + 1 < w0 + 1024u) continue;  // the new region starts in half 1
+      fresh = true;
       break;
+    }
+    if (fresh) {
+      w0 = r & ~15u;
+      carry_b = 0;
+      carry_t = 0;
+    } else {
+      w0 += 1024u;
     }
   }
   ok = false;
-  return lim;
+  return cb + lim;
 }
 
 // ---------------------------------------------------------------------------
-// Spec walks.
+// Junction walks.
+// ---------------------------------------------------------------------------
+// Exit of piece k as its current results give it: the last cut of its spec
+// walk if its junction met that walk, else the junction walk's exit.
+__device__ __forceinline__ uint32_t exit_of(const WPtrs &w, uint32_t k, uint64_t lb) {
+  return w.jm[k] != kUnmerged ? w.spec[lb + w.spec_n[k] - 1u] : w.jexit[k];
+}
+
+// Index of the first of sp[q..ns) that is >= v (the warp reads 32 at a time;
+// the list increases).  Reads bypass L1: the list may have been written
+// during this kernel by another SM.
+__device__ __forceinline__ uint32_t seek(const uint32_t *sp, uint32_t ns, uint32_t q,
+                                         uint32_t v) {
+  const int lane = threadIdx.x & 31;
+  for (uint32_t s = 0; s <= ns / 32u + 1u; ++s) {
+    const uint32_t e = q + lane < ns ? __ldcg(sp + q + lane) : kFull;
+    const uint32_t below = __ballot_sync(kFull, e < v);
+    q += __popc(below);
+    if (below != kFull) break;
+  }
+  return q;
+}
+
+// Walk piece k's chain from x (relative to the piece start) until it reaches
+// a cut of the piece's spec walk or leaves the piece; record where it
+// started, the cuts before the meeting cut, the meeting index or the exit.
+// With `done` set, the piece's spec walk may still be running (another warp):
+// its cuts are compared once done[k] is set, the cuts walked before that
+// first, in order.  Returns whether the walk met the spec walk.
+__device__ bool junction_walk(const WGeom &g, const DevParams &p, const WPtrs &w,
+                              uint32_t k, const Piece &pc, uint32_t x, const uint32_t *done,
+                              uint32_t &chunks, uint32_t &wins, bool &ok) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t *sp = w.spec + pc.lb;
+  uint32_t *jc = w.jcut + pc.lb;
+  bool have = done == nullptr;
+  uint32_t ns = have ? __ldcg(w.spec_n + k) : 0u;
+  uint32_t q = 0, n = 0, checked = 0, jm = kUnmerged, jexit = 0;
+  uint32_t rel = x;
+  if (x == 0) {
+    jm = 0;  // the spec walk starts at the input itself
+  } else {
+    bool fin = false;
+    for (uint32_t it = 0; it <= pc.cap && !fin; ++it) {
+      if (!have) {
+        uint32_t f = 0;
+        if (lane == 0) f = ld_acquire(done + k);
+        have = __shfl_sync(kFull, f, 0) != 0u;
+        if (have) {
+          ns = __ldcg(w.spec_n + k);
+          __syncwarp();
+          for (; checked < n; ++checked) {  // cuts walked before the spec walk was known
+            const uint32_t u = __ldcg(jc + checked);
+            q = seek(sp, ns, q, u);
+            if (q < ns && __ldcg(sp + q) == u) {
+              jm = q;
+              n = checked;
+              fin = true;
+              break;
+            }
+          }
+          if (fin) break;
+        }
+      }
+      if (have) {
+        q = seek(sp, ns, q, rel);
+        if (q < ns && __ldcg(sp + q) == rel) {
+          jm = q;
+          break;
+        }
+      }
+      if (rel >= pc.len) {
+        jexit = rel;
+        if (rel == pc.len) {  // a cut exactly at the piece end belongs to it
+          if (n < pc.cap) { if (lane == 0) jc[n] = rel; ++n; } else ok = false;
+        }
+        fin = true;
+        break;
+      }
+      if (n < pc.cap) {
+        if (lane == 0) jc[n] = rel;
+        ++n;
+      } else {
+        ok = false;
+        fin = true;
+        break;
+      }
+      if (have) checked = n;
+      rel = (uint32_t)(chunk_end_warp(g, p, pc.ps + rel, pc.fend, wins, ok) - pc.ps);
+      ++chunks;
+    }
+    if (!fin && jm == kUnmerged) ok = false;
+  }
+  if (lane == 0) {
+    w.jin[k] = x;
+    w.jn[k] = n;
+    w.jm[k] = jm;
+    w.jexit[k] = jexit;
+  }
+  __syncwarp();
+  return jm != kUnmerged;
+}
+
+// ---------------------------------------------------------------------------
+// Piece walks: one warp per piece, longest first.  A warp walks its piece's
+// chain from the piece start (the spec walk), publishes it, and then walks
+// on from the exit into the file's next piece as that piece's junction walk:
+// the exit is where the true chain enters the next piece whenever this
+// piece's own junction met its spec walk.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kWalkThreads, kWalkMinBlocks)
-spec_kernel(WGeom g, DevParams p, WPtrs w) {
+walk_kernel(WGeom g, DevParams p, WPtrs w) {
   const int lane = threadIdx.x & 31;
   const uint32_t np = w.hdr->npieces;
-  uint32_t pieces = 0, chunks = 0, wins = 0;
+  uint32_t pieces = 0, chunks = 0, wins = 0, walks = 0, jchunks = 0, unmerged = 0;
   bool ok = true;
   for (;;) {
     uint32_t t = 0;
@@ -473,115 +626,34 @@ spec_kernel(WGeom g, DevParams p, WPtrs w) {
         break;
       }
     } while (c < pe);
-    if (lane == 0) w.spec_n[k] = n;
-    ++pieces;
-    chunks += n;
-  }
-  if (lane == 0) {
-    atomicAdd(&w.hdr->stats[WS_PIECES], pieces);
-    atomicAdd(&w.hdr->stats[WS_SPEC_CHUNKS], chunks);
-    atomicAdd(&w.hdr->stats[WS_WINDOWS], wins);
-    if (!ok) set_status(w.hdr, SEQCDC_ECAPACITY);
-  }
-}
-
-// ---------------------------------------------------------------------------
-// Junction walks.
-// ---------------------------------------------------------------------------
-// Exit of piece k as its current results give it: the last cut of its spec
-// walk if its junction met that walk, else the junction walk's exit.
-__device__ __forceinline__ uint32_t exit_of(const WPtrs &w, uint32_t k, uint64_t lb) {
-  return w.jm[k] != kUnmerged ? w.spec[lb + w.spec_n[k] - 1u] : w.jexit[k];
-}
-
-// Walk piece k's chain from x (relative to the piece start) until it reaches
-// a cut of the piece's spec walk or leaves the piece; record where it
-// started, the cuts before the meeting cut, the meeting index or the exit.
-// Returns whether the walk met the spec walk.
-__device__ bool junction_walk(const WGeom &g, const DevParams &p, const WPtrs &w,
-                              uint32_t k, const Piece &pc, uint32_t x, uint32_t &chunks,
-                              uint32_t &wins, bool &ok) {
-  const int lane = threadIdx.x & 31;
-  const uint32_t ns = w.spec_n[k];
-  const uint32_t *sp = w.spec + pc.lb;
-  uint32_t *jc = w.jcut + pc.lb;
-  uint32_t q = 0, n = 0, jm = kUnmerged, jexit = 0;
-  uint32_t rel = x;
-  if (x == 0) {
-    jm = 0;  // the spec walk starts at the input itself
-  } else {
-    bool done = false;
-    for (uint32_t it = 0; it <= pc.cap && !done; ++it) {
-      // First spec cut >= rel: both lists increase, so q only moves on.
-      for (uint32_t s = 0; s <= ns / 32u + 1u; ++s) {
-        const uint32_t v = q + lane < ns ? sp[q + lane] : kFull;
-        const uint32_t below = __ballot_sync(kFull, v < rel);
-        q += __popc(below);
-        if (below != kFull) break;
-      }
-      const uint32_t at = q < ns ? sp[q] : kFull;
-      if (at == rel) {
-        jm = q;
-        done = true;
-      } else if (rel >= pc.len) {
-        jexit = rel;
-        if (rel == pc.len) {  // a cut exactly at the piece end belongs to it
-          if (n < pc.cap) { if (lane == 0) jc[n] = rel; ++n; } else ok = false;
-        }
-        done = true;
-      } else {
-        if (n < pc.cap) { if (lane == 0) jc[n] = rel; ++n; } else { ok = false; done = true; }
-        if (!done) {
-          rel = (uint32_t)(chunk_end_warp(g, p, pc.ps + rel, pc.fend, wins, ok) - pc.ps);
-          ++chunks;
-        }
-      }
-    }
-    if (!done) ok = false;
-  }
-  if (lane == 0) {
-    w.jin[k] = x;
-    w.jn[k] = n;
-    w.jm[k] = jm;
-    w.jexit[k] = jexit;
-  }
-  __syncwarp();
-  return jm != kUnmerged;
-}
-
-__global__ void __launch_bounds__(kWalkThreads, kWalkMinBlocks)
-junction_kernel(WGeom g, DevParams p, WPtrs w) {
-  const int lane = threadIdx.x & 31;
-  const uint32_t np = w.hdr->npieces;
-  uint32_t walks = 0, chunks = 0, unmerged = 0, wins = 0;
-  bool ok = true;
-  for (;;) {
-    uint32_t t = 0;
-    if (lane == 0) t = atomicAdd(&w.hdr->jticket, 1u);
-    t = __shfl_sync(kFull, t, 0);
-    if (t >= np) break;
-    const uint32_t k = w.order[t];
-    const Piece pc = piece_of(g, w, p, k);
-    if (pc.kl == 0) {  // a file's first piece: its spec walk is its chain
-      if (lane == 0) {
+    if (lane == 0) {
+      w.spec_n[k] = n;
+      if (pc.kl == 0) {  // a file's first piece: its spec walk is its chain
         w.jin[k] = 0;
         w.jn[k] = 0;
         w.jm[k] = 0;
         w.jexit[k] = 0;
       }
-      continue;
+      __threadfence();
+      asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(w.sdone + k), "r"(1u) : "memory");
     }
-    // The previous piece is a full piece of the same file; its exit is at
-    // or after this piece's start.
-    const uint64_t lb_prev = pc.lb - g.fullcap;
-    const uint32_t x = w.spec[lb_prev + w.spec_n[k - 1] - 1u] - g.P;
-    const bool met = junction_walk(g, p, w, k, pc, x, chunks, wins, ok);
-    ++walks;
-    unmerged += met ? 0u : 1u;
+    __syncwarp();
+    ++pieces;
+    chunks += n;
+    if (k + 1 < w.piece_base[pc.file + 1]) {
+      const Piece pn = piece_of(g, w, p, k + 1);
+      const bool met = junction_walk(g, p, w, k + 1, pn, (uint32_t)(c - pn.ps), w.sdone,
+                                     jchunks, wins, ok);
+      ++walks;
+      unmerged += met ? 0u : 1u;
+    }
   }
   if (lane == 0) {
+    atomicAdd(&w.hdr->stats[WS_PIECES], pieces);
+    atomicAdd(&w.hdr->stats[WS_SPEC_CHUNKS], chunks);
+    atomicAdd(&w.hdr->stats[WS_WINDOWS], wins);
     atomicAdd(&w.hdr->stats[WS_JUNCTIONS], walks);
-    atomicAdd(&w.hdr->stats[WS_JCHUNKS], chunks);
+    atomicAdd(&w.hdr->stats[WS_JCHUNKS], jchunks);
     atomicAdd(&w.hdr->stats[WS_UNMERGED], unmerged);
     if (!ok) set_status(w.hdr, SEQCDC_ECAPACITY);
   }
@@ -628,7 +700,7 @@ wrepair_kernel(WGeom g, DevParams p, WPtrs w) {
       const Piece pc = piece_of(g, w, p, k);
       const uint32_t x = exit_of(w, k - 1u, pc.lb - g.fullcap) - g.P;
       if (x == w.jin[k]) continue;
-      junction_walk(g, p, w, k, pc, x, chunks, wins, ok);
+      junction_walk(g, p, w, k, pc, x, nullptr, chunks, wins, ok);
       ++redone;
     }
   }
@@ -742,7 +814,7 @@ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 struct WLayout {
   size_t hdr, piece_base, list_base, ftile, ftile_l, piece_file, order, spec_n, spec, jin,
-      jn, jm, jexit, jcut, first_bad, count, ctile, total;
+      jn, jm, jexit, jcut, first_bad, count, ctile, sdone, total;
   uint64_t npmax, nlist, nftiles, nctiles;
   uint32_t P, fullcap;
 };
@@ -781,6 +853,7 @@ WLayout make_wlayout(const seqcdc_params_t *p, uint64_t total, uint64_t nfiles, 
   l.first_bad = take((nfiles + 1) * 4);
   l.count = take(l.npmax * 4);
   l.ctile = take(l.nctiles * 4);
+  l.sdone = take(l.npmax * 4);
   l.total = o;
   return l;
 }
@@ -805,6 +878,7 @@ WPtrs wptrs(void *d_ws, const WLayout &l) {
   w.first_bad = reinterpret_cast<uint32_t *>(b + l.first_bad);
   w.count = reinterpret_cast<uint32_t *>(b + l.count);
   w.ctile = reinterpret_cast<uint32_t *>(b + l.ctile);
+  w.sdone = reinterpret_cast<uint32_t *>(b + l.sdone);
   return w;
 }
 
@@ -847,9 +921,8 @@ int run(const seqcdc_params_t *p, const uint8_t *d_data, uint64_t total,
   const uint64_t most = 16u * (uint64_t)sms;
   const unsigned wgrid = (unsigned)(want < most ? want : most);
   if (prof_begin) cudaEventRecord(static_cast<cudaEvent_t>(prof_begin), st);
-  spec_kernel<<<wgrid, kWalkThreads, 0, st>>>(g, dp, w);
+  walk_kernel<<<wgrid, kWalkThreads, 0, st>>>(g, dp, w);
   if (prof_end) cudaEventRecord(static_cast<cudaEvent_t>(prof_end), st);
-  junction_kernel<<<wgrid, kWalkThreads, 0, st>>>(g, dp, w);
   const uint64_t vb = (l.npmax + 255) / 256;
   wverify_kernel<<<(unsigned)(vb < 4096 ? vb : 4096), 256, 0, st>>>(g, dp, w);
   const uint64_t rb = (nfiles + 3) / 4;

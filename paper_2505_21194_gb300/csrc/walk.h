@@ -19,7 +19,7 @@ size_t workspace_bytes(const seqcdc_params_t *p, uint64_t total, uint64_t nfiles
 
 // One chunking call (arguments as seqcdc_chunk / seqcdc_chunk_batch; the
 // parameters are already validated).  `prof_begin` / `prof_end` (may be null)
-// are recorded around the spec-walk kernel.
+// are recorded around the piece-walk kernel.
 int run(const seqcdc_params_t *p, const uint8_t *d_data, uint64_t total,
         const uint64_t *d_offsets, uint64_t nfiles, uint64_t *d_cuts, uint64_t cap,
         uint64_t *d_cut_offsets, uint64_t *d_count, void *d_ws, size_t ws_bytes,
