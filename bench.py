@@ -359,11 +359,25 @@ def run_gpu(args):
     h_offs = torch.from_numpy(offs_np.astype(np.int64)).pin_memory()
     h_co = torch.empty(nfiles + 1, dtype=torch.int64).pin_memory()
     h_cuts = torch.empty(cap, dtype=torch.int64).pin_memory()
-    e2e_steps = max(1, min(args.steps, 5))
-    torch.cuda.synchronize(dev)
-    t0 = time.perf_counter()
+    e2e_steps = max(3, min(args.steps, 7))
+
+    def h2d_copy_gbs():
+        """The bare host-to-device copy of the batch (pinned), for reference."""
+        torch.cuda.synchronize(dev)
+        ca, cb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ca.record()
+        d_data.copy_(h_data, non_blocking=True)
+        cb.record()
+        torch.cuda.synchronize(dev)
+        return total / (ca.elapsed_time(cb) * 1e-3) / 1e9
+
+    h2d_copy_gbs()
+    h2d_before = h2d_copy_gbs()
     d2h = 0
+    serial_s = []
     for _ in range(e2e_steps):
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
         d_data.copy_(h_data, non_blocking=True)
         d_offs.copy_(h_offs, non_blocking=True)
         step()
@@ -372,8 +386,9 @@ def run_gpu(args):
         k = int(h_co[-1])
         h_cuts[:k].copy_(d_cuts[:k], non_blocking=True)
         torch.cuda.synchronize(dev)
+        serial_s.append(time.perf_counter() - t0)
         d2h = (nfiles + 1) * 8 + k * 8
-    e2e_serial_s = (time.perf_counter() - t0) / e2e_steps
+    e2e_serial_s = statistics.median(serial_s)
     # host check of the last result: CSR is consistent
     assert int(h_co[-1]) == ncuts
     # The host-data entry point: file-aligned pieces with each piece's copy in
@@ -382,24 +397,20 @@ def run_gpu(args):
     pieces = 16
     pipe = HostBatchPipeline(p, tuning, str(dev))
     pipe.run(h_data, offs_np, pieces)
-    torch.cuda.synchronize(dev)
-    t0 = time.perf_counter()
+    pipe_s = []
     for _ in range(e2e_steps):
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
         hc, hco = pipe.run(h_data, offs_np, pieces)
-    e2e_s = (time.perf_counter() - t0) / e2e_steps
+        pipe_s.append(time.perf_counter() - t0)
+    e2e_s = statistics.median(pipe_s)
     e2e_gbs = total * world / e2e_s / 1e9
     assert int(hco[-1]) == ncuts and hc.size == ncuts
     pr = split_files(offs_np.astype(np.int64), pieces)
     d2h_pipe = sum((b - a + 1) * 8 + (int(offs_np[b] - offs_np[a]) // p.min_size + (b - a)) * 8 + 4
                    for a, b in pr)
-    # the bare host-to-device copy of the batch, for reference
-    torch.cuda.synchronize(dev)
-    ca, cb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ca.record()
-    d_data.copy_(h_data, non_blocking=True)
-    cb.record()
-    torch.cuda.synchronize(dev)
-    h2d_gbs = total / (ca.elapsed_time(cb) * 1e-3) / 1e9
+    h2d_gbs = h2d_copy_gbs()
+    # d_data now holds the batch again (the copies above wrote the same bytes)
 
     # CUDA-graph-captured step (same work, one graph launch per step).
     graph_ms = None
@@ -589,7 +600,8 @@ def run_gpu(args):
                 "serial": {"value": round(total * world / e2e_serial_s / 1e9, 2),
                            "d2h_bytes_per_step": int(d2h),
                            "api": "one host-to-device copy, seqcdc_chunk_batch, copies back"},
-                "h2d_copy_GBs": round(h2d_gbs, 1),
+                "h2d_copy_GBs": {"before": round(h2d_before, 1), "after": round(h2d_gbs, 1)},
+                "runs": "median of %d" % e2e_steps,
                 "host_cpus": ("%d CPUs local to the GPU" % len(numa_cpus)) if numa_cpus
                              else "not bound"},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,

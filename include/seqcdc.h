@@ -89,7 +89,11 @@ typedef struct {
  *                  (128, 256, 512; any other value means the default).
  *   algorithm      SEQCDC_ALGO_AUTO (0), SEQCDC_ALGO_MAP or SEQCDC_ALGO_WALK.
  *                  AUTO takes the chain walk for batches of at least
- *                  SEQCDC_WALK_MIN_FILES files and the segment map otherwise.
+ *                  SEQCDC_WALK_MIN_FILES files and the segment map otherwise,
+ *                  except that a call whose workspace is too small for the
+ *                  segment map but large enough for the chain walk takes the
+ *                  chain walk (so a workspace sized for a larger call serves
+ *                  every smaller one).
  *                  The chain walk needs many chains (pieces) at once to be
  *                  fast, and walks stretches without run ends (long runs of
  *                  equal bytes, where every cut is forced at max_size) one

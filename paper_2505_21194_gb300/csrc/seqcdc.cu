@@ -1549,8 +1549,21 @@ int run(const seqcdc_params_t *p, const uint8_t *d_data, uint64_t total,
   if (!d_ws || ((uintptr_t)d_ws & 255u)) return SEQCDC_EINVAL;
   if (total > 0 && (!d_data || ((uintptr_t)d_data & 15u))) return SEQCDC_EINVAL;
   if (total > 0 && !d_cuts) return SEQCDC_EINVAL;
-  if (use_walk(tuning, nfiles, d_offsets != nullptr)) {
+  bool walk = use_walk(tuning, nfiles, d_offsets != nullptr);
+  // AUTO with a workspace too small for the segment map but large enough for
+  // the chain walk takes the walk (same output): a workspace sized for a
+  // larger batch then serves every smaller call, as the walk's workspace
+  // grows with the bytes and the files while the map's is larger.
+  if (!walk && (!tuning || tuning->algorithm == SEQCDC_ALGO_AUTO) &&
+      ws_bytes < make_layout(p, total, nfiles, pick_segment(p, tuning)).total &&
+      ws_bytes >= seqcdc_walk::workspace_bytes(p, total, nfiles,
+                                               seqcdc_walk::pick_piece(p, tuning)))
+    walk = true;
+  if (walk) {
     if (cap < total / p->min_size + nfiles) return SEQCDC_ECAPACITY;
+    if (ws_bytes < seqcdc_walk::workspace_bytes(p, total, nfiles,
+                                                seqcdc_walk::pick_piece(p, tuning)))
+      return SEQCDC_ECAPACITY;
     const int sms_w = sm_count();
     if (sms_w <= 0) return SEQCDC_ECUDA;
     return seqcdc_walk::run(p, d_data, total, d_offsets, nfiles, d_cuts, cap,

@@ -86,8 +86,14 @@ def test_host_side_errors_before_launch(seqcdc_lib):
     assert lib.seqcdc_chunk(P, fake, n, fake, n, fake, fake + 8, ws, None, None) == E.SEQCDC_EINVAL
     # misaligned input
     assert lib.seqcdc_chunk(P, fake + 3, n, fake, n, fake, fake, ws, None, None) == E.SEQCDC_EINVAL
-    # workspace too small, capacity too small
-    assert lib.seqcdc_chunk(P, fake, n, fake, n, fake, fake, ws - 1, None, None) == E.SEQCDC_ECAPACITY
+    # workspace too small (for either path), capacity too small
+    ws_walk = seqcdc_lib.seqcdc_workspace_size(p, n, 1, (0, 0, E.ALGO_WALK, 0))
+    assert ws_walk < ws
+    assert lib.seqcdc_chunk(P, fake, n, fake, n, fake, fake, ws_walk - 1, None,
+                            None) == E.SEQCDC_ECAPACITY
+    t_map = ctypes.byref(E.Tuning(0, 0, E.ALGO_MAP, 0))
+    assert lib.seqcdc_chunk(P, fake, n, fake, n, fake, fake, ws - 1, t_map,
+                            None) == E.SEQCDC_ECAPACITY
     assert lib.seqcdc_chunk(P, fake, n, fake, n // 4096, fake, fake, ws, None, None) == E.SEQCDC_ECAPACITY
     # NULL count / offsets
     assert lib.seqcdc_chunk(P, fake, n, fake, n, None, fake, ws, None, None) == E.SEQCDC_EINVAL

@@ -224,3 +224,33 @@ def test_walk_offsets_beyond_4gib(gpu):
     window = np.concatenate([np.zeros(zeros - start, np.uint8), tail])
     exp = oracle.chunk(window, p).astype(np.int64) + start
     assert np.array_equal(got[head.size:], exp)
+
+
+def test_auto_workspace_sized_for_a_larger_batch(gpu):
+    """A workspace sized for 300 files (the chain walk under AUTO) serves a
+    call with 200 of them, which AUTO alone would give the segment map with
+    its larger workspace: the call takes the chain walk and is exact."""
+    import torch
+    s = gpu
+    p = oracle.presets(8)
+    pp = _p(s, p)
+    rng = np.random.default_rng(12)
+    sizes = rng.integers(1000, 200000, 300)
+    offs = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    data = W.mixed_base(int(offs[-1]), 6, block=4096)
+    ws_bytes = s.seqcdc_workspace_size(pp, int(offs[-1]), 300)
+    assert ws_bytes < s.seqcdc_workspace_size(pp, int(offs[200]), 200)
+    ws = torch.empty(ws_bytes, dtype=torch.uint8, device="cuda")
+    sub = offs[:201]
+    total = int(sub[-1])
+    d = torch.from_numpy(data[:total]).cuda()
+    o = torch.from_numpy(sub).cuda()
+    cap = total // pp.min_size + 200
+    cuts = torch.empty(cap, dtype=torch.int64, device="cuda")
+    co = torch.empty(201, dtype=torch.int64, device="cuda")
+    s.seqcdc_chunk_batch(pp, d, total, o, 200, cuts, cap, co, ws, ws_bytes)
+    assert s.seqcdc_status(ws) == 0
+    n = int(co[-1].item())
+    ecuts, eco = oracle.chunk_batch(data[:total], sub.astype(np.uint64), p)
+    same(co.cpu().numpy(), eco)
+    same(cuts[:n].cpu().numpy(), ecuts)
