@@ -31,7 +31,7 @@ from . import seqcdc
 
 SEGMENTS = (32768, 49152, 65536, 98304, 131072, 196608, 262144)
 THREADS = (128, 256, 512)
-PIECES = (262144, 524288, 1048576, 2097152, 4194304)
+PIECES = (262144, 524288, 786432, 1048576, 1572864, 2097152, 4194304)
 CACHE_VERSION = "v2"
 _lock = threading.Lock()
 

@@ -55,7 +55,8 @@ constexpr int kWalkThreads = 128;      // walk kernels: four warps per block
 #endif
 constexpr int kWalkMinBlocks = SEQCDC_WALK_MIN_BLOCKS;
 constexpr int kFileTile = 1024;        // files per plan block
-constexpr int kPieceTile = 256;        // pieces per compaction block
+constexpr int kPieceTile = 32;         // pieces per compaction tile (8 warps copy 4 each)
+constexpr int kEmitThreads = 256;
 constexpr uint32_t kUnmerged = 0xFFFFFFFFu;
 constexpr uint32_t kNoBad = 0xFFFFFFFFu;
 constexpr uint32_t kFull = 0xFFFFFFFFu;
@@ -763,10 +764,10 @@ __global__ void wemit_kernel(WGeom g, DevParams p, WPtrs w, uint64_t *d_cuts, ui
   }
   __syncthreads();
   const uint64_t i = lo + threadIdx.x;
-  const uint32_t c = i < np ? w.count[i] : 0u;
+  const uint32_t c = (threadIdx.x < kPieceTile && i < np) ? w.count[i] : 0u;
   uint32_t tot;
   const uint32_t ex = block_excl_scan(c, scratch, &tot);
-  offs[threadIdx.x] = ex;
+  if (threadIdx.x < kPieceTile) offs[threadIdx.x] = ex;
   if (threadIdx.x == 0) offs[kPieceTile] = tot;
   __syncthreads();
   const uint64_t prefix = s_prefix;
@@ -929,8 +930,8 @@ int run(const seqcdc_params_t *p, const uint8_t *d_data, uint64_t total,
   const uint64_t rcap = 4u * (uint64_t)sms;
   wrepair_kernel<<<(unsigned)(rb < rcap ? (rb ? rb : 1) : rcap), kWalkThreads, 0, st>>>(g, dp, w);
   wcount_kernel<<<(unsigned)l.nctiles, kPieceTile, 0, st>>>(g, dp, w);
-  wemit_kernel<<<(unsigned)l.nctiles, kPieceTile, 0, st>>>(g, dp, w, d_cuts, cap,
-                                                           d_cut_offsets, d_count);
+  wemit_kernel<<<(unsigned)l.nctiles, kEmitThreads, 0, st>>>(g, dp, w, d_cuts, cap,
+                                                             d_cut_offsets, d_count);
   return cudaGetLastError() == cudaSuccess ? SEQCDC_OK : SEQCDC_ECUDA;
 }
 
