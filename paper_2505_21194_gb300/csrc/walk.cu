@@ -393,6 +393,9 @@ __device__ uint64_t chunk_end_warp(const WGeom &g, const DevParams &p, uint64_t 
   ++wins;
   const uint32_t lim = (uint32_t)(lim_abs - cb);
   uint32_t r = (uint32_t)(r_abs - cb);
+  // A skip past the limit ends the chunk at the limit, so SkipSize can be
+  // clamped to it and every position stays below 2^32.
+  const uint32_t skip = p.S < lim ? p.S : lim;
   const int32_t lb = 16 * lane;     // the lane's first position in a half
   uint32_t opp = 0;                 // opposing pairs counted in the current region
   uint32_t w0 = 0;                  // window start
@@ -457,13 +460,15 @@ __device__ uint64_t chunk_end_warp(const WGeom &g, const DevParams &p, uint64_t 
           if (lane >= d) sc += y;
         }
         const int ol = __ffs(__ballot_sync(kFull, sc >= need)) - 1;
-        uint32_t bp = 0;
-        if (lane == ol) bp = nth_set_bit(om, need - (sc - cnt));
-        bp = __shfl_sync(kFull, bp, ol);
-        const uint64_t rn = (uint64_t)hb + 16u * ol + bp + 1u + p.S;
+        // The k-th set bit of lane ol's word: lane t checks bit t.
+        const uint32_t word = __shfl_sync(kFull, om, ol);
+        const uint32_t kth = __shfl_sync(kFull, need - (sc - cnt), ol);
+        const bool hit = ((word >> lane) & 1u) &&
+                         (uint32_t)__popc(word & (0xffffffffu >> (31 - lane))) == kth;
+        const uint32_t bp = __ffs(__ballot_sync(kFull, hit)) - 1;
+        r = hb + 16u * ol + bp + 1u + skip;
         opp = 0;
-        if (rn + 1 >= lim) return cb + lim;
-        r = (uint32_t)rn;
+        if (r + 1 >= lim) return cb + lim;
         if (r + 1 < hb + 512u) continue;  // the next region starts in this half
         moved = true;
         break;
