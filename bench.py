@@ -316,7 +316,7 @@ def run_gpu(args):
     if st != 0:
         raise RuntimeError("device status %d during warm-up" % st)
     ncuts = int(d_co[-1].item())
-    path_stats = seqcdc.seqcdc_stats(d_ws, stream)
+    path_stats = seqcdc.seqcdc_stats(d_ws, stream, walk=walk)
 
     sampler = ClockSampler(dev.index if dev.index is not None else 0)
     sampler.start()

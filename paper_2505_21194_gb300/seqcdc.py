@@ -230,14 +230,17 @@ def seqcdc_status(d_ws, stream=None) -> int:
 
 STAT_NAMES = ("segments", "abnormal", "no_image", "lookback_waits", "inconsistent",
               "recomputed", "replayed", "lookback_steps")
+WALK_STAT_NAMES = ("pieces", "piece_walk_chunks", "junction_walks", "junction_chunks",
+                   "junctions_not_met", "inconsistent", "repaired", "windows")
 
 
-def seqcdc_stats(d_ws, stream=None) -> dict:
-    """Path counters of the last call that used workspace ``d_ws``."""
+def seqcdc_stats(d_ws, stream=None, walk: bool = False) -> dict:
+    """Path counters of the last call that used workspace ``d_ws`` (named for
+    the chain walk with ``walk=True``, else for the segment map)."""
     out = (ctypes.c_uint32 * 8)()
     _check(load_library().seqcdc_stats(_ptr(d_ws), _stream_handle(stream), out, 8),
            "seqcdc_stats")
-    return dict(zip(STAT_NAMES, list(out)))
+    return dict(zip(WALK_STAT_NAMES if walk else STAT_NAMES, list(out)))
 
 
 def seqcdc_profile_events(ev_begin=None, ev_end=None) -> None:
