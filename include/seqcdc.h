@@ -100,7 +100,7 @@ typedef struct {
  *                  file at a time; the segment map has neither limit.
  *   piece_bytes    chain walk: bytes of a piece, the unit one warp walks
  *                  (rounded up to a multiple of 64 KiB; at least
- *                  4 x max_size, at most 64 MiB; default 1 MiB).
+ *                  4 x max_size, at most 64 MiB; default 768 KiB).
  */
 #define SEQCDC_ALGO_AUTO 0u
 #define SEQCDC_ALGO_MAP  1u
@@ -118,7 +118,7 @@ typedef struct {
  * call with these parameters and this tuning (NULL or zero fields: library
  * defaults) runs with; out->algorithm is copied from the tuning (AUTO is
  * decided per call, from the number of files).  The defaults are 256 threads,
- * 64 KiB segments (max_size if larger) and 1 MiB pieces.  Returns
+ * 64 KiB segments (max_size if larger) and 768 KiB pieces.  Returns
  * SEQCDC_EINVAL for an invalid parameter set or a NULL out.
  */
 int seqcdc_resolve_tuning(const seqcdc_params_t *p, const seqcdc_tuning_t *tuning,

@@ -48,10 +48,10 @@ namespace {
 constexpr uint32_t kWin = 1024;        // bytes per warp window (32 per lane)
 constexpr int kWalkThreads = 128;      // walk kernels: four warps per block
 // Blocks of the walk kernels resident per SM that the register budget is
-// sized for: 8 blocks of 4 warps (the walks are bound by latency and issue;
-// this keeps 32 chains in flight per SM without spilling).
+// sized for: 16 blocks of 4 warps, 32 registers per thread without spills
+// (the walks are bound by latency and issue; 64 chains in flight per SM).
 #ifndef SEQCDC_WALK_MIN_BLOCKS
-#define SEQCDC_WALK_MIN_BLOCKS 8
+#define SEQCDC_WALK_MIN_BLOCKS 16
 #endif
 constexpr int kWalkMinBlocks = SEQCDC_WALK_MIN_BLOCKS;
 constexpr int kFileTile = 1024;        // files per plan block
@@ -60,7 +60,7 @@ constexpr int kEmitThreads = 256;
 constexpr uint32_t kUnmerged = 0xFFFFFFFFu;
 constexpr uint32_t kNoBad = 0xFFFFFFFFu;
 constexpr uint32_t kFull = 0xFFFFFFFFu;
-constexpr uint32_t kDefaultPiece = 1u << 20;
+constexpr uint32_t kDefaultPiece = 768u << 10;
 constexpr uint32_t kPrefetch = 2048;   // bytes asked of L2 for the next chunk's scan
 
 // Workspace header: status and statistics at the offsets seqcdc_status and

@@ -10,7 +10,7 @@
 namespace seqcdc_walk {
 
 // Piece size a call runs with: `piece_bytes` from the tuning (0 = default
-// 1 MiB), rounded up to 64 KiB, at least 4 x max_size, at most 64 MiB.
+// 768 KiB), rounded up to 64 KiB, at least 4 x max_size, at most 64 MiB.
 uint32_t pick_piece(const seqcdc_params_t *p, const seqcdc_tuning_t *t);
 
 // Workspace bytes of one call over `total` bytes in `nfiles` files.

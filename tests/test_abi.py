@@ -125,12 +125,12 @@ def test_resolve_tuning_defaults_and_rules(seqcdc_lib):
 
 
 def test_resolve_tuning_piece_rules(seqcdc_lib):
-    """Chain-walk piece size: default 1 MiB; rounded up to 64 KiB; at least
+    """Chain-walk piece size: default 768 KiB; rounded up to 64 KiB; at least
     4 x max_size; at most 64 MiB.  The algorithm field is passed through."""
     s = seqcdc_lib
     p8, p16 = s.seqcdc_params(8, 0), s.seqcdc_params(16, 0)
     t = s.seqcdc_resolve_tuning(p8)
-    assert t.piece_bytes == 1 << 20 and t.algorithm == s.ALGO_AUTO
+    assert t.piece_bytes == 768 << 10 and t.algorithm == s.ALGO_AUTO
     t = s.seqcdc_resolve_tuning(p8, (0, 0, s.ALGO_WALK, 100000))
     assert t.piece_bytes == 131072 and t.algorithm == s.ALGO_WALK
     assert s.seqcdc_resolve_tuning(p8, (0, 0, 2, 65536)).piece_bytes == 65536
@@ -152,5 +152,5 @@ def test_workspace_follows_the_path(seqcdc_lib):
     assert s.seqcdc_workspace_size(p, total, many) == walk
     assert s.seqcdc_workspace_size(p, total, few) == \
         s.seqcdc_workspace_size(p, total, few, (0, 0, s.ALGO_MAP, 0))
-    # 8 GiB in 1 MiB pieces: the walk's lists take a few bytes per input KiB
+    # 8 GiB in 768 KiB pieces: the walk's lists take a few bytes per input KiB
     assert walk < total // 64

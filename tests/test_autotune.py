@@ -32,7 +32,7 @@ def test_candidates_respect_max_size_and_library_rules(seqcdc_lib):
 def test_default_candidate_follows_auto_rule(seqcdc_lib):
     s = seqcdc_lib
     p = s.seqcdc_params(8, 0)
-    assert A.default_candidate(p, s.WALK_MIN_FILES) == (0, 0, s.ALGO_WALK, 1 << 20)
+    assert A.default_candidate(p, s.WALK_MIN_FILES) == (0, 0, s.ALGO_WALK, 768 << 10)
     assert A.default_candidate(p, s.WALK_MIN_FILES - 1) == (65536, 256, s.ALGO_MAP, 0)
     assert A.default_candidate(p, 1000, batch=False)[2] == s.ALGO_MAP
 
