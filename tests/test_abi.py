@@ -154,3 +154,20 @@ def test_workspace_follows_the_path(seqcdc_lib):
         s.seqcdc_workspace_size(p, total, few, (0, 0, s.ALGO_MAP, 0))
     # 8 GiB in 768 KiB pieces: the walk's lists take a few bytes per input KiB
     assert walk < total // 64
+
+
+def test_walk_workspace_is_monotone(seqcdc_lib):
+    """The chain walk's workspace grows with the bytes and the files, so a
+    workspace sized for a batch serves every smaller one (what AUTO's
+    fallback to the walk relies on)."""
+    s = seqcdc_lib
+    rng = np.random.default_rng(0)
+    for kib in (4, 8, 16):
+        p = s.seqcdc_params(kib, 0)
+        t = (0, 0, s.ALGO_WALK, 0)
+        for _ in range(200):
+            t1 = int(rng.integers(0, 1 << 34))
+            f1 = int(rng.integers(1, 20000))
+            t2 = t1 + int(rng.integers(0, 1 << 30))
+            f2 = f1 + int(rng.integers(0, 5000))
+            assert s.seqcdc_workspace_size(p, t1, f1, t) <= s.seqcdc_workspace_size(p, t2, f2, t)
