@@ -8,13 +8,15 @@ increasing mode.  Inputs are generated on the host from a fixed seed, copied
 to HBM once, and are far larger than L2 (no flush needed between steps).
 
 Printed: one JSON line with the metric, the device-resident throughput
-(`value`), the end-to-end throughput through host buffers (`e2e`), the
-roofline of the dominant kernel, the plain one-launch-per-file loop for
-comparison, clocks, the CPU oracle as a reported baseline (all host cores and
-one thread), `serve`: p50/p99 latency and sustained GB/s of the
-continuous-batching server under open-loop Poisson arrivals at 25, 50, 100
-and 200 GB/s offered load, and `dedup`: the deduplication savings of the
-backup-like stream at the three settings in both modes.
+(`value`, the path the autotuner picks: the chain walk for this batch), the
+end-to-end throughput through host buffers (`e2e`), the roofline of the
+dominant kernel, the other path (segment map) on the same batch, the plain
+one-launch-per-file loop for comparison, clocks, the CPU oracle as a reported
+baseline (all host cores and one thread), `serve`: p50/p99 latency and
+sustained GB/s of the continuous-batching server under open-loop Poisson
+arrivals at 25, 50, 100 and 200 GB/s offered load, and `dedup`: the
+deduplication savings of the backup-like stream at the three settings in both
+modes.
 
 `--impl reference` times the CPU oracle (the plain single-threaded chunker,
 files spread over the host cores) on the same workload instead.
