@@ -100,7 +100,8 @@ typedef struct {
  *                  file at a time; the segment map has neither limit.
  *   piece_bytes    chain walk: bytes of a piece, the unit one warp walks
  *                  (rounded up to a multiple of 64 KiB; at least
- *                  4 x max_size, at most 64 MiB; default 768 KiB).
+ *                  4 x max_size, at most 64 MiB; default 768 KiB, or
+ *                  384 x min_size when min_size exceeds 4 KiB).
  */
 #define SEQCDC_ALGO_AUTO 0u
 #define SEQCDC_ALGO_MAP  1u
@@ -118,7 +119,8 @@ typedef struct {
  * call with these parameters and this tuning (NULL or zero fields: library
  * defaults) runs with; out->algorithm is copied from the tuning (AUTO is
  * decided per call, from the number of files).  The defaults are 256 threads,
- * 64 KiB segments (max_size if larger) and 768 KiB pieces.  Returns
+ * 64 KiB segments (max_size if larger) and 768 KiB pieces (384 x min_size
+ * above a 4 KiB min_size).  Returns
  * SEQCDC_EINVAL for an invalid parameter set or a NULL out.
  */
 int seqcdc_resolve_tuning(const seqcdc_params_t *p, const seqcdc_tuning_t *tuning,

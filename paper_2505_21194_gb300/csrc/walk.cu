@@ -893,7 +893,13 @@ WPtrs wptrs(void *d_ws, const WLayout &l) {
 namespace seqcdc_walk {
 
 uint32_t pick_piece(const seqcdc_params_t *p, const seqcdc_tuning_t *t) {
-  uint64_t P = (t && t->piece_bytes) ? t->piece_bytes : kDefaultPiece;
+  // Default: chains started at a piece start need about 25 chunks on
+  // average, and up to ~120, to meet the true chain; chunks (and skips) grow
+  // with min_size, so pieces do too.  Measured on a 10,000-file batch:
+  // 768 KiB is best at min 1 KiB and 4 KiB, 3 MiB (384 x min) at min 8 KiB.
+  uint64_t P = kDefaultPiece;
+  if (p && p->min_size > 4096u) P = 384u * p->min_size;
+  if (t && t->piece_bytes) P = t->piece_bytes;
   const uint64_t floor = p ? 4u * p->max_size : 0u;
   if (P < floor) P = floor;
   P = (P + 65535u) & ~(uint64_t)65535u;

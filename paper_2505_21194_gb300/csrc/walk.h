@@ -9,8 +9,9 @@
 
 namespace seqcdc_walk {
 
-// Piece size a call runs with: `piece_bytes` from the tuning (0 = default
-// 768 KiB), rounded up to 64 KiB, at least 4 x max_size, at most 64 MiB.
+// Piece size a call runs with: `piece_bytes` from the tuning (0 = default:
+// 768 KiB, or 384 x min_size when min_size exceeds 4 KiB), rounded up to
+// 64 KiB, at least 4 x max_size, at most 64 MiB.
 uint32_t pick_piece(const seqcdc_params_t *p, const seqcdc_tuning_t *t);
 
 // Workspace bytes of one call over `total` bytes in `nfiles` files.

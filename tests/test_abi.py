@@ -125,7 +125,8 @@ def test_resolve_tuning_defaults_and_rules(seqcdc_lib):
 
 
 def test_resolve_tuning_piece_rules(seqcdc_lib):
-    """Chain-walk piece size: default 768 KiB; rounded up to 64 KiB; at least
+    """Chain-walk piece size: default 768 KiB (384 x min_size above a 4 KiB
+    minimum); rounded up to 64 KiB; at least
     4 x max_size; at most 64 MiB.  The algorithm field is passed through."""
     s = seqcdc_lib
     p8, p16 = s.seqcdc_params(8, 0), s.seqcdc_params(16, 0)
@@ -137,6 +138,10 @@ def test_resolve_tuning_piece_rules(seqcdc_lib):
     assert s.seqcdc_resolve_tuning(p16, (0, 0, 2, 65536)).piece_bytes == 131072
     assert s.seqcdc_resolve_tuning(p8, (0, 0, 2, 1 << 30)).piece_bytes == 64 << 20
     assert s.seqcdc_resolve_tuning(p8, (0, 0, s.ALGO_MAP, 0)).algorithm == s.ALGO_MAP
+    # the default grows with min_size above 4 KiB (16 KB setting: min 8 KiB)
+    assert s.seqcdc_resolve_tuning(s.seqcdc_params(4, 0)).piece_bytes == 768 << 10
+    assert s.seqcdc_resolve_tuning(p16).piece_bytes == 384 * 8192
+    assert s.seqcdc_resolve_tuning(p16, (0, 0, 2, 1 << 20)).piece_bytes == 1 << 20
 
 
 def test_workspace_follows_the_path(seqcdc_lib):
