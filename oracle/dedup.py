@@ -5,8 +5,10 @@ The fingerprint of a chunk is its SHA-256 digest (the hash named for
 fingerprinting in Sec. II), computed with the Python standard library's
 hashlib; a chunk is stored once per distinct digest, and the savings are
 1 - (bytes of distinct chunks) / (all bytes) (Eq. 1).  Pinned in
-tests/test_fingerprint.py by the FIPS 180-4 example digests and by inputs
-whose savings are known by construction.
+tests/test_fingerprint.py by the published SHA-256 known answers (the worked
+examples of FIPS 180-2 Appendix B and the zero-length validation vector,
+stored in tests/golden/sha256_known_answers.json) and by inputs whose distinct
+chunks and savings are known by construction.
 """
 from __future__ import annotations
 

@@ -1,14 +1,18 @@
 """Fingerprints (SHA-256 of each chunk) and distinct-chunk counting.
 
-Reference: the standard library's SHA-256 (hashlib) and ``oracle/dedup.py``.
-The GPU kernel is checked on message lengths around the padding boundaries
-(55/56/63/64/119/120 bytes), on chunks at every byte alignment, on the chunk
-lists the chunker produces, and on inputs whose distinct-chunk count is known
-by construction.
+Reference: the standard library's SHA-256 (hashlib) and ``oracle/dedup.py``,
+pinned by the published known answers of the Secure Hash Standard
+(``tests/golden/sha256_known_answers.json``: FIPS 180-2 Appendix B and the
+zero-length SHAVS vector).  The GPU kernel is checked against the same known
+answers, on message lengths around the padding boundaries (55/56/63/64/119/120
+bytes), on chunks at every byte alignment, on the chunk lists the chunker
+produces, and on inputs whose distinct-chunk count is known by construction.
 """
 from __future__ import annotations
 
 import hashlib
+import json
+import os
 
 import numpy as np
 import pytest
@@ -16,6 +20,29 @@ import pytest
 import oracle
 from oracle import dedup as D
 from paper_2505_21194_gb300 import workloads as W
+
+
+_GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "sha256_known_answers.json")
+
+
+def _known_answers():
+    with open(_GOLDEN) as f:
+        vecs = json.load(f)["vectors"]
+    return [(v["name"], np.frombuffer((v["ascii"] * v["repeat"]).encode(), dtype=np.uint8),
+             bytes.fromhex(v["sha256"])) for v in vecs]
+
+
+def test_oracle_fingerprints_match_published_known_answers():
+    """FIPS 180-2 Appendix B and the zero-length vector, through the oracle's
+    fingerprint function (one chunk per message)."""
+    for name, msg, digest in _known_answers():
+        assert D.fingerprints(msg, [(0, msg.size)]) == [digest], name
+    # the same messages side by side in one buffer, as chunks of a stream
+    kas = _known_answers()
+    data = np.concatenate([m for _, m, _ in kas])
+    ends = np.cumsum([m.size for _, m, _ in kas])
+    ranges = list(zip([0] + ends[:-1].tolist(), ends.tolist()))
+    assert D.fingerprints(data, ranges) == [d for _, _, d in kas]
 
 
 def test_oracle_distinct_and_savings_known_by_construction():
@@ -122,3 +149,29 @@ def test_gpu_fingerprints_of_chunker_output_and_dedup(gpu):
     n2, b2 = s.dedup(dig[:1], sizes[:1])
     assert (n2, b2) == (1, int(sizes[0]))
     assert s.dedup(dig[:0], sizes[:0]) == (0, 0)
+
+
+@pytest.mark.gpu
+def test_gpu_sha256_published_known_answers(gpu):
+    """The GPU kernel on FIPS 180-2 Appendix B's three messages, each a chunk
+    of its own file and, shifted to every alignment, a chunk inside a file
+    (the zero-length message cannot be a chunk: chunks are never empty)."""
+    s = gpu
+    kas = [k for k in _known_answers() if k[1].size > 0]
+    files, cuts, co, expect = [], [], [0], []
+    for name, msg, digest in kas:
+        for shift in range(4):
+            pad = np.full(shift, 0x5A, dtype=np.uint8)
+            files.append(np.concatenate([pad, msg]))
+            if shift:
+                cuts += [shift, shift + msg.size]
+                expect += [None, (name, digest)]
+            else:
+                cuts += [msg.size]
+                expect += [(name, digest)]
+            co.append(len(cuts))
+    offs = np.concatenate([[0], np.cumsum([f.size for f in files])])
+    got, gsz, _ = _gpu_digests(s, np.concatenate(files), offs, cuts, co)
+    for i, e in enumerate(expect):
+        if e is not None:
+            assert got[i].tobytes() == e[1], (e[0], i)
