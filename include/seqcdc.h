@@ -243,6 +243,23 @@ int seqcdc_status(const void *d_ws, void *stream);
 int seqcdc_stats(const void *d_ws, void *stream, uint32_t *out, uint32_t n);
 
 /*
+ * Bound, in nanoseconds, on every device-side wait of the chunking calls made
+ * later from this host thread; returns the previous bound.  The default is
+ * SEQCDC_DEFAULT_WAIT_NS (2 s).  Only the segment map waits: its resolve pass
+ * finds each segment's true entry by decoupled look-back, which waits for a
+ * preceding segment to publish its exit (the chain of Sec. III is sequential,
+ * so a segment's first chunk depends on where the previous segment's last
+ * chunk ends).  A wait that outlasts the bound gives up: the kernel records
+ * SEQCDC_ETIMEOUT in the workspace status (read it with seqcdc_status) and
+ * finishes without that value, so the call ends and the CUDA context stays
+ * usable, but the outputs of that call are not valid.  A bound of 0 gives up
+ * at the first check that finds the value missing.  Calls on other host
+ * threads are not affected.  Allocates nothing; makes no CUDA call.
+ */
+#define SEQCDC_DEFAULT_WAIT_NS 2000000000ull
+uint64_t seqcdc_set_wait_limit_ns(uint64_t ns);
+
+/*
  * Measurement hook: record the CUDA events `ev_begin` / `ev_end` (cudaEvent_t
  * passed as void*) on the call's stream immediately before and after the
  * dominant kernel (the segment kernel of the segment map, the piece-walk

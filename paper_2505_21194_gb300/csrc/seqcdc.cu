@@ -63,7 +63,7 @@ constexpr int kFileTile = 1024;    // files per plan block
 constexpr int kItemTile = 256;     // items per compaction block
 constexpr uint32_t kMaxSeqLength = 16;
 constexpr uint64_t kMaxMaxSize = 131072;
-constexpr uint64_t kWaitNs = 2000000000ull;  // 2 s bound on any device wait
+constexpr uint64_t kWaitNs = SEQCDC_DEFAULT_WAIT_NS;  // default bound on a device wait
 
 // Item state bits (set once, in this order of availability).
 constexpr uint32_t F_IMG = 1u;     // image (distinct exits) published
@@ -121,6 +121,7 @@ struct Geom {
   uint64_t nfiles;
   uint32_t L;
   uint32_t cap;             // natural cuts tabulated per item (L / 64)
+  uint64_t wait_ns;         // bound on each device-side wait (ns)
 };
 
 // Natural cuts tabulated per item: one per 96 bytes.  Uniform random input
@@ -164,9 +165,10 @@ struct WsPtrs {
 // Small device helpers.
 // ---------------------------------------------------------------------------
 
-// Wait until (*flag & mask) != 0, at most kWaitNs.  Returns the flag value, or
-// 0 after recording SEQCDC_ETIMEOUT in the workspace status.
-__device__ uint32_t wait_any(const uint32_t *flag, uint32_t mask, WsHeader *hdr) {
+// Wait until (*flag & mask) != 0, at most limit_ns.  Returns the flag value,
+// or 0 after recording SEQCDC_ETIMEOUT in the workspace status.
+__device__ uint32_t wait_any(const uint32_t *flag, uint32_t mask, WsHeader *hdr,
+                             uint64_t limit_ns) {
   uint32_t v = ld_acquire(flag);
   if (v & mask) return v;
   const uint64_t t0 = global_ns();
@@ -176,7 +178,7 @@ __device__ uint32_t wait_any(const uint32_t *flag, uint32_t mask, WsHeader *hdr)
     if (backoff < 512) backoff <<= 1;
     v = ld_acquire(flag);
     if (v & mask) return v;
-    if (global_ns() - t0 > kWaitNs) break;
+    if (global_ns() - t0 > limit_ns) break;
   }
   atomicExch(&hdr->status, (uint32_t)SEQCDC_ETIMEOUT);
   return 0;
@@ -929,7 +931,7 @@ __device__ uint64_t exit_of(const WsPtrs &ws, const ResShared &r, const uint32_t
 // its true exit).  The composite is one value per lane: lane j holds the exit
 // of item-1 reached from value j of the current image.  A composite that is
 // the same for every value settles the entry at once.
-__device__ uint64_t lookback(const ResShared &r, const WsPtrs &ws) {
+__device__ uint64_t lookback(const ResShared &r, const WsPtrs &ws, uint64_t limit_ns) {
   const int lane = threadIdx.x & 31;
   const uint32_t item = r.item;
   uint32_t k = item - 1;
@@ -941,13 +943,13 @@ __device__ uint64_t lookback(const ResShared &r, const WsPtrs &ws) {
     // Lane 0 waits; every lane acquires for its own reads but all branch on
     // lane 0's snapshot (flags only gain bits).
     uint32_t st = 0;
-    if (lane == 0) st = wait_any(&ws.state[k], F_INCL | F_AGG | F_NOAGG, ws.hdr);
+    if (lane == 0) st = wait_any(&ws.state[k], F_INCL | F_AGG | F_NOAGG, ws.hdr, limit_ns);
     st = __shfl_sync(0xffffffffu, st, 0);
     if (st == 0) break;  // timed out; status is recorded
     (void)ld_acquire(&ws.state[k]);
     __syncwarp();
     if (!(st & F_INCL) && (st & F_NOAGG)) {
-      if (lane == 0) st = wait_any(&ws.state[k], F_INCL, ws.hdr);
+      if (lane == 0) st = wait_any(&ws.state[k], F_INCL, ws.hdr, limit_ns);
       st = __shfl_sync(0xffffffffu, st, 0);
       waited = true;
       if (st == 0) break;
@@ -962,7 +964,7 @@ __device__ uint64_t lookback(const ResShared &r, const WsPtrs &ws) {
       const uint32_t hit = __ballot_sync(0xffffffffu, lane < (int)n && v == e && have);
       if (hit) { x = __shfl_sync(0xffffffffu, comp, __ffs(hit) - 1); break; }
       // Outside the composite's domain: wait for item-1's own true exit.
-      if (lane == 0) st = wait_any(&ws.state[item - 1], F_INCL, ws.hdr);
+      if (lane == 0) st = wait_any(&ws.state[item - 1], F_INCL, ws.hdr, limit_ns);
       st = __shfl_sync(0xffffffffu, st, 0);
       waited = true;
       if (st) {
@@ -996,7 +998,7 @@ __device__ uint64_t lookback(const ResShared &r, const WsPtrs &ws) {
     ++steps;
     const uint32_t hv = __ballot_sync(0xffffffffu, have);
     if (hv == 0) {  // nothing composes any more: wait for item-1's true exit
-      if (lane == 0) st = wait_any(&ws.state[item - 1], F_INCL, ws.hdr);
+      if (lane == 0) st = wait_any(&ws.state[item - 1], F_INCL, ws.hdr, limit_ns);
       st = __shfl_sync(0xffffffffu, st, 0);
       waited = true;
       if (st) {
@@ -1078,7 +1080,7 @@ resolve_kernel(Geom g, WsPtrs ws) {
       __threadfence();
       atomicOr(&ws.state[item], ok ? F_AGG : F_NOAGG);
     }
-    x = lookback(r, ws);
+    x = lookback(r, ws, g.wait_ns);
   }
   // Emission from x along the candidate links (lane 0).  When x is not known
   // or is not one of the item's tabulated entries (a forced cut entered it),
@@ -1487,6 +1489,7 @@ size_t workspace_for(const seqcdc_params_t *p, uint64_t total, uint64_t nfiles,
 
 thread_local cudaEvent_t g_prof_begin = nullptr;
 thread_local cudaEvent_t g_prof_end = nullptr;
+thread_local uint64_t g_wait_ns = kWaitNs;
 
 constexpr int kMaxDevices = 64;
 
@@ -1579,7 +1582,7 @@ int run(const seqcdc_params_t *p, const uint8_t *d_data, uint64_t total,
   if (cap < total / p->min_size + nfiles) return SEQCDC_ECAPACITY;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const WsPtrs w = ws_ptrs(d_ws, l);
-  Geom g{d_data, total, d_offsets, nfiles, L, cand_cap(L)};
+  Geom g{d_data, total, d_offsets, nfiles, L, cand_cap(L), g_wait_ns};
   DevParams dp{p->mode, p->seq_length, p->skip_trigger, p->skip_size,
                (uint32_t)p->min_size, (uint32_t)p->max_size};
   const size_t smem = map_smem_bytes(max_words(L, p->max_size), L);
@@ -1757,6 +1760,12 @@ int seqcdc_stats(const void *d_ws, void *stream, uint32_t *out, uint32_t n) {
   if (cudaStreamSynchronize(st) != cudaSuccess) return SEQCDC_ECUDA;
   for (uint32_t k = 0; k < n && k < 8; ++k) out[k] = h.stats[k];
   return SEQCDC_OK;
+}
+
+uint64_t seqcdc_set_wait_limit_ns(uint64_t ns) {
+  const uint64_t prev = g_wait_ns;
+  g_wait_ns = ns;
+  return prev;
 }
 
 int seqcdc_profile_events(void *ev_begin, void *ev_end) {

@@ -109,6 +109,8 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
         lib.seqcdc_status.restype = ctypes.c_int
         lib.seqcdc_stats.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_uint32), u32]
         lib.seqcdc_stats.restype = ctypes.c_int
+        lib.seqcdc_set_wait_limit_ns.argtypes = [u64]
+        lib.seqcdc_set_wait_limit_ns.restype = u64
         lib.seqcdc_profile_events.argtypes = [vp, vp]
         lib.seqcdc_profile_events.restype = ctypes.c_int
         lib.seqcdc_fingerprint_batch.argtypes = [vp, u64, vp, u64, vp, vp, u64, vp, vp, vp]
@@ -243,6 +245,15 @@ def seqcdc_stats(d_ws, stream=None, walk: bool = False) -> dict:
     return dict(zip(WALK_STAT_NAMES if walk else STAT_NAMES, list(out)))
 
 
+DEFAULT_WAIT_NS = 2_000_000_000   # SEQCDC_DEFAULT_WAIT_NS
+
+
+def seqcdc_set_wait_limit_ns(ns: int) -> int:
+    """Bound on device-side waits of later calls from this host thread;
+    returns the previous bound (see include/seqcdc.h)."""
+    return int(load_library().seqcdc_set_wait_limit_ns(int(ns)))
+
+
 def seqcdc_profile_events(ev_begin=None, ev_end=None) -> None:
     """Bracket the segment kernel of later calls with two torch.cuda.Events."""
     h = (lambda e: int(e.cuda_event) if e is not None else None)
@@ -273,6 +284,15 @@ def _workspace(p, total, nfiles, tuning, device):
     return ws, ws_bytes
 
 
+def _on_stream(stream, device):
+    """The stream a convenience call runs on (``stream`` or the current one),
+    made current for the call: the tensors it allocates then belong to that
+    stream in PyTorch's caching allocator, and the count it reads back is
+    ordered after the kernels."""
+    import torch
+    return stream if stream is not None else torch.cuda.current_stream(device)
+
+
 def chunk(data, p: Params, tuning=None, stream=None, check: bool = True):
     """Chunk one uint8 CUDA tensor; returns an int64 tensor of cut offsets."""
     import torch
@@ -281,13 +301,15 @@ def chunk(data, p: Params, tuning=None, stream=None, check: bool = True):
     data = data.contiguous().view(-1)
     n = data.numel()
     cap = n // p.min_size + 1
-    cuts = torch.empty(max(cap, 1), dtype=torch.int64, device=data.device)
-    count = torch.zeros(1, dtype=torch.int64, device=data.device)
-    ws, ws_bytes = _workspace(p, n, 1, tuning, data.device)
-    seqcdc_chunk(p, data, n, cuts, cap, count, ws, ws_bytes, tuning, stream)
-    if check:
-        _check(seqcdc_status(ws, stream), "seqcdc_chunk (device)")
-    k = int(count.item())
+    st = _on_stream(stream, data.device)
+    with torch.cuda.stream(st):
+        cuts = torch.empty(max(cap, 1), dtype=torch.int64, device=data.device)
+        count = torch.zeros(1, dtype=torch.int64, device=data.device)
+        ws, ws_bytes = _workspace(p, n, 1, tuning, data.device)
+        seqcdc_chunk(p, data, n, cuts, cap, count, ws, ws_bytes, tuning, st)
+        if check:
+            _check(seqcdc_status(ws, st), "seqcdc_chunk (device)")
+        k = int(count.item())
     return cuts[:k]
 
 
@@ -304,14 +326,16 @@ def chunk_batch(data, offsets, p: Params, tuning=None, stream=None,
     nfiles = offsets.numel() - 1
     total = data.numel()
     cap = total // p.min_size + nfiles
-    cuts = torch.empty(max(cap, 1), dtype=torch.int64, device=data.device)
-    cut_offsets = torch.empty(nfiles + 1, dtype=torch.int64, device=data.device)
-    ws, ws_bytes = _workspace(p, total, nfiles, tuning, data.device)
-    seqcdc_chunk_batch(p, data, total, offsets, nfiles, cuts, cap, cut_offsets,
-                       ws, ws_bytes, tuning, stream)
-    if check:
-        _check(seqcdc_status(ws, stream), "seqcdc_chunk_batch (device)")
-    total_cuts = int(cut_offsets[-1].item())
+    st = _on_stream(stream, data.device)
+    with torch.cuda.stream(st):
+        cuts = torch.empty(max(cap, 1), dtype=torch.int64, device=data.device)
+        cut_offsets = torch.empty(nfiles + 1, dtype=torch.int64, device=data.device)
+        ws, ws_bytes = _workspace(p, total, nfiles, tuning, data.device)
+        seqcdc_chunk_batch(p, data, total, offsets, nfiles, cuts, cap, cut_offsets,
+                           ws, ws_bytes, tuning, st)
+        if check:
+            _check(seqcdc_status(ws, st), "seqcdc_chunk_batch (device)")
+        total_cuts = int(cut_offsets[-1].item())
     return BatchResult(cuts[:total_cuts], cut_offsets)
 
 

@@ -17,7 +17,7 @@ HEADER = os.path.join(os.path.dirname(os.path.dirname(__file__)), "include", "se
 def _declared():
     with open(HEADER) as f:
         text = f.read()
-    return sorted(set(re.findall(r"^[a-z_ ]+\*?\s*(seqcdc_\w+)\(", text, re.M)))
+    return sorted(set(re.findall(r"^[a-z0-9_ ]+\*?\s*(seqcdc_\w+)\(", text, re.M)))
 
 
 def test_header_declares_entry_points():
