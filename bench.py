@@ -7,16 +7,19 @@ text content in 64 KiB pieces, laid out in CSR; 8 KiB parameter setting,
 increasing mode.  Inputs are generated on the host from a fixed seed, copied
 to HBM once, and are far larger than L2 (no flush needed between steps).
 
-Printed: one JSON line with the metric, the device-resident throughput
-(`value`, the path the autotuner picks: the chain walk for this batch), the
-end-to-end throughput through host buffers (`e2e`), the roofline of the
-dominant kernel, the other path (segment map) on the same batch, the plain
-one-launch-per-file loop for comparison, clocks, the CPU oracle as a reported
-baseline (all host cores and one thread), `serve`: p50/p99 latency and
+Printed: a `detail:` line with the verbose results, then the one JSON line.
+The JSON line carries the metric, the device-resident throughput (`value`,
+the path the autotuner picks: the chain walk for this batch), the end-to-end
+throughput through host buffers (`e2e`), the roofline of the dominant kernel
+(with the path and its sizes), clocks, the CPU oracle as a reported baseline,
+and flat scalar fields for the rest: the CUDA-graph step, the plain
+one-launch-per-file loop and the other path on the same batch; the single
+streams (16 MiB random, the 1 GiB backup-like stream, the 64 GiB adversarial
+stream) with their path and kernel roofline fraction; p50/p99 latency and
 sustained GB/s of the continuous-batching server under open-loop Poisson
-arrivals at 25, 50, 100 and 200 GB/s offered load, and `dedup`: the
-deduplication savings of the backup-like stream at the three settings in both
-modes.
+arrivals at 25, 50, 100 and 200 GB/s offered load; the deduplication savings
+of the backup-like stream; SHA-256 fingerprinting; the mean chunk sizes of
+the parameter sweep.  `config` is the same dict in both arms.
 
 `--impl reference` times the CPU oracle (the plain single-threaded chunker,
 files spread over the host cores) on the same workload instead.
@@ -172,6 +175,16 @@ def make_workload(rank: int, nfiles: int = NFILES):
     return W.file_batch(nfiles, seed=SEED + rank)
 
 
+def workload_config(total: int, nfiles: int) -> dict:
+    """The workload both arms report (the same dict, so that the two lines
+    describe the same configuration)."""
+    return {"workload": "batched: %d log-normal files (median 256 KiB, sigma 1.5, "
+                        "4 KiB..64 MiB), half random / half Markov text, CSR" % nfiles,
+            "setting": "8 KiB (Table I; min 4 KiB, max 16 KiB)", "mode": "increasing",
+            "total_bytes": int(total), "nfiles": int(nfiles),
+            "l2": "inputs (%.1f GiB) far larger than L2; no flush" % (total / 2**30)}
+
+
 # Source files each dominant kernel is built from: a DRAM-traffic record
 # under profiles/ is used only while their hash still matches.
 KERNEL_SOURCES = {
@@ -245,9 +258,7 @@ def run_reference(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(total / args.steps * 1e3, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-        "config": {"workload": "10,000 log-normal files (median 256 KiB, sigma 1.5), "
-                               "CSR, 8 KiB setting, increasing mode",
-                   "total_bytes": int(data.size), "nfiles": NFILES},
+        "config": workload_config(data.size, offs.size - 1),
         "cpu_baseline": {"value": round(gbs, 3), "unit": "GB/s", "cores": threads,
                          "kind": "oracle",
                          "sample": "full 10,000-file batch per step, files spread over %d "
@@ -568,6 +579,21 @@ def run_gpu(args):
         torch.cuda.synchronize(dev)
     if rank != 0:
         return
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
+                "unit": "GB/s", "frac": round(achieved / peak, 4),
+                "traffic": traffic, "kernel": kernel,
+                "peak_source": peak_kind,
+                "kernel_ms": round(seg_ms, 4),
+                "algorithmic_bytes": int(alg_bytes),
+                "algorithmic": ("scan spans (%d B, %.3f of the input) + 4 B per cut"
+                                % (span, span / max(total, 1))) if walk else
+                               "every input byte once + 8 B per cut",
+                "input_GBs": round(total / (seg_ms * 1e-3) / 1e9, 1),
+                "path": "chain walk" if walk else "segment map",
+                "piece_bytes": eff.piece_bytes if walk else None,
+                "segment_bytes": None if walk else eff.segment_bytes,
+                "block_threads": None if walk else eff.block_threads,
+                "tuning": tune_src, "cuts": ncuts}
     line = {
         "metric": METRIC,
         "value": round(gbs, 2),
@@ -581,63 +607,72 @@ def run_gpu(args):
         "vs_baseline": None,
         "dtype": "u8",
         "data": "synthetic",
-        "config": {
-            "workload": "batched: %d log-normal files (median 256 KiB, sigma 1.5, "
-                        "4 KiB..64 MiB), half random / half Markov text, CSR; "
-                        "8 KiB setting, increasing mode" % nfiles,
-            "total_bytes": total, "nfiles": nfiles, "cuts": ncuts,
-            "path": "chain walk" if walk else "segment map",
-            "piece_bytes": eff.piece_bytes if walk else None,
-            "segment_bytes": None if walk else eff.segment_bytes,
-            "block_threads": None if walk else eff.block_threads,
-            "tuning": tune_src,
-            "l2": "inputs (%.1f GiB) far larger than L2; no flush" % (total / 2**30),
-            "parallelism": "1 GPU per rank, independent batches (weak scaling)",
-        },
+        "config": workload_config(total, nfiles),
+        "parallelism": "1 GPU per rank, independent batches (weak scaling)",
         "e2e": {"value": round(e2e_gbs, 2), "unit": "GB/s",
                 "h2d_bytes_per_step": int(total + (nfiles + 1) * 8),
                 "d2h_bytes_per_step": int(d2h_pipe),
                 "api": "pipeline.HostBatchPipeline.run (%d file-aligned pieces, copies "
                        "overlapped with chunking)" % pieces,
-                "serial": {"value": round(total * world / e2e_serial_s / 1e9, 2),
-                           "d2h_bytes_per_step": int(d2h),
-                           "api": "one host-to-device copy, seqcdc_chunk_batch, copies back"},
-                "h2d_copy_GBs": {"before": round(h2d_before, 1), "after": round(h2d_gbs, 1)},
+                "serial_GBs": round(total * world / e2e_serial_s / 1e9, 2),
+                "h2d_copy_GBs": round(h2d_before, 1),
+                "h2d_copy_GBs_after": round(h2d_gbs, 1),
                 "runs": "median of %d" % e2e_steps,
                 "host_cpus": ("%d CPUs local to the GPU" % len(numa_cpus)) if numa_cpus
                              else "not bound"},
-        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
-                     "unit": "GB/s", "frac": round(achieved / peak, 4),
-                     "traffic": traffic, "kernel": kernel,
-                     "peak_source": peak_kind,
-                     "kernel_ms": round(seg_ms, 4),
-                     "algorithmic_bytes": int(alg_bytes),
-                     "algorithmic": ("scan spans (%d B, %.3f of the input) + 4 B per cut"
-                                     % (span, span / max(total, 1))) if walk else
-                                    "every input byte once + 8 B per cut",
-                     "input_GBs": round(total / (seg_ms * 1e-3) / 1e9, 1)},
-        "other_path": other,
-        "plain_one_launch_per_file": (
-            {"value": round(total / (plain_ms * 1e-3) / 1e9, 3), "unit": "GB/s",
-             "ms_per_pass": round(plain_ms, 2)} if plain_ms else None),
-        "graph_captured": ({"ms_per_step": round(graph_ms, 4),
-                            "value": round(total * world / (graph_ms * 1e-3) / 1e9, 2)}
-                           if graph_ms else None),
-        "fingerprint": fp,
+        "roofline": roofline,
         "gpu_launches": launches_per_step * args.steps,
-        "path_stats": path_stats,
         "clocks": clocks,
+        "graph_GBs": round(total * world / (graph_ms * 1e-3) / 1e9, 2) if graph_ms else None,
+        "plain_loop_GBs": round(total / (plain_ms * 1e-3) / 1e9, 3) if plain_ms else None,
+        "batched_vs_plain": round(plain_ms / ms_step, 1) if plain_ms else None,
+        "other_path": other["path"] if other else None,
+        "other_path_GBs": other["value"] if other else None,
+        "fingerprint_GBs": fp["value"] if fp else None,
+        "fingerprint_checked": fp["checked_vs_host_sha256"] if fp else None,
+        "fingerprint_mismatches": fp["mismatches"] if fp else None,
     }
+    detail = {"path_stats": path_stats, "other_path": other, "fingerprint": fp,
+              "plain_one_launch_per_file": ({"ms_per_pass": round(plain_ms, 2)}
+                                            if plain_ms else None),
+              "graph_captured": ({"ms_per_step": round(graph_ms, 4)} if graph_ms else None),
+              "e2e_serial_d2h_bytes_per_step": int(d2h)}
     backup = None
-    if not args.no_serve or not args.no_dedup:
+    if not args.no_serve or not args.no_dedup or not args.no_single:
         from paper_2505_21194_gb300 import workloads as W
         backup = W.backup_stream(SEED)
+    if not args.no_single:
+        ss = single_streams(dev, backup, peak, with_cfg5=not args.no_cfg5)
+        detail["single_stream"] = ss
+        for name, r in ss.items():
+            key = name.split("_")[0]
+            line["%s_GBs" % key] = r["GBs"]
+            line["%s_path" % key] = r["path"]
+            line["%s_kernel_frac" % key] = r["frac"]
     if not args.no_serve:
         # batches of a few ~16 MiB requests: the library's own choice per batch
-        line["serve"] = serve_levels(dev, p, None, SERVE_LOADS_GBS, backup)
+        sv = serve_levels(dev, p, None, SERVE_LOADS_GBS, backup)
+        detail["serve"] = sv
+        for lv in sv["levels"]:
+            g = lv["offered_GBs"]
+            line["serve_%d_p50_ms" % g] = lv["p50_ms"]
+            line["serve_%d_p99_ms" % g] = lv["p99_ms"]
+            line["serve_%d_sustained_GBs" % g] = lv["sustained_GBs"]
+        line["serve_checked"] = sv["checked"]
+        line["serve_mismatches"] = sv["mismatches"]
     if not args.no_dedup:
-        line["dedup"] = dedup_savings(dev, backup)
-        line["sweep"] = sweep_report(dev, backup)
+        dd = dedup_savings(dev, backup)
+        sw = sweep_report(dev, backup)
+        detail["dedup"], detail["sweep"] = dd, sw
+        for r in dd["settings"]:
+            if r["mode"] == "increasing":
+                line["dedup_savings_%dKiB" % r["setting_KiB"]] = r["savings"]
+        line["dedup_host_sha256_agrees"] = all(r["host_sha256_agrees"] for r in dd["settings"])
+        for variant in ("seq_length", "seq_length+1", "no_skipping"):
+            means = [r["mean_bytes"] / 1024 for r in sw["uniform_random_256MiB"]
+                     if r["variant"] == variant]
+            line["mean_chunk_KiB_random_%s" % variant.replace("+", "_plus_")] = \
+                "/".join("%.2f" % m for m in means)
     if world == 1 and not args.no_cpu:
         threads = os.cpu_count() or 1
         dt, _ = cpu_oracle_pass(data_np, offs_np, threads)
@@ -658,14 +693,102 @@ def run_gpu(args):
             "kind": "oracle",
             "sample": "%d pass(es) over the full 10,000-file batch, files spread over "
                       "%d host threads" % (reps, threads),
-            "single_thread": {"value": round(int(offs_np[nsamp]) / dt1 / 1e9, 3),
-                              "unit": "GB/s", "cores": 1,
-                              "sample": "the first %d files (%d bytes), one thread"
-                                        % (nsamp, int(offs_np[nsamp]))}}
+            "single_thread_GBs": round(int(offs_np[nsamp]) / dt1 / 1e9, 3),
+            "single_thread_sample": "the first %d files (%d bytes), one thread"
+                                    % (nsamp, int(offs_np[nsamp]))}
+    # The verbose detail first (not JSON-parsed), the one JSON line last.
+    print("detail: " + json.dumps(detail), flush=True)
     print(json.dumps(line), flush=True)
 
 
 SERVE_LOADS_GBS = (25, 50, 100, 200)
+
+
+def time_stream(dev, d, p, peak, reps=5, flush=None, tuning=None):
+    """One device-resident stream chunked by seqcdc_chunk (the library's own
+    path choice unless `tuning` says otherwise): median call time and
+    dominant-kernel time over `reps` calls (CUDA events on the launching
+    stream; `flush`, a tensor larger than L2, is rewritten before each call),
+    the path, the cut count and the dominant kernel's roofline fraction."""
+    import torch
+    from paper_2505_21194_gb300 import seqcdc
+    n = d.numel()
+    cap = n // p.min_size + 1
+    cuts = torch.empty(max(cap, 1), dtype=torch.int64, device=dev)
+    cnt = torch.zeros(1, dtype=torch.int64, device=dev)
+    ws_bytes = seqcdc.seqcdc_workspace_size(p, n, 1, tuning)
+    ws = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    algo = seqcdc.seqcdc_algorithm(p, n, 1, False, ws_bytes, tuning)
+
+    def call():
+        seqcdc.seqcdc_chunk(p, d, n, cuts, cap, cnt, ws, ws_bytes, tuning, stream)
+
+    for _ in range(3):
+        call()
+    if seqcdc.seqcdc_status(ws, stream) != 0:
+        raise RuntimeError("device status during warm-up")
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    for e in ev:
+        e.record(stream)
+    steps, kern = [], []
+    for _ in range(reps):
+        if flush is not None:
+            flush.add_(1)
+        ev[0].record(stream)
+        seqcdc.seqcdc_profile_events(ev[2], ev[3])
+        call()
+        seqcdc.seqcdc_profile_events(None, None)
+        ev[1].record(stream)
+        torch.cuda.synchronize(dev)
+        steps.append(ev[0].elapsed_time(ev[1]))
+        kern.append(ev[2].elapsed_time(ev[3]))
+    if seqcdc.seqcdc_status(ws, stream) != 0:
+        raise RuntimeError("device status in the timed calls")
+    k = int(cnt.item())
+    ms, kms = statistics.median(steps), statistics.median(kern)
+    walk = algo == seqcdc.ALGO_WALK
+    if walk:
+        co = torch.tensor([0, k], dtype=torch.int64, device=dev)
+        alg = scan_span_bytes(cuts, co, k, p) + 4 * k
+    else:
+        alg = n + 8 * k
+    del ws, cuts
+    return {"GBs": round(n / (ms * 1e-3) / 1e9, 2), "ms": round(ms, 4),
+            "path": "chain walk" if walk else "segment map",
+            "kernel": "walk_kernel" if walk else "map_kernel",
+            "kernel_ms": round(kms, 4), "cuts": k, "bytes": n,
+            "frac": round(alg / (kms * 1e-3) / 1e9 / peak, 4),
+            "algorithmic_bytes": int(alg)}
+
+
+def single_streams(dev, backup, peak, with_cfg5=True):
+    """The single-stream workloads: 16 MiB of uniform random bytes (seed 0,
+    8 KiB setting; L2 flushed before every call), the ~1 GiB backup-like
+    stream (8 KiB setting, increasing) and the 64 GiB adversarial stream
+    (16 KiB setting), each in one seqcdc_chunk call."""
+    import torch
+    from paper_2505_21194_gb300 import seqcdc, workloads as W
+    out = {}
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    d = torch.from_numpy(W.uniform_random(16 << 20, SEED)).to(dev)
+    out["cfg1_16MiB_random"] = time_stream(dev, d, seqcdc.seqcdc_params(8, 0), peak,
+                                           reps=7, flush=flush)
+    del d, flush
+    d = torch.from_numpy(backup[0]).to(dev)
+    out["cfg2_1GiB_backup"] = time_stream(dev, d, seqcdc.seqcdc_params(8, 0), peak)
+    del d
+    if with_cfg5:
+        block, nblocks = 16 << 20, 4096
+        d = torch.empty(block * nblocks, dtype=torch.uint8, device=dev)
+        for i in range(nblocks):
+            d[i * block:(i + 1) * block].copy_(
+                torch.from_numpy(W.adversarial_block(i, SEED, block)))
+        out["cfg5_64GiB_adversarial"] = time_stream(dev, d, seqcdc.seqcdc_params(16, 0),
+                                                    peak, reps=3)
+        del d
+    torch.cuda.empty_cache()
+    return out
 
 
 def sweep_report(dev, backup):
@@ -812,6 +935,10 @@ def main():
                     help="skip the deduplication-savings report on the backup-like stream")
     ap.add_argument("--no-serve", action="store_true",
                     help="skip the serving measurement (open-loop Poisson arrivals)")
+    ap.add_argument("--no-single", action="store_true",
+                    help="skip the single-stream workloads (16 MiB, 1 GiB, 64 GiB)")
+    ap.add_argument("--no-cfg5", action="store_true",
+                    help="skip the 64 GiB adversarial stream among the single streams")
     ap.add_argument("--nfiles", type=int, default=NFILES,
                     help="files in the batch (default: the 10,000-file workload)")
     args = ap.parse_args()

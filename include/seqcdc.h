@@ -147,6 +147,15 @@ size_t seqcdc_workspace_size(const seqcdc_params_t *p, uint64_t total_bytes,
                              uint64_t nfiles, const seqcdc_tuning_t *tuning);
 
 /*
+ * The path (SEQCDC_ALGO_MAP or SEQCDC_ALGO_WALK) that a chunking call with
+ * these arguments takes: seqcdc_chunk() for batch == 0 (nfiles = 1),
+ * seqcdc_chunk_batch() otherwise, with a workspace of ws_bytes bytes.
+ * Returns 0 for an invalid parameter set.  Makes no CUDA call.
+ */
+int seqcdc_algorithm(const seqcdc_params_t *p, uint64_t total_bytes, uint64_t nfiles,
+                     int batch, size_t ws_bytes, const seqcdc_tuning_t *tuning);
+
+/*
  * Chunk one byte stream d_in[0..n).
  *   d_cuts   out: up to `cap` uint64 chunk end offsets.
  *   cap      capacity of d_cuts in entries; must be >= n / min_size + 1

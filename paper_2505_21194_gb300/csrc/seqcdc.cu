@@ -1544,6 +1544,22 @@ bool resolve_smem_configured(size_t smem) {
   return true;
 }
 
+// The path a call takes: use_walk's rule, and for AUTO with a workspace too
+// small for the segment map but large enough for the chain walk, the walk
+// (same output): a workspace sized for a larger batch then serves every
+// smaller call, as the walk's workspace grows with the bytes and the files
+// while the map's is larger.
+bool decide_walk(const seqcdc_params_t *p, uint64_t total, uint64_t nfiles, bool batch,
+                 size_t ws_bytes, const seqcdc_tuning_t *tuning) {
+  bool walk = use_walk(tuning, nfiles, batch);
+  if (!walk && (!tuning || tuning->algorithm == SEQCDC_ALGO_AUTO) &&
+      ws_bytes < make_layout(p, total, nfiles, pick_segment(p, tuning)).total &&
+      ws_bytes >= seqcdc_walk::workspace_bytes(p, total, nfiles,
+                                               seqcdc_walk::pick_piece(p, tuning)))
+    walk = true;
+  return walk;
+}
+
 int run(const seqcdc_params_t *p, const uint8_t *d_data, uint64_t total,
         const uint64_t *d_offsets, uint64_t nfiles, uint64_t *d_cuts,
         uint64_t cap, uint64_t *d_cut_offsets, uint64_t *d_count, void *d_ws,
@@ -1552,16 +1568,7 @@ int run(const seqcdc_params_t *p, const uint8_t *d_data, uint64_t total,
   if (!d_ws || ((uintptr_t)d_ws & 255u)) return SEQCDC_EINVAL;
   if (total > 0 && (!d_data || ((uintptr_t)d_data & 15u))) return SEQCDC_EINVAL;
   if (total > 0 && !d_cuts) return SEQCDC_EINVAL;
-  bool walk = use_walk(tuning, nfiles, d_offsets != nullptr);
-  // AUTO with a workspace too small for the segment map but large enough for
-  // the chain walk takes the walk (same output): a workspace sized for a
-  // larger batch then serves every smaller call, as the walk's workspace
-  // grows with the bytes and the files while the map's is larger.
-  if (!walk && (!tuning || tuning->algorithm == SEQCDC_ALGO_AUTO) &&
-      ws_bytes < make_layout(p, total, nfiles, pick_segment(p, tuning)).total &&
-      ws_bytes >= seqcdc_walk::workspace_bytes(p, total, nfiles,
-                                               seqcdc_walk::pick_piece(p, tuning)))
-    walk = true;
+  const bool walk = decide_walk(p, total, nfiles, d_offsets != nullptr, ws_bytes, tuning);
   if (walk) {
     if (cap < total / p->min_size + nfiles) return SEQCDC_ECAPACITY;
     if (ws_bytes < seqcdc_walk::workspace_bytes(p, total, nfiles,
@@ -1703,6 +1710,13 @@ size_t seqcdc_workspace_size(const seqcdc_params_t *p, uint64_t total_bytes,
   if (nfiles != 1) return as_batch;
   const size_t as_stream = workspace_for(p, total_bytes, nfiles, tuning, false);
   return as_batch > as_stream ? as_batch : as_stream;
+}
+
+int seqcdc_algorithm(const seqcdc_params_t *p, uint64_t total_bytes, uint64_t nfiles,
+                     int batch, size_t ws_bytes, const seqcdc_tuning_t *tuning) {
+  if (!params_ok(p)) return 0;
+  return decide_walk(p, total_bytes, nfiles, batch != 0, ws_bytes, tuning)
+             ? (int)SEQCDC_ALGO_WALK : (int)SEQCDC_ALGO_MAP;
 }
 
 int seqcdc_chunk(const seqcdc_params_t *p, const uint8_t *d_in, uint64_t n,

@@ -98,6 +98,8 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
         lib.seqcdc_resolve_tuning.restype = ctypes.c_int
         lib.seqcdc_workspace_size.argtypes = [P, u64, u64, T]
         lib.seqcdc_workspace_size.restype = ctypes.c_size_t
+        lib.seqcdc_algorithm.argtypes = [P, u64, u64, ctypes.c_int, ctypes.c_size_t, T]
+        lib.seqcdc_algorithm.restype = ctypes.c_int
         lib.seqcdc_chunk.argtypes = [P, vp, u64, vp, u64, vp, vp, ctypes.c_size_t, T, vp]
         lib.seqcdc_chunk.restype = ctypes.c_int
         lib.seqcdc_chunk_batch.argtypes = [P, vp, u64, vp, u64, vp, u64, vp, vp,
@@ -189,6 +191,16 @@ def seqcdc_workspace_size(p: Params, total_bytes: int, nfiles: int,
     if n == 0:
         raise SeqCDCError(SEQCDC_EINVAL, "seqcdc_workspace_size")
     return n
+
+
+def seqcdc_algorithm(p: Params, total_bytes: int, nfiles: int, batch: bool,
+                     ws_bytes: int, tuning=None) -> int:
+    """ALGO_MAP or ALGO_WALK: the path a call with these arguments takes."""
+    a = load_library().seqcdc_algorithm(ctypes.byref(p), total_bytes, nfiles,
+                                        1 if batch else 0, ws_bytes, _tuning(tuning))
+    if a == 0:
+        raise SeqCDCError(SEQCDC_EINVAL, "seqcdc_algorithm")
+    return a
 
 
 def seqcdc_chunk(p: Params, d_in, n: int, d_cuts, cap: int, d_count, d_ws,
