@@ -309,8 +309,7 @@ def run_gpu(args):
         best = (0, 0, seqcdc.ALGO_AUTO, 0)
     tuning = seqcdc.Tuning(*best)
     eff = seqcdc.seqcdc_resolve_tuning(p, tuning)
-    walk = best[2] == seqcdc.ALGO_WALK or (best[2] == seqcdc.ALGO_AUTO and
-                                          nfiles >= seqcdc.WALK_MIN_FILES)
+    walk = seqcdc.seqcdc_algorithm(p, total, nfiles, True, 1 << 62, tuning) == seqcdc.ALGO_WALK
     cap = total // p.min_size + nfiles
     ws_bytes = seqcdc.seqcdc_workspace_size(p, total, nfiles, tuning)
 
@@ -537,8 +536,9 @@ def run_gpu(args):
         kernel = "walk_kernel"
         span = scan_span_bytes(d_cuts, d_co, ncuts, p)
         alg_bytes = span + ncuts * 4
-        # plan_tiles, plan_scan, fill, walk, verify, repair, count, emit
-        launches_per_step = 8
+        # plan_tiles, plan_scan, fill, walk, 3 x (verify, run_repair), verify,
+        # repair, count, emit
+        launches_per_step = 14
     else:
         kernel = "map_kernel"
         span = None

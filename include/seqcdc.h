@@ -89,15 +89,14 @@ typedef struct {
  *                  (128, 256, 512; any other value means the default).
  *   algorithm      SEQCDC_ALGO_AUTO (0), SEQCDC_ALGO_MAP or SEQCDC_ALGO_WALK.
  *                  AUTO takes the chain walk for batches of at least
- *                  SEQCDC_WALK_MIN_FILES files and the segment map otherwise,
- *                  except that a call whose workspace is too small for the
- *                  segment map but large enough for the chain walk takes the
- *                  chain walk (so a workspace sized for a larger call serves
- *                  every smaller one).
- *                  The chain walk needs many chains (pieces) at once to be
- *                  fast, and walks stretches without run ends (long runs of
- *                  equal bytes, where every cut is forced at max_size) one
- *                  file at a time; the segment map has neither limit.
+ *                  SEQCDC_WALK_MIN_FILES files and for any call of at least
+ *                  SEQCDC_WALK_MIN_PIECES full pieces (total_bytes /
+ *                  piece_bytes), and the segment map otherwise, except that
+ *                  a call whose workspace is too small for the segment map
+ *                  but large enough for the chain walk takes the chain walk
+ *                  (so a workspace sized for a larger call serves every
+ *                  smaller one).  The chain walk needs many chains (pieces)
+ *                  at once to be fast; the segment map does not.
  *   piece_bytes    chain walk: bytes of a piece, the unit one warp walks
  *                  (rounded up to a multiple of 64 KiB; at least
  *                  4 x max_size, at most 64 MiB; default 768 KiB, or
@@ -107,6 +106,7 @@ typedef struct {
 #define SEQCDC_ALGO_MAP  1u
 #define SEQCDC_ALGO_WALK 2u
 #define SEQCDC_WALK_MIN_FILES 256u
+#define SEQCDC_WALK_MIN_PIECES 256u
 typedef struct {
     uint32_t segment_bytes;
     uint32_t block_threads;
@@ -204,9 +204,12 @@ int seqcdc_chunk_batch(const seqcdc_params_t *p, const uint8_t *d_data,
  *   SEQCDC_NOALLOC_SCRATCH_BYTES  size of that array.  It is part of the
  *             library image: every GPU that loads the library holds these
  *             bytes until the process exits.  The input may be at most as
- *             large as fits: seqcdc_workspace_size(p, n, 1, tuning) must not
- *             exceed it (about 112 MiB of input for the paper's parameter
- *             sets), else SEQCDC_ERANGE is returned before anything runs.
+ *             large as fits: the call takes the path whose workspace fits
+ *             in it (with AUTO, the chain walk where the segment map's would
+ *             not), and that workspace must not exceed it, else
+ *             SEQCDC_ERANGE is returned before anything runs.  With the
+ *             paper's parameter sets that is up to about 1 GiB of input at
+ *             the 4 KB setting, 4 GiB at 8 KB and 8 GiB at 16 KB.
  *   d_in, n, d_cuts, cap, d_count, tuning, stream  as for seqcdc_chunk().
  *   d_status  optional (may be NULL): one uint32 on the device that receives
  *             the call's device-side status (SEQCDC_OK, SEQCDC_ETIMEOUT or

@@ -76,11 +76,12 @@ def candidates(p, segments: Iterable[int] = SEGMENTS, threads: Iterable[int] = T
     return out
 
 
-def default_candidate(p, nfiles: int, batch: bool = True) -> Tuple[int, int, int, int]:
-    """The tuple a call with the library defaults runs as (AUTO resolved:
-    the chain walk for batches of at least SEQCDC_WALK_MIN_FILES files)."""
+def default_candidate(p, nfiles: int, batch: bool = True,
+                      total_bytes: int = 0) -> Tuple[int, int, int, int]:
+    """The tuple a call with the library defaults runs as (AUTO resolved by
+    the library's own rule, seqcdc_algorithm)."""
     eff = seqcdc.seqcdc_resolve_tuning(p)
-    if batch and nfiles >= seqcdc.WALK_MIN_FILES:
+    if seqcdc.seqcdc_algorithm(p, total_bytes, nfiles, batch, 1 << 62) == seqcdc.ALGO_WALK:
         return (0, 0, seqcdc.ALGO_WALK, eff.piece_bytes)
     return (eff.segment_bytes, eff.block_threads, seqcdc.ALGO_MAP, 0)
 
@@ -172,7 +173,7 @@ def autotune(p, d_data, d_offsets, cache_path: Optional[str] = None,
     cands = cands or candidates(p)
     timer = timer or time_candidate
     times = {tuple(c): timer(p, d_data, d_offsets, tuple(c)) for c in cands}
-    best = pick_best(times, default_candidate(p, int(sizes.size)))
+    best = pick_best(times, default_candidate(p, int(sizes.size), True, int(sizes.sum())))
     store_cache(path, key, {"tuning": list(best), "ms": times[best],
                             "sample_bytes": int(d_data.numel()),
                             "timed": {"x".join(str(v) for v in c): round(t, 4)

@@ -1394,15 +1394,18 @@ uint32_t pick_segment(const seqcdc_params_t *p, const seqcdc_tuning_t *t) {
   return L;
 }
 
-// Which path a call takes: the tuning's choice, else the chain walk for
-// batches of many files (each piece is a chain one warp walks; a batch of
-// few large files or one stream gives too few of them at once) and the
-// segment map otherwise.
-bool use_walk(const seqcdc_tuning_t *t, uint64_t nfiles, bool batch) {
+// Which path a call takes: the tuning's choice, else the chain walk when
+// the call has many chains to walk at once (each piece is a chain one warp
+// walks): batches of many files, or at least SEQCDC_WALK_MIN_PIECES full
+// pieces of input; the segment map otherwise (a short stream or a batch of
+// few small files gives too few chains).
+bool use_walk(const seqcdc_params_t *p, const seqcdc_tuning_t *t, uint64_t total,
+              uint64_t nfiles, bool batch) {
   const uint32_t a = t ? t->algorithm : SEQCDC_ALGO_AUTO;
   if (a == SEQCDC_ALGO_WALK) return true;
   if (a == SEQCDC_ALGO_MAP) return false;
-  return batch && nfiles >= SEQCDC_WALK_MIN_FILES;
+  if (batch && nfiles >= SEQCDC_WALK_MIN_FILES) return true;
+  return total / seqcdc_walk::pick_piece(p, t) >= SEQCDC_WALK_MIN_PIECES;
 }
 
 size_t workspace_for(const seqcdc_params_t *p, uint64_t total, uint64_t nfiles,
@@ -1482,7 +1485,7 @@ WsPtrs ws_ptrs(void *d_ws, const Layout &l) {
 
 size_t workspace_for(const seqcdc_params_t *p, uint64_t total, uint64_t nfiles,
                      const seqcdc_tuning_t *t, bool batch) {
-  if (use_walk(t, nfiles, batch))
+  if (use_walk(p, t, total, nfiles, batch))
     return seqcdc_walk::workspace_bytes(p, total, nfiles, seqcdc_walk::pick_piece(p, t));
   return make_layout(p, total, nfiles, pick_segment(p, t)).total;
 }
@@ -1551,7 +1554,7 @@ bool resolve_smem_configured(size_t smem) {
 // while the map's is larger.
 bool decide_walk(const seqcdc_params_t *p, uint64_t total, uint64_t nfiles, bool batch,
                  size_t ws_bytes, const seqcdc_tuning_t *tuning) {
-  bool walk = use_walk(tuning, nfiles, batch);
+  bool walk = use_walk(p, tuning, total, nfiles, batch);
   if (!walk && (!tuning || tuning->algorithm == SEQCDC_ALGO_AUTO) &&
       ws_bytes < make_layout(p, total, nfiles, pick_segment(p, tuning)).total &&
       ws_bytes >= seqcdc_walk::workspace_bytes(p, total, nfiles,
@@ -1743,8 +1746,14 @@ int seqcdc_chunk_noalloc(const seqcdc_params_t *p, const uint8_t *d_in,
                          uint64_t *d_count, uint32_t *d_status,
                          const seqcdc_tuning_t *tuning, void *stream) {
   if (!d_count || !params_ok(p)) return SEQCDC_EINVAL;
-  const size_t need = workspace_for(p, n, 1, tuning, false);
-  if (need > (size_t)SEQCDC_NOALLOC_SCRATCH_BYTES) return SEQCDC_ERANGE;
+  // The path the call takes with this scratch (AUTO takes the chain walk
+  // where the segment map's workspace would not fit), and its workspace.
+  const size_t scratch = (size_t)SEQCDC_NOALLOC_SCRATCH_BYTES;
+  const size_t need =
+      decide_walk(p, n, 1, false, scratch, tuning)
+          ? seqcdc_walk::workspace_bytes(p, n, 1, seqcdc_walk::pick_piece(p, tuning))
+          : make_layout(p, n, 1, pick_segment(p, tuning)).total;
+  if (need > scratch) return SEQCDC_ERANGE;
   void *ws = noalloc_scratch_address();
   if (!ws) return SEQCDC_ECUDA;
   const int rc = run(p, d_in, n, nullptr, 1, d_cuts, cap, nullptr, d_count, ws,

@@ -62,6 +62,8 @@ constexpr uint32_t kNoBad = 0xFFFFFFFFu;
 constexpr uint32_t kFull = 0xFFFFFFFFu;
 constexpr uint32_t kDefaultPiece = 768u << 10;
 constexpr uint32_t kPrefetch = 2048;   // bytes asked of L2 for the next chunk's scan
+// Rounds of verify + parallel run repair before the sequential repair.
+constexpr uint32_t kWalkRepairRounds = 3;
 
 // Workspace header: status and statistics at the offsets seqcdc_status and
 // seqcdc_stats read.
@@ -71,7 +73,9 @@ struct WalkHeader {
   uint32_t npieces;
   uint32_t stats[8];
   uint32_t nlong, nshort;  // walk-order fill counters
-  uint32_t pad[51];
+  uint32_t nruns[kWalkRepairRounds];  // runs of inconsistent pieces found by each verify round
+  uint32_t runq[kWalkRepairRounds];   // run queue head of each parallel repair round
+  uint32_t pad[51 - 2 * kWalkRepairRounds];
 };
 static_assert(sizeof(WalkHeader) == 256, "walk header is 256 bytes");
 
@@ -114,6 +118,9 @@ struct WPtrs {
   uint32_t *first_bad;   // per file: first inconsistent piece
   uint32_t *count;       // per piece: cuts it owns (c with start < c <= end)
   uint32_t *ctile;       // per compaction tile: their sum
+  uint32_t *bad;         // per piece: round + 1 if the verify of that round found it inconsistent
+  uint32_t *runs;        // first pieces of the runs of inconsistent pieces (one round's list)
+  uint32_t *claim;       // per piece: the last repair round (round + 1) that owns it
 };
 
 __device__ __forceinline__ uint64_t wfile_start(const WGeom &g, uint64_t f) {
@@ -285,6 +292,10 @@ __global__ void wplan_scan_kernel(WGeom g, DevParams p, WPtrs w, uint64_t nftile
     h->npieces = running;
     h->nlong = 0;
     h->nshort = 0;
+    for (uint32_t q = 0; q < kWalkRepairRounds; ++q) {
+      h->nruns[q] = 0;
+      h->runq[q] = 0;
+    }
     for (int k = 0; k < 8; ++k) h->stats[k] = 0;
   }
   for (uint64_t f = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; f < g.nfiles;
@@ -313,6 +324,7 @@ __global__ void wfill_kernel(WGeom g, WPtrs w) {
     }
     w.piece_file[k] = (uint32_t)a;
     w.sdone[k] = 0u;
+    w.claim[k] = 0u;
     const uint64_t ps = wfile_start(g, a) + (k - w.piece_base[a]) * (uint64_t)g.P;
     longp = w.piece_base[a + 1] - w.piece_base[a] > 1u ||
             wfile_end(g, a) - ps >= (uint64_t)(g.P >> 1);
@@ -668,23 +680,91 @@ walk_kernel(WGeom g, DevParams p, WPtrs w) {
 // ---------------------------------------------------------------------------
 // Verify and repair.
 // ---------------------------------------------------------------------------
-__global__ void wverify_kernel(WGeom g, DevParams p, WPtrs w) {
+// Whether piece k (not a file's first) was walked from a wrong entry: its
+// junction started somewhere other than its predecessor's exit.
+__device__ __forceinline__ bool inconsistent(const WGeom &g, const WPtrs &w, uint32_t k,
+                                             uint32_t f, uint32_t kl) {
+  const uint64_t lb_prev = w.list_base[f] + (uint64_t)(kl - 1u) * g.fullcap;
+  return exit_of(w, k - 1u, lb_prev) - g.P != w.jin[k];
+}
+
+// Round `round` < kWalkRepairRounds: flag the inconsistent pieces and list
+// the first piece of every maximal run of them for the parallel repair.
+// Round kWalkRepairRounds: record each file's first inconsistent piece for
+// the sequential repair.
+__global__ void wverify_kernel(WGeom g, DevParams p, WPtrs w, uint32_t round) {
   const uint32_t np = w.hdr->npieces;
   uint32_t bad = 0;
   for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < np;
        k += (uint64_t)gridDim.x * blockDim.x) {
     const uint32_t f = w.piece_file[k];
     const uint32_t kl = (uint32_t)k - w.piece_base[f];
-    if (kl == 0) continue;
-    const uint64_t lb_prev = w.list_base[f] + (uint64_t)(kl - 1u) * g.fullcap;
-    const uint32_t x = exit_of(w, (uint32_t)k - 1u, lb_prev) - g.P;
-    if (x != w.jin[k]) {
+    const bool is_bad = kl > 0 && inconsistent(g, w, (uint32_t)k, f, kl);
+    if (round < kWalkRepairRounds) {
+      w.bad[k] = is_bad ? round + 1u : 0u;
+      if (is_bad && (kl == 1 || !inconsistent(g, w, (uint32_t)k - 1u, f, kl - 1u))) {
+        // A run starts here: it and the piece before it (whose exit the run's
+        // repair starts from) belong to this round's repair of the run.
+        atomicMax(&w.claim[k], round + 1u);
+        atomicMax(&w.claim[k - 1], round + 1u);
+        w.runs[atomicAdd(&w.hdr->nruns[round], 1u)] = (uint32_t)k;
+      }
+    } else if (is_bad) {
       atomicMin(&w.first_bad[f], (uint32_t)k);
-      ++bad;
     }
+    bad += is_bad ? 1u : 0u;
   }
   for (int d = 16; d; d >>= 1) bad += __shfl_down_sync(kFull, bad, d);
-  if ((threadIdx.x & 31) == 0 && bad) atomicAdd(&w.hdr->stats[WS_INCONSISTENT], bad);
+  if (round == 0 && (threadIdx.x & 31) == 0 && bad)
+    atomicAdd(&w.hdr->stats[WS_INCONSISTENT], bad);
+}
+
+// Parallel repair: one warp per run of inconsistent pieces (from the list of
+// this round), pieces in order: each piece whose junction input differs from
+// its predecessor's exit walks again from that exit.  Past the end of its
+// run the warp goes on while its new exits keep changing the next piece's
+// input (stretches where every piece's own walk agrees with its neighbours'
+// but not with the true chain, such as runs of equal bytes or ramps), taking
+// each such piece by raising its claim to this round; it stops at a piece
+// already claimed this round.  Every run's first piece and the piece before
+// it are claimed by the verify, so each piece has at most one writer per
+// round, and the piece a run's repair starts from is written by nobody.
+// What a round leaves inconsistent the next round's verify lists again.
+__global__ void __launch_bounds__(kWalkThreads)
+wrun_repair_kernel(WGeom g, DevParams p, WPtrs w, uint32_t round) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t nruns = w.hdr->nruns[round];
+  const uint32_t tag = round + 1u;
+  uint32_t redone = 0, chunks = 0, wins = 0;
+  bool ok = true;
+  for (;;) {
+    uint32_t t = 0;
+    if (lane == 0) t = atomicAdd(&w.hdr->runq[round], 1u);
+    t = __shfl_sync(kFull, t, 0);
+    if (t >= nruns) break;
+    const uint32_t a = w.runs[t];
+    const uint32_t kend = w.piece_base[w.piece_file[a] + 1];
+    bool in_run = true;
+    for (uint32_t k = a; k < kend; ++k) {
+      const Piece pc = piece_of(g, w, p, k);
+      const uint32_t x = exit_of(w, k - 1u, pc.lb - g.fullcap) - g.P;
+      if (in_run && (k == a || w.bad[k] == tag)) {
+        if (x == w.jin[k]) continue;
+      } else {
+        in_run = false;
+        if (x == w.jin[k]) break;  // the chain agrees from here on
+        uint32_t old = 0;
+        if (lane == 0) old = atomicMax(&w.claim[k], tag);
+        if (__shfl_sync(kFull, old, 0) >= tag) break;  // another run's piece
+      }
+      junction_walk(g, p, w, k, pc, x, nullptr, chunks, wins, ok);
+      ++redone;
+    }
+  }
+  if (lane == 0) {
+    if (redone) atomicAdd(&w.hdr->stats[WS_REPAIRED], redone);
+    if (!ok) set_status(w.hdr, SEQCDC_ECAPACITY);
+  }
 }
 
 // One warp per file (files taken in strides): from the first inconsistent
@@ -820,7 +900,7 @@ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 struct WLayout {
   size_t hdr, piece_base, list_base, ftile, ftile_l, piece_file, order, spec_n, spec, jin,
-      jn, jm, jexit, jcut, first_bad, count, ctile, sdone, total;
+      jn, jm, jexit, jcut, first_bad, count, ctile, sdone, bad, runs, claim, total;
   uint64_t npmax, nlist, nftiles, nctiles;
   uint32_t P, fullcap;
 };
@@ -860,6 +940,9 @@ WLayout make_wlayout(const seqcdc_params_t *p, uint64_t total, uint64_t nfiles, 
   l.count = take(l.npmax * 4);
   l.ctile = take(l.nctiles * 4);
   l.sdone = take(l.npmax * 4);
+  l.bad = take(l.npmax * 4);
+  l.runs = take(l.npmax * 4);
+  l.claim = take(l.npmax * 4);
   l.total = o;
   return l;
 }
@@ -885,6 +968,9 @@ WPtrs wptrs(void *d_ws, const WLayout &l) {
   w.count = reinterpret_cast<uint32_t *>(b + l.count);
   w.ctile = reinterpret_cast<uint32_t *>(b + l.ctile);
   w.sdone = reinterpret_cast<uint32_t *>(b + l.sdone);
+  w.bad = reinterpret_cast<uint32_t *>(b + l.bad);
+  w.runs = reinterpret_cast<uint32_t *>(b + l.runs);
+  w.claim = reinterpret_cast<uint32_t *>(b + l.claim);
   return w;
 }
 
@@ -936,7 +1022,18 @@ int run(const seqcdc_params_t *p, const uint8_t *d_data, uint64_t total,
   walk_kernel<<<wgrid, kWalkThreads, 0, st>>>(g, dp, w);
   if (prof_end) cudaEventRecord(static_cast<cudaEvent_t>(prof_end), st);
   const uint64_t vb = (l.npmax + 255) / 256;
-  wverify_kernel<<<(unsigned)(vb < 4096 ? vb : 4096), 256, 0, st>>>(g, dp, w);
+  const unsigned vgrid = (unsigned)(vb < 4096 ? vb : 4096);
+  // Rounds of verify + parallel run repair (a persistent grid of warps takes
+  // runs from the round's list), then the last verify for the sequential
+  // repair of whatever is left.
+  const uint64_t rwant = (l.npmax + 3) / 4;
+  const uint64_t rmost = 4u * (uint64_t)sms;
+  const unsigned rrgrid = (unsigned)(rwant < rmost ? (rwant ? rwant : 1) : rmost);
+  for (uint32_t round = 0; round < kWalkRepairRounds; ++round) {
+    wverify_kernel<<<vgrid, 256, 0, st>>>(g, dp, w, round);
+    wrun_repair_kernel<<<rrgrid, kWalkThreads, 0, st>>>(g, dp, w, round);
+  }
+  wverify_kernel<<<vgrid, 256, 0, st>>>(g, dp, w, kWalkRepairRounds);
   const uint64_t rb = (nfiles + 3) / 4;
   const uint64_t rcap = 4u * (uint64_t)sms;
   wrepair_kernel<<<(unsigned)(rb < rcap ? (rb ? rb : 1) : rcap), kWalkThreads, 0, st>>>(g, dp, w);

@@ -145,9 +145,10 @@ def test_resolve_tuning_piece_rules(seqcdc_lib):
 
 
 def test_workspace_follows_the_path(seqcdc_lib):
-    """A batch of at least SEQCDC_WALK_MIN_FILES files takes the chain walk by
-    default and sizes its workspace for it; forcing either path sizes for
-    that path; a single stream is sized for the path it may take."""
+    """A batch of at least SEQCDC_WALK_MIN_FILES files, or of at least
+    SEQCDC_WALK_MIN_PIECES full pieces, takes the chain walk by default and
+    sizes its workspace for it; forcing either path sizes for that path; a
+    short single stream takes the segment map."""
     s = seqcdc_lib
     p = s.seqcdc_params(8, 0)
     total, many, few = 8 << 30, s.WALK_MIN_FILES, s.WALK_MIN_FILES - 1
@@ -155,8 +156,20 @@ def test_workspace_follows_the_path(seqcdc_lib):
     smap = s.seqcdc_workspace_size(p, total, many, (0, 0, s.ALGO_MAP, 0))
     assert walk < smap
     assert s.seqcdc_workspace_size(p, total, many) == walk
+    # few files but many pieces: still the walk; few files of few pieces: the map
     assert s.seqcdc_workspace_size(p, total, few) == \
-        s.seqcdc_workspace_size(p, total, few, (0, 0, s.ALGO_MAP, 0))
+        s.seqcdc_workspace_size(p, total, few, (0, 0, s.ALGO_WALK, 0))
+    small = (s.WALK_MIN_PIECES - 1) * (768 << 10)
+    assert s.seqcdc_workspace_size(p, small, few) == \
+        s.seqcdc_workspace_size(p, small, few, (0, 0, s.ALGO_MAP, 0))
+    big = ws = 1 << 62
+    for t, nf, batch, algo in ((small, 1, False, s.ALGO_MAP),
+                               (small + (768 << 10), 1, False, s.ALGO_WALK),
+                               (small, few, True, s.ALGO_MAP),
+                               (small, many, True, s.ALGO_WALK),
+                               (total, 1, False, s.ALGO_WALK)):
+        assert s.seqcdc_algorithm(p, t, nf, batch, ws) == algo, (t, nf, batch)
+    assert s.seqcdc_algorithm(p, total, 1, False, big, (0, 0, s.ALGO_MAP, 0)) == s.ALGO_MAP
     # 8 GiB in 768 KiB pieces: the walk's lists take a few bytes per input KiB
     assert walk < total // 64
 

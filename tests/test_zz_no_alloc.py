@@ -54,8 +54,9 @@ def test_noalloc_matches_allocating_entry_point_twice(gpu):
 def test_noalloc_refuses_inputs_beyond_its_scratch(gpu):
     s = gpu
     p = s.seqcdc_params(8, 0)
-    n = 1 << 30  # far more than the fixed scratch can plan for
-    assert s.seqcdc_workspace_size(p, n, 1) > s.SEQCDC_NOALLOC_SCRATCH_BYTES
+    n = 64 << 30  # far more than the fixed scratch can plan for, on either path
+    for algo in (s.ALGO_MAP, s.ALGO_WALK):
+        assert s.seqcdc_workspace_size(p, n, 1, (0, 0, algo, 0)) > s.SEQCDC_NOALLOC_SCRATCH_BYTES
     lib = s.load_library()
     import ctypes
     rc = lib.seqcdc_chunk_noalloc(ctypes.byref(p), 1 << 40, n, 1 << 40, n, 1 << 40,
