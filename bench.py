@@ -649,6 +649,10 @@ def run_gpu(args):
             line["%s_GBs" % key] = r["GBs"]
             line["%s_path" % key] = r["path"]
             line["%s_kernel_frac" % key] = r["frac"]
+            if "host_stream" in r:
+                line["%s_host_stream_GBs" % key] = r["host_stream"]["GBs"]
+                line["%s_host_h2d_copy_GBs" % key] = r["host_stream"]["h2d_copy_GBs"]
+                line["%s_host_stream_same_cuts" % key] = r["host_stream"]["same_cuts"]
     if not args.no_serve:
         # batches of a few ~16 MiB requests: the library's own choice per batch
         sv = serve_levels(dev, p, None, SERVE_LOADS_GBS, backup)
@@ -668,6 +672,14 @@ def run_gpu(args):
             if r["mode"] == "increasing":
                 line["dedup_savings_%dKiB" % r["setting_KiB"]] = r["savings"]
         line["dedup_host_sha256_agrees"] = all(r["host_sha256_agrees"] for r in dd["settings"])
+        sr = sw["search"]
+        for reading in (0, 1):
+            line["search_table1_mean_KiB_reading%d" % reading] = "/".join(
+                "%.2f" % (sr[k]["table1"]["mean_bytes_by_reading"][reading] / 1024)
+                for k in (4, 8, 16))
+            line["search_settings_within_5pct_reading%d" % reading] = "/".join(
+                str(sum(1 for r in sr[k]["within"] if r["reading"] == reading))
+                for k in (4, 8, 16))
         for variant in ("seq_length", "seq_length+1", "no_skipping"):
             means = [r["mean_bytes"] / 1024 for r in sw["uniform_random_256MiB"]
                      if r["variant"] == variant]
@@ -777,7 +789,33 @@ def single_streams(dev, backup, peak, with_cfg5=True):
     del d, flush
     d = torch.from_numpy(backup[0]).to(dev)
     out["cfg2_1GiB_backup"] = time_stream(dev, d, seqcdc.seqcdc_params(8, 0), peak)
-    del d
+    # The same stream fed from pinned host memory in 256 MiB blocks through the
+    # resumable stream pipeline (copies overlapped with chunking), against the
+    # bare host-to-device copy of the same bytes.
+    from paper_2505_21194_gb300.pipeline import HostStreamPipeline
+    h = torch.from_numpy(backup[0]).pin_memory()
+    n = h.numel()
+    pipe = HostStreamPipeline(seqcdc.seqcdc_params(8, 0), device=str(dev))
+    blocks = [h[a:a + (256 << 20)] for a in range(0, n, 256 << 20)]
+    ref = pipe.run(blocks)
+    ts, tc = [], []
+    for _ in range(3):
+        torch.cuda.synchronize(dev)
+        t = time.perf_counter()
+        got = pipe.run(blocks)
+        ts.append(time.perf_counter() - t)
+        torch.cuda.synchronize(dev)
+        t = time.perf_counter()
+        d.copy_(h, non_blocking=True)
+        torch.cuda.synchronize(dev)
+        tc.append(time.perf_counter() - t)
+    same = bool(got.size == out["cfg2_1GiB_backup"]["cuts"] and np.array_equal(got, ref))
+    out["cfg2_1GiB_backup"]["host_stream"] = {
+        "GBs": round(n / statistics.median(ts) / 1e9, 2),
+        "h2d_copy_GBs": round(n / statistics.median(tc) / 1e9, 2),
+        "same_cuts": same, "blocks": len(blocks),
+        "api": "pipeline.HostStreamPipeline.run, 256 MiB pinned blocks, median of 3"}
+    del d, h, pipe
     if with_cfg5:
         block, nblocks = 16 << 20, 4096
         d = torch.empty(block * nblocks, dtype=torch.uint8, device=dev)
@@ -812,6 +850,15 @@ def sweep_report(dev, backup):
                              "mean_bytes": r["mean_bytes"], "at_max": r["at_max"]})
         out[name] = rows
         del d
+    # Sec. V's Monte-Carlo search: SeqLength 3..8 x SkipTrigger 20..80 (step
+    # 5) x SkipSize 128/256/512, Sec. VI's min / max, both readings of
+    # SeqLength, on 64 MiB of uniform random bytes.
+    from paper_2505_21194_gb300.sweep import search
+    d = torch.from_numpy(W.uniform_random(64 << 20, SEED + 9)).to(dev)
+    t = time.perf_counter()
+    out["search"] = search(d)
+    out["search_s"] = round(time.perf_counter() - t, 2)
+    del d
     return out
 
 
@@ -896,7 +943,7 @@ def serve_levels(dev, p, tuning, loads, backup, duration_s=1.0):
                 b = stream[voffs[k]:voffs[k + 1]]
                 expect[k] = oracle.chunk(b, op).astype(np.int64)
                 alone[k] = seqcdc.chunk(torch.from_numpy(b).to(dev), p, tuning).cpu().numpy()
-            got = st.results[r.rid]
+            got = st.results[r.rid].cpu().numpy()
             checked += 1
             bad += int(not (np.array_equal(got, expect[k]) and np.array_equal(got, alone[k])))
         levels.append({"offered_GBs": gbs, "requests": st.requests, "batches": st.batches,
@@ -907,7 +954,8 @@ def serve_levels(dev, p, tuning, loads, backup, duration_s=1.0):
             "arrivals": "Poisson, open loop, %.1f s per level" % duration_s,
             "hbm_budget_GiB": 64, "max_batch_GiB": 4, "levels": levels,
             "checked": checked, "mismatches": bad,
-            "latency": "arrival to completion of the batch's copy back (device clock)"}
+            "latency": "arrival to completion of the batch's chunking (device clock); "
+                       "cut lists stay on the device"}
 
 
 def main():

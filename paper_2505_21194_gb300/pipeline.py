@@ -7,13 +7,15 @@ pinned host memory), with a few device slots in rotation: while piece k is
 chunked, piece k+1 is copied in and the cut lists of piece k-1 are copied
 out.  Files are chunked independently, so the pieces are too.
 
-``chunk_stream_host`` chunks one long stream delivered as host blocks of any
-size (more than fits on the device, if need be).  A chunk depends only on
-bytes from its start to start + max_size, so every cut of a prefix except its
-last is a cut of the whole stream (Sec. IV: a forced cut at the end of the
-input is the only cut the end decides).  Each block is chunked together with
-the bytes after the previous block's last proven cut; the final cut of the
-last block is the stream end.
+``HostStreamPipeline`` (and ``chunk_stream_host`` on top of it) chunks one
+long stream delivered as host blocks of any size (more than fits on the
+device, if need be), resumable block by block.  A chunk depends only on bytes
+from its start to start + max_size, so every cut of a prefix except its last
+is a cut of the whole stream (Sec. IV: a forced cut at the end of the input is
+the only cut the end decides).  Each block is chunked together with the bytes
+after the previous block's last proven cut, kept on the device; the copy of a
+block to the device overlaps the chunking of the one before; the final cut of
+the last block is the stream end.
 
 All chunking runs in the library's CUDA kernels; this module moves bytes and
 orders streams.
@@ -165,31 +167,173 @@ def chunk_batch_host(h_data, h_offsets, p, pieces: int = 16, slots: int = 3,
     return HostBatchPipeline(p, tuning, device, slots).run(h_data, h_offsets, pieces)
 
 
+class HostStreamPipeline:
+    """Chunking of one long stream that arrives as host blocks of any size,
+    resumable block by block, with the copies overlapped.
+
+    A chunk depends only on the bytes from its start to start + max_size
+    (Sec. IV), so every cut of a prefix except its last is a cut of the whole
+    stream.  Each block is chunked together with the bytes after the
+    previous block's last proven cut (the carried tail, at most max_size
+    bytes, kept on the device).  Per block:
+      1. its bytes go host -> device into a staging slot on a copy stream
+         (``slots`` slots in rotation, reused across calls);
+      2. meanwhile the host waits for the previous block's chunking and reads
+         its cut count and cut list (small device -> host copies);
+      3. on the compute stream the carried tail and the block are copied
+         device -> device, back to back, into an aligned work buffer (two in
+         rotation), which ``seqcdc_chunk`` chunks; its cut list is copied to
+         pinned host memory.
+    So the copy of block i+1 runs while block i is chunked.  ``feed`` returns
+    the proven cuts of the block before (absolute offsets); ``finish`` returns
+    the rest, ending at the stream end.  Blocks larger than ``block_bytes`` are
+    taken in parts.  Pinned host blocks (torch tensors) are copied
+    asynchronously; numpy or pageable blocks go through a pinned staging copy
+    on the host first.
+    """
+
+    def __init__(self, p, tuning=None, device="cuda", block_bytes: int = 256 << 20,
+                 slots: int = 3):
+        import torch
+        self.torch = torch
+        self.p, self.tuning = p, tuning
+        self.dev = torch.device(device)
+        self.B = max(int(block_bytes), 1 << 16)
+        self.mx = int(p.max_size)
+        self.copy_in = torch.cuda.Stream(self.dev)
+        self.compute = torch.cuda.Stream(self.dev)
+        n = self.B + self.mx
+        self.cap = n // p.min_size + 1
+        self.stage = [torch.empty(self.B, dtype=torch.uint8, device=self.dev)
+                      for _ in range(max(2, slots))]
+        self.h_stage = [None] * len(self.stage)   # pinned staging, made when needed
+        self.stage_free = [None] * len(self.stage)
+        # a 16-byte aligned work buffer per rotation step (the chunker's rule)
+        self.work = [torch.empty(n + 16, dtype=torch.uint8, device=self.dev) for _ in range(2)]
+        self.cuts = [torch.empty(self.cap, dtype=torch.int64, device=self.dev) for _ in range(2)]
+        self.count = [torch.zeros(1, dtype=torch.int64, device=self.dev) for _ in range(2)]
+        self.h_cuts = [torch.empty(self.cap, dtype=torch.int64, pin_memory=True) for _ in range(2)]
+        self.h_count = [torch.zeros(1, dtype=torch.int64, pin_memory=True) for _ in range(2)]
+        self.ws_bytes = seqcdc.seqcdc_workspace_size(p, n, 1, tuning)
+        self.ws = [torch.empty(self.ws_bytes, dtype=torch.uint8, device=self.dev)
+                   for _ in range(2)]
+        self.h_status = [torch.zeros(1, dtype=torch.int32, pin_memory=True) for _ in range(2)]
+        self.reset()
+
+    def reset(self):
+        """Start a new stream (the carried tail is dropped)."""
+        self.base = 0          # absolute offset of work[cur][0]
+        self.nblk = 0          # blocks (parts) chunked so far
+        self.pending = None    # (work index, bytes in the work buffer, event)
+        self.carry = (None, 0, 0)  # (work index, offset of the tail, its length)
+
+    def _part(self, blk):
+        """Copy one part (<= block_bytes) host -> device staging; returns
+        (staging index, length, event)."""
+        torch = self.torch
+        k = self.nblk % len(self.stage)
+        n = int(blk.numel() if hasattr(blk, "numel") else blk.size)
+        if self.stage_free[k] is not None:
+            self.copy_in.wait_event(self.stage_free[k])
+        src = blk
+        if not (hasattr(blk, "is_pinned") and blk.is_pinned()):
+            if self.h_stage[k] is None:
+                self.h_stage[k] = torch.empty(self.B, dtype=torch.uint8, pin_memory=True)
+            h = self.h_stage[k]
+            if self.stage_free[k] is not None:
+                self.stage_free[k].synchronize()  # its last copy out of h_stage is over
+            h[:n].copy_(torch.from_numpy(np.ascontiguousarray(blk, dtype=np.uint8))
+                        if not hasattr(blk, "numel") else blk)
+            src = h[:n]
+        with torch.cuda.stream(self.copy_in):
+            self.stage[k][:n].copy_(src, non_blocking=True)
+            ev = torch.cuda.Event()
+            ev.record(self.copy_in)
+        return k, n, ev
+
+    def _collect(self, final: bool):
+        """Wait for the pending chunking; return its proven cuts (all of them
+        when `final`) and set the carried tail."""
+        if self.pending is None:
+            return np.empty(0, np.int64)
+        w, nbytes, ev = self.pending
+        self.pending = None
+        ev.synchronize()
+        st = int(self.h_status[w][0])
+        if st != seqcdc.SEQCDC_OK:
+            raise seqcdc.SeqCDCError(st, "HostStreamPipeline (device)")
+        k = int(self.h_count[w][0])
+        cuts = self.h_cuts[w][:k].numpy()
+        if final or k <= 1:
+            keep = cuts if final else cuts[:0]
+        else:
+            keep = cuts[:-1]
+        last = int(keep[-1]) if keep.size and not final else 0
+        out = keep + self.base
+        if not final:
+            self.carry = (w, last, nbytes - last)
+            self.base += last
+        return out
+
+    def _chunk_part(self, k, n, loaded):
+        torch = self.torch
+        w = self.nblk % 2
+        cw, coff, clen = self.carry
+        self.compute.wait_event(loaded)
+        with torch.cuda.stream(self.compute):
+            if clen:
+                self.work[w][:clen].copy_(self.work[cw][coff:coff + clen])
+            self.work[w][clen:clen + n].copy_(self.stage[k][:n])
+            freed = torch.cuda.Event()
+            freed.record(self.compute)
+        self.stage_free[k] = freed
+        total = clen + n
+        seqcdc.seqcdc_chunk(self.p, self.work[w], total, self.cuts[w], self.cap, self.count[w],
+                            self.ws[w], self.ws_bytes, self.tuning, self.compute)
+        with torch.cuda.stream(self.compute):
+            self.h_count[w].copy_(self.count[w], non_blocking=True)
+            self.h_cuts[w][:self.cap].copy_(self.cuts[w], non_blocking=True)
+            self.h_status[w].copy_(self.ws[w][:4].view(torch.int32), non_blocking=True)
+            ev = torch.cuda.Event()
+            ev.record(self.compute)
+        self.pending = (w, total, ev)
+        self.nblk += 1
+
+    def feed(self, blk) -> np.ndarray:
+        """Add a block (pinned torch uint8 tensor, or numpy bytes); returns the
+        cuts proven so far that were not returned before (absolute)."""
+        outs = []
+        n = int(blk.numel() if hasattr(blk, "numel") else np.asarray(blk).size)
+        for a in range(0, n, self.B):
+            part = blk[a:min(n, a + self.B)]
+            k, m, loaded = self._part(part)           # copy in: overlaps the chunking before
+            outs.append(self._collect(final=False))   # wait for the previous part
+            self._chunk_part(k, m, loaded)
+        return np.concatenate(outs) if outs else np.empty(0, np.int64)
+
+    def finish(self) -> np.ndarray:
+        """The remaining cuts, the last one at the stream end; then reset."""
+        out = self._collect(final=True)   # the last part fed is always pending
+        self.reset()
+        return out
+
+    def run(self, blocks) -> np.ndarray:
+        """Cut list of the whole stream given as an iterable of blocks."""
+        parts = [self.feed(b) for b in blocks]
+        parts.append(self.finish())
+        return np.concatenate(parts)
+
+
 def chunk_stream_host(blocks: Iterable[np.ndarray], p, tuning=None,
-                      device="cuda") -> Iterator[np.ndarray]:
+                      device="cuda", block_bytes: int = 256 << 20) -> Iterator[np.ndarray]:
     """Chunk one stream given as host blocks (any sizes); yields the absolute
     cut offsets block by block (their concatenation is the stream's cut
-    list).  The device holds one block plus the carried tail at a time."""
-    import torch
-    dev = torch.device(device)
-    carry = np.empty(0, dtype=np.uint8)
-    base = 0
+    list), through a HostStreamPipeline (copies overlapped with chunking)."""
+    pipe = HostStreamPipeline(p, tuning, device, block_bytes)
     for blk in blocks:
-        blk = np.asarray(blk, dtype=np.uint8)
-        buf = np.concatenate([carry, blk]) if carry.size else blk
-        if buf.size == 0:
-            continue
-        d = torch.from_numpy(buf).to(dev)
-        cuts = seqcdc.chunk(d, p, tuning).cpu().numpy()
-        del d
-        if cuts.size > 1:
-            keep = cuts[:-1]
-            yield keep + base
-            last = int(keep[-1])
-            carry = buf[last:].copy()
-            base += last
-        else:
-            carry = buf.copy()
-    if carry.size:
-        d = torch.from_numpy(carry).to(dev)
-        yield seqcdc.chunk(d, p, tuning).cpu().numpy() + base
+        out = pipe.feed(blk)
+        if out.size:
+            yield out
+    out = pipe.finish()
+    if out.size:
+        yield out

@@ -3,12 +3,17 @@
 Requests are byte strings held in pinned host memory that arrive over time
 (open loop).  The server admits arrived requests first come, first served,
 while the request bytes in flight on the device stay within an HBM budget.
-Each admission round becomes one CSR batch: the requests are copied into one
-device buffer on a copy stream, chunked by ``seqcdc_chunk_batch`` on a compute
-stream (each file of a batch is chunked as if it were alone), and their cut
-lists are copied back to pinned host memory.  A request's latency runs from
-its arrival to the completion of its batch, read on the device clock (CUDA
-events) and aligned to the host clock at the start of the run.
+Each admission round becomes one CSR batch in one of a few preallocated
+pipeline slots (device buffers for the bytes, offsets, cut lists and a
+workspace that fits any batch on either chunking path), so that serving
+allocates no device memory per batch: the requests are copied into the slot
+on a copy stream and chunked by ``seqcdc_chunk_batch`` on a compute stream
+(each file of a batch is chunked as if it were alone).  Cut lists stay on the
+device; only the batch's 4-byte status word comes back, and the cut lists of
+the requests the caller asks for are kept as device tensors.  A request's
+latency runs from its arrival to the completion of its batch's chunking, read
+on the device clock (CUDA events) and aligned to the host clock at the start
+of the run.
 
 The batching rule (``form_batch``) and the statistics are plain functions so
 that they can be checked without a GPU.  The chunking itself runs only in the
@@ -82,14 +87,28 @@ def poisson_arrivals(rate_per_s: float, duration_s: float, npayloads: int,
 
 
 @dataclasses.dataclass
+class _Slot:
+    """Device buffers of one pipeline slot, allocated once: request bytes,
+    CSR offsets, cut lists, CSR index and a workspace that fits any batch of
+    up to max_bytes bytes and max_files files on either chunking path."""
+    data: object
+    offs: object
+    cuts: object
+    co: object
+    ws: object
+    ws_bytes: int
+    h_offs: object        # pinned staging for the offsets
+    h_status: object      # pinned: the device status word of the slot's last batch
+
+
+@dataclasses.dataclass
 class _Batch:
     reqs: List[Request]
     nbytes: int
-    done: object          # torch.cuda.Event after the copy back
-    keep: tuple           # device tensors alive until the batch is done
-    h_cuts: object        # pinned host int64
-    h_co: object          # pinned host int64
-    slot: int             # staging slot
+    done: object          # CUDA event: the batch is chunked (latency ends here)
+    ready: object         # CUDA event: its status word (and kept results) copied
+    slot: int
+    kept: Optional[tuple]  # (cuts, cut offsets) device copies when a request is kept
 
 
 @dataclasses.dataclass
@@ -100,13 +119,14 @@ class ServeStats:
     wall_s: float
     sustained_gbs: float
     latency: Dict[str, float]
-    results: Dict[int, np.ndarray]      # cut lists of the requests asked for
+    results: Dict[int, object]      # cut lists (device tensors) of the requests asked for
 
 
 class Server:
     """One GPU, one copy stream and one compute stream; up to ``max_inflight``
-    batches in the pipeline (copy of one overlapping the chunking of the
-    previous)."""
+    batches in the pipeline (the copy of one overlapping the chunking of the
+    previous), each in its own preallocated slot, so that serving allocates
+    no device memory per batch."""
 
     def __init__(self, p, pool, pool_offsets, budget_bytes: int = 64 * GIB,
                  max_batch_bytes: int = 4 * GIB, max_inflight: int = 3,
@@ -130,58 +150,61 @@ class Server:
         self.compute = torch.cuda.Stream(self.device)
         self.max_files = int(max_batch_files)
         seqcdc.load_library()
-        # Pinned staging for each pipeline slot, allocated once: offsets in,
-        # cut lists and CSR index out (a batch's cut list is bounded by its
-        # bytes / min_size + its files).
-        big = max(self.max_batch, int(self.sizes.max(initial=0)))
+        # A batch holds at most max_batch bytes, or one payload larger than that.
+        big = max(self.max_batch, int(self.sizes.max(initial=0)), 16)
         cap = big // p.min_size + self.max_files
-        self._stage = [(torch.empty(self.max_files + 1, dtype=torch.int64, pin_memory=True),
-                        torch.empty(cap, dtype=torch.int64, pin_memory=True),
-                        torch.empty(self.max_files + 1, dtype=torch.int64, pin_memory=True))
+        nf = self.max_files
+        ws_bytes = max(seqcdc.seqcdc_workspace_size(p, big, nf, (0, 0, seqcdc.ALGO_MAP, 0)),
+                       seqcdc.seqcdc_workspace_size(p, big, nf, (0, 0, seqcdc.ALGO_WALK, 0)))
+        if tuning is not None:
+            ws_bytes = max(ws_bytes, seqcdc.seqcdc_workspace_size(p, big, nf, tuning))
+        dev = self.device
+        self._slots = [_Slot(torch.empty(big, dtype=torch.uint8, device=dev),
+                             torch.empty(nf + 1, dtype=torch.int64, device=dev),
+                             torch.empty(cap, dtype=torch.int64, device=dev),
+                             torch.empty(nf + 1, dtype=torch.int64, device=dev),
+                             torch.empty(ws_bytes, dtype=torch.uint8, device=dev), ws_bytes,
+                             torch.empty(nf + 1, dtype=torch.int64, pin_memory=True),
+                             torch.zeros(1, dtype=torch.int32, pin_memory=True))
                        for _ in range(self.max_inflight)]
-        self._free_stage = list(range(self.max_inflight))
+        self._free = list(range(self.max_inflight))
 
     # -- one batch ---------------------------------------------------------
-    def _launch(self, reqs: List[Request]) -> _Batch:
+    def _launch(self, reqs: List[Request], keep: set) -> _Batch:
         torch = self.torch
         sizes = np.array([r.nbytes for r in reqs], dtype=np.int64)
         offs = np.zeros(len(reqs) + 1, dtype=np.int64)
         np.cumsum(sizes, out=offs[1:])
-        total = int(offs[-1])
-        nfiles = len(reqs)
+        total, nfiles = int(offs[-1]), len(reqs)
         cap = total // self.p.min_size + nfiles
-        slot = self._free_stage.pop()
-        h_offs_all, h_cuts_all, h_co_all = self._stage[slot]
-        h_offs = h_offs_all[:nfiles + 1]
-        h_offs.copy_(torch.from_numpy(offs))
+        k = self._free.pop()
+        s = self._slots[k]
+        # The slot's previous batch has completed (it was popped as done), so
+        # its staging and device buffers are free.
+        s.h_offs[:nfiles + 1].copy_(torch.from_numpy(offs))
         with torch.cuda.stream(self.copy):
-            d_data = torch.empty(max(total, 16), dtype=torch.uint8, device=self.device)
             for r, o in zip(reqs, offs[:-1].tolist()):
                 src = self.pool[int(self.offs[r.payload]):int(self.offs[r.payload + 1])]
-                d_data[o:o + r.nbytes].copy_(src, non_blocking=True)
-            d_offs = h_offs.to(self.device, non_blocking=True)
+                s.data[o:o + r.nbytes].copy_(src, non_blocking=True)
+            s.offs[:nfiles + 1].copy_(s.h_offs[:nfiles + 1], non_blocking=True)
             copied = torch.cuda.Event()
             copied.record(self.copy)
         self.compute.wait_event(copied)
+        seqcdc.seqcdc_chunk_batch(self.p, s.data, total, s.offs, nfiles, s.cuts, cap, s.co,
+                                  s.ws, s.ws_bytes, self.tuning, self.compute)
         with torch.cuda.stream(self.compute):
-            d_cuts = torch.empty(max(cap, 1), dtype=torch.int64, device=self.device)
-            d_co = torch.empty(nfiles + 1, dtype=torch.int64, device=self.device)
-            ws_bytes = seqcdc.seqcdc_workspace_size(self.p, total, nfiles, self.tuning)
-            d_ws = torch.empty(ws_bytes, dtype=torch.uint8, device=self.device)
-            # the copy stream wrote these; the compute stream reads them
-            d_data.record_stream(self.compute)
-            d_offs.record_stream(self.compute)
-            seqcdc.seqcdc_chunk_batch(self.p, d_data, total, d_offs, nfiles, d_cuts,
-                                      cap, d_co, d_ws, ws_bytes, self.tuning,
-                                      self.compute)
-            h_cuts = h_cuts_all[:max(cap, 1)]
-            h_co = h_co_all[:nfiles + 1]
-            h_cuts.copy_(d_cuts, non_blocking=True)
-            h_co.copy_(d_co, non_blocking=True)
             done = torch.cuda.Event(enable_timing=True)
             done.record(self.compute)
-        return _Batch(reqs, total, done, (d_data, d_offs, d_cuts, d_co, d_ws, h_offs),
-                      h_cuts, h_co, slot)
+            # the batch's device status word (4 bytes back per batch)
+            s.h_status.copy_(s.ws[:4].view(torch.int32), non_blocking=True)
+            kept = None
+            if any(r.rid in keep for r in reqs):
+                # requests the caller asked for: their cut lists stay on the
+                # device, copied out of the slot before it is reused
+                kept = (s.cuts[:max(cap, 1)].clone(), s.co[:nfiles + 1].clone())
+            ready = torch.cuda.Event()
+            ready.record(self.compute)
+        return _Batch(reqs, total, done, ready, k, kept)
 
     # -- the serving loop --------------------------------------------------
     def run(self, arrivals: Iterable[Request], keep: Optional[set] = None,
@@ -192,7 +215,7 @@ class Server:
         queue: collections.deque = collections.deque()
         inflight: collections.deque = collections.deque()
         inflight_bytes = 0
-        lat, results = [], {}
+        lat, kept_batches = [], []
         nbatches, nbytes = 0, 0
         first_arrival = arrivals[0].arrival if arrivals else 0.0
         last_done = first_arrival
@@ -208,32 +231,41 @@ class Server:
                 queue.append(arrivals[i])
                 i += 1
             progressed = False
-            while inflight and inflight[0].done.query():
+            while inflight and inflight[0].ready.query():
                 b = inflight.popleft()
                 t_done = start.elapsed_time(b.done) / 1e3
                 last_done = max(last_done, t_done)
-                co = b.h_co.numpy()
-                cuts = b.h_cuts.numpy()
-                for j, r in enumerate(b.reqs):
+                for r in b.reqs:
                     lat.append(t_done - r.arrival)
-                    if r.rid in keep:
-                        results[r.rid] = cuts[co[j]:co[j + 1]].copy()
+                st = int(self._slots[b.slot].h_status[0])
+                if st != seqcdc.SEQCDC_OK:
+                    raise seqcdc.SeqCDCError(st, "serve batch (device)")
+                if b.kept is not None:
+                    kept_batches.append(b)
                 inflight_bytes -= b.nbytes
                 nbytes += b.nbytes
-                self._free_stage.append(b.slot)
+                self._free.append(b.slot)
                 progressed = True
-            if queue and len(inflight) < self.max_inflight:
+            if queue and len(inflight) < self.max_inflight and self._free:
                 k = form_batch(queue, inflight_bytes, self.budget, self.max_batch,
                                self.max_files)
                 if k:
                     reqs = [queue.popleft() for _ in range(k)]
-                    b = self._launch(reqs)
+                    b = self._launch(reqs, keep)
                     inflight.append(b)
                     inflight_bytes += b.nbytes
                     nbatches += 1
                     progressed = True
             if not progressed:
                 time.sleep(poll_s)
+        torch.cuda.synchronize(self.device)
+        results = {}
+        for b in kept_batches:
+            cuts, co = b.kept
+            co_h = co.cpu().numpy()
+            for j, r in enumerate(b.reqs):
+                if r.rid in keep:
+                    results[r.rid] = cuts[int(co_h[j]):int(co_h[j + 1])]
         wall = max(last_done - first_arrival, 1e-9)
         return ServeStats(len(lat), nbatches, nbytes, wall, nbytes / wall / 1e9,
                           latency_stats(lat), results)

@@ -83,3 +83,37 @@ def test_host_pipeline_reused_and_growing(gpu):
         c, co = pipe.run(torch.from_numpy(data).pin_memory(), offs, pieces=4)
         assert np.array_equal(co, r.cut_offsets.cpu().numpy())
         assert np.array_equal(c, r.cuts.cpu().numpy())
+
+
+@pytest.mark.gpu
+def test_host_stream_pipeline_resumable_uneven_blocks(gpu):
+    """A 40 MiB stream through 4 MiB slots in uneven blocks (one larger than
+    a slot, some of a few bytes), with a stretch of constant bytes (no run
+    ends: every cut there is forced at max_size): after every feed the cuts
+    returned so far are a prefix of the oracle's; the whole list equals it;
+    the pipeline is reused for a second stream (numpy blocks this time)."""
+    import torch
+    from paper_2505_21194_gb300.pipeline import HostStreamPipeline
+    s = gpu
+    rng = np.random.default_rng(11)
+    data = W.mixed_base(40 << 20, 12)
+    data[(9 << 20):(9 << 20) + 700000] = 7
+    for kib, mode in ((8, 0), (16, 1)):
+        p = s.seqcdc_params(kib, mode)
+        exp = oracle.chunk(data, oracle.presets(kib, mode)).astype(np.int64)
+        pipe = HostStreamPipeline(p, block_bytes=4 << 20)
+        h = torch.from_numpy(data).pin_memory()
+        bounds = [0, 3, 17, 5 << 20, (5 << 20) + 1, 11 << 20, 19 << 20, 19 << 20,
+                  (30 << 20) + 12345, data.size]
+        got = []
+        for a, b in zip(bounds[:-1], bounds[1:]):
+            got.append(pipe.feed(h[a:b]))
+            so_far = np.concatenate(got)
+            assert np.array_equal(so_far, exp[:so_far.size])
+            assert so_far.size == 0 or so_far[-1] <= b
+        got.append(pipe.finish())
+        assert np.array_equal(np.concatenate(got), exp)
+        # reuse: the same stream again, in numpy blocks of random sizes
+        cut = np.unique(rng.integers(0, data.size, 7))
+        blocks = np.split(data, cut)
+        assert np.array_equal(pipe.run(blocks), exp)

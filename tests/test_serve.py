@@ -1,8 +1,9 @@
 """Serving: the batching rule and statistics on the CPU; the server on the GPU.
 
 On the GPU, every request of a short open-loop run is checked: its cut list
-from the batch it was served in must equal the oracle's for its payload and
-the library's cut list for the payload chunked alone (tolerance 0).
+from the batch it was served in (a device tensor) must equal the oracle's for
+its payload and the library's cut list for the payload chunked alone
+(tolerance 0); a second run checks that serving allocates no device memory.
 """
 from __future__ import annotations
 
@@ -80,4 +81,14 @@ def test_server_results_equal_oracle_and_alone(gpu):
             assert np.array_equal(got_alone, exp)
         alone[k] = exp
     for r in arr:
-        assert np.array_equal(st.results[r.rid], alone[r.payload]), r
+        got = st.results[r.rid]
+        assert got.is_cuda                       # cut lists stay on the device
+        assert np.array_equal(got.cpu().numpy(), alone[r.payload]), r
+    # Serving allocates nothing per batch: every buffer is in a slot made when
+    # the server was built (with no request kept, not even the result copies).
+    torch.cuda.synchronize()
+    before = torch.cuda.memory_stats()["allocation.all.allocated"]
+    st2 = srv.run(poisson_arrivals(400.0, 0.25, len(payloads), sizes, seed=5))
+    torch.cuda.synchronize()
+    assert st2.batches > 0 and st2.results == {}
+    assert torch.cuda.memory_stats()["allocation.all.allocated"] == before

@@ -32,3 +32,35 @@ def test_sweep_means_equal_oracle(gpu):
         assert r["mean_bytes"] == pytest.approx(data.size / cuts.size, abs=0.05)
         sizes = np.diff(np.concatenate([[0], cuts.astype(np.int64)]))
         assert r["at_max"] == pytest.approx(float((sizes == s[5]).mean()), abs=1e-4)
+
+
+def test_target_limits_follow_sec_vi(seqcdc_lib):
+    from paper_2505_21194_gb300.sweep import target_limits
+    for kib in (4, 8, 16):
+        o = oracle.presets(kib)
+        assert target_limits(kib) == (o.min_size, o.max_size)
+
+
+@pytest.mark.gpu
+def test_search_means_equal_oracle(gpu):
+    """Every mean the search reports (a wide tolerance keeps the whole small
+    grid) equals the oracle's on the same sample, under both readings."""
+    import torch
+    from paper_2505_21194_gb300.sweep import search, target_limits
+    data = W.uniform_random(4 << 20, 21)
+    d = torch.from_numpy(data).cuda()
+    res = search(d, targets_kib=(4, 16), seq_lengths=(4, 5), triggers=(50, 55),
+                 skip_sizes=(256, 512), tol=10.0)
+    checked = 0
+    for kib, r in res.items():
+        mn, mx = target_limits(kib)
+        assert len(r["within"]) == 2 * 2 * 2 * 2        # the whole grid
+        for row in r["within"]:
+            q = Params(0, row["seq_length"] + row["reading"], row["skip_trigger"],
+                       row["skip_size"], mn, mx)
+            cuts = oracle.chunk(data, q)
+            assert row["mean_bytes"] == pytest.approx(data.size / cuts.size, abs=0.05)
+            checked += 1
+        # Table I's row is in the grid: its means under both readings
+        assert set(r["table1"]["mean_bytes_by_reading"]) == {0, 1}
+    assert checked == 32
