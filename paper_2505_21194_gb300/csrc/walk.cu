@@ -61,7 +61,6 @@ constexpr uint32_t kUnmerged = 0xFFFFFFFFu;
 constexpr uint32_t kNoBad = 0xFFFFFFFFu;
 constexpr uint32_t kFull = 0xFFFFFFFFu;
 constexpr uint32_t kDefaultPiece = 768u << 10;
-constexpr uint32_t kPrefetch = 2048;   // bytes asked of L2 for the next chunk's scan
 // Rounds of verify + parallel run repair before the sequential repair.
 constexpr uint32_t kWalkRepairRounds = 3;
 
@@ -384,9 +383,10 @@ __device__ __forceinline__ Win load_win(const WGeom &g, uint64_t base) {
 // A window is 1 KiB loaded at once; a 512-byte half is classified only when
 // the scan reaches it.  Lane l's word of a half holds the half's positions
 // 16 l .. 16 l + 15 in bits 0..15.  Positions are 32-bit offsets from the
-// first window's start.  While the chunk is scanned, L2 is asked for the
-// 2 KiB where the next chunk's scan can start at the earliest (min_size
-// after this scan's start), where it does start for most chunks.
+// first window's start.  Only the windows the scan reaches are read: with
+// many chains in flight per SM the loads' latency is hidden (an L2 prefetch
+// of the next chunk's likely window, 1-3 KiB, measured no faster and moved
+// three to four times the bytes).
 __device__ uint64_t chunk_end_warp(const WGeom &g, const DevParams &p, uint64_t c,
                                    uint64_t fend, uint32_t &wins, bool &ok) {
   const int lane = threadIdx.x & 31;
@@ -394,12 +394,6 @@ __device__ uint64_t chunk_end_warp(const WGeom &g, const DevParams &p, uint64_t 
   const uint64_t lim_abs = c + (rest > p.mx ? p.mx : rest);
   const uint64_t r_abs = c + (p.mn > p.R ? p.mn - p.R : 0u);
   if (r_abs + 1 >= lim_abs) return lim_abs;
-  if (lane == 0) {
-    const uint64_t a = (r_abs + p.mn + 15) & ~15ull;
-    if (a + kPrefetch <= g.total)
-      asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(g.data + a),
-                   "r"(kPrefetch) : "memory");
-  }
   const uint64_t cb = r_abs & ~15ull;
   Win cur = load_win(g, cb);
   ++wins;
@@ -734,6 +728,7 @@ __global__ void __launch_bounds__(kWalkThreads)
 wrun_repair_kernel(WGeom g, DevParams p, WPtrs w, uint32_t round) {
   const int lane = threadIdx.x & 31;
   const uint32_t nruns = w.hdr->nruns[round];
+  if (nruns == 0) return;  // the usual case once the chains are consistent
   const uint32_t tag = round + 1u;
   uint32_t redone = 0, chunks = 0, wins = 0;
   bool ok = true;
@@ -1027,7 +1022,7 @@ int run(const seqcdc_params_t *p, const uint8_t *d_data, uint64_t total,
   // runs from the round's list), then the last verify for the sequential
   // repair of whatever is left.
   const uint64_t rwant = (l.npmax + 3) / 4;
-  const uint64_t rmost = 4u * (uint64_t)sms;
+  const uint64_t rmost = 2u * (uint64_t)sms;
   const unsigned rrgrid = (unsigned)(rwant < rmost ? (rwant ? rwant : 1) : rmost);
   for (uint32_t round = 0; round < kWalkRepairRounds; ++round) {
     wverify_kernel<<<vgrid, 256, 0, st>>>(g, dp, w, round);
