@@ -217,6 +217,8 @@ int seqcdc_chunk_batch(const seqcdc_params_t *p, const uint8_t *d_data,
  * It calls no cudaMalloc, cudaFree or other allocating routine.  The first
  * call on a device looks up the array's device address (once per device,
  * with that device current); make that first call before any stream capture.
+ * A cudaDeviceReset() unloads the library's device image and invalidates
+ * that address: do not use this entry point after one in the same process.
  * All calls share the one array and it keeps the last call's contents (the
  * kernels reset what they need): calls that overlap on the GPU -- from two
  * streams or two host threads without ordering -- race and give wrong results.
