@@ -189,9 +189,9 @@ def workload_config(total: int, nfiles: int) -> dict:
 # under profiles/ is used only while their hash still matches.
 KERNEL_SOURCES = {
     "walk_kernel": ("paper_2505_21194_gb300/csrc/walk.cu",
-                    "paper_2505_21194_gb300/csrc/common.cuh", "include/seqcdc.h"),
+                    "paper_2505_21194_gb300/csrc/common.cuh"),
     "map_kernel": ("paper_2505_21194_gb300/csrc/seqcdc.cu",
-                   "paper_2505_21194_gb300/csrc/common.cuh", "include/seqcdc.h"),
+                   "paper_2505_21194_gb300/csrc/common.cuh"),
 }
 
 
