@@ -106,7 +106,7 @@ typedef struct {
 #define SEQCDC_ALGO_MAP  1u
 #define SEQCDC_ALGO_WALK 2u
 #define SEQCDC_WALK_MIN_FILES 256u
-#define SEQCDC_WALK_MIN_PIECES 256u
+#define SEQCDC_WALK_MIN_PIECES 1024u
 typedef struct {
     uint32_t segment_bytes;
     uint32_t block_threads;
@@ -279,7 +279,9 @@ uint64_t seqcdc_set_wait_limit_ns(uint64_t ns);
  * dominant kernel (the segment kernel of the segment map, the piece-walk
  * kernel of the chain walk) of every later seqcdc_chunk / seqcdc_chunk_batch
  * call made from this host thread, so that its device time can be read with
- * cudaEventElapsedTime.  Pass NULL, NULL to stop.  The events are owned by the
+ * cudaEventElapsedTime.  A call made while its stream is being captured into
+ * a CUDA graph records them as external event nodes, which fire on every
+ * launch of the graph.  Pass NULL, NULL to stop.  The events are owned by the
  * caller.  Always returns SEQCDC_OK.
  */
 int seqcdc_profile_events(void *ev_begin, void *ev_end);

@@ -160,4 +160,16 @@ __device__ __forceinline__ uint32_t run_ends(uint32_t pt, uint32_t T, uint32_t R
   return ew;
 }
 
+// Record a measurement event on `st`.  While the stream is being captured
+// into a CUDA graph the record becomes an event node that fires on every
+// launch of the graph (an external record), so that the events bracket the
+// kernel in each replay.
+inline void record_event(cudaEvent_t ev, cudaStream_t st) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusActive)
+    cudaEventRecordWithFlags(ev, st, cudaEventRecordExternal);
+  else
+    cudaEventRecord(ev, st);
+}
+
 }  // namespace

@@ -1605,9 +1605,9 @@ int run(const seqcdc_params_t *p, const uint8_t *d_data, uint64_t total,
   if (sms <= 0) return SEQCDC_ECUDA;
   plan_tiles_kernel<<<(unsigned)l.nftiles, 256, 0, st>>>(g, w);
   plan_scan_kernel<<<(unsigned)l.nftiles, 256, 0, st>>>(g, w, l.nftiles, l.imax);
-  if (g_prof_begin) cudaEventRecord(g_prof_begin, st);
+  if (g_prof_begin) record_event(g_prof_begin, st);
   map_fn<<<(unsigned)l.imax, threads, smem, st>>>(g, dp, w);
-  if (g_prof_end) cudaEventRecord(g_prof_end, st);
+  if (g_prof_end) record_event(g_prof_end, st);
   // Warps per resolve block: up to kResolveWarps while their staging areas
   // stay within 96 KiB.
   const size_t rper = 2 * sizeof(uint32_t) * cand_cap(L);

@@ -1013,9 +1013,9 @@ int run(const seqcdc_params_t *p, const uint8_t *d_data, uint64_t total,
   const uint64_t want = (l.npmax + 3) / 4;
   const uint64_t most = 16u * (uint64_t)sms;
   const unsigned wgrid = (unsigned)(want < most ? want : most);
-  if (prof_begin) cudaEventRecord(static_cast<cudaEvent_t>(prof_begin), st);
+  if (prof_begin) record_event(static_cast<cudaEvent_t>(prof_begin), st);
   walk_kernel<<<wgrid, kWalkThreads, 0, st>>>(g, dp, w);
-  if (prof_end) cudaEventRecord(static_cast<cudaEvent_t>(prof_end), st);
+  if (prof_end) record_event(static_cast<cudaEvent_t>(prof_end), st);
   const uint64_t vb = (l.npmax + 255) / 256;
   const unsigned vgrid = (unsigned)(vb < 4096 ? vb : 4096);
   // Rounds of verify + parallel run repair (a persistent grid of warps takes

@@ -22,6 +22,7 @@ orders streams.
 """
 from __future__ import annotations
 
+import collections
 from typing import Iterable, Iterator, List, Optional, Tuple
 
 import numpy as np
@@ -184,15 +185,17 @@ class HostStreamPipeline:
          device -> device, back to back, into an aligned work buffer (two in
          rotation), which ``seqcdc_chunk`` chunks; its cut list is copied to
          pinned host memory.
-    So the copy of block i+1 runs while block i is chunked.  ``feed`` returns
-    the proven cuts of the block before (absolute offsets); ``finish`` returns
+    The copies in run up to ``slots - 1`` blocks ahead of the chunking, so
+    the copy engine stays busy while the host does its bookkeeping.  ``feed``
+    returns the cuts proven so far that were not returned before (absolute
+    offsets; blocks still in flight are not yet chunked); ``finish`` returns
     the rest, ending at the stream end.  Blocks larger than ``block_bytes`` are
     taken in parts.  Pinned host blocks (torch tensors) are copied
     asynchronously; numpy or pageable blocks go through a pinned staging copy
     on the host first.
     """
 
-    def __init__(self, p, tuning=None, device="cuda", block_bytes: int = 256 << 20,
+    def __init__(self, p, tuning=None, device="cuda", block_bytes: int = 128 << 20,
                  slots: int = 3):
         import torch
         self.torch = torch
@@ -224,6 +227,8 @@ class HostStreamPipeline:
         """Start a new stream (the carried tail is dropped)."""
         self.base = 0          # absolute offset of work[cur][0]
         self.nblk = 0          # blocks (parts) chunked so far
+        self.nin = 0           # parts copied in so far
+        self.inflight = collections.deque()  # parts copied in, not yet chunked
         self.pending = None    # (work index, bytes in the work buffer, event)
         self.carry = (None, 0, 0)  # (work index, offset of the tail, its length)
 
@@ -231,7 +236,8 @@ class HostStreamPipeline:
         """Copy one part (<= block_bytes) host -> device staging; returns
         (staging index, length, event)."""
         torch = self.torch
-        k = self.nblk % len(self.stage)
+        k = self.nin % len(self.stage)
+        self.nin += 1
         n = int(blk.numel() if hasattr(blk, "numel") else blk.size)
         if self.stage_free[k] is not None:
             self.copy_in.wait_event(self.stage_free[k])
@@ -305,17 +311,28 @@ class HostStreamPipeline:
         outs = []
         n = int(blk.numel() if hasattr(blk, "numel") else np.asarray(blk).size)
         for a in range(0, n, self.B):
-            part = blk[a:min(n, a + self.B)]
-            k, m, loaded = self._part(part)           # copy in: overlaps the chunking before
-            outs.append(self._collect(final=False))   # wait for the previous part
-            self._chunk_part(k, m, loaded)
+            self.inflight.append(self._part(blk[a:min(n, a + self.B)]))
+            # chunk the oldest part once the copies ahead fill the free slots
+            while len(self.inflight) >= len(self.stage):
+                outs.append(self._advance())
         return np.concatenate(outs) if outs else np.empty(0, np.int64)
+
+    def _advance(self) -> np.ndarray:
+        """Chunk the oldest part copied in: wait for the part before it,
+        then enqueue it; returns the cuts the wait proved."""
+        k, m, loaded = self.inflight.popleft()
+        out = self._collect(final=False)
+        self._chunk_part(k, m, loaded)
+        return out
 
     def finish(self) -> np.ndarray:
         """The remaining cuts, the last one at the stream end; then reset."""
-        out = self._collect(final=True)   # the last part fed is always pending
+        outs = []
+        while self.inflight:
+            outs.append(self._advance())
+        outs.append(self._collect(final=True))   # the last part is pending
         self.reset()
-        return out
+        return np.concatenate(outs)
 
     def run(self, blocks) -> np.ndarray:
         """Cut list of the whole stream given as an iterable of blocks."""
@@ -325,7 +342,7 @@ class HostStreamPipeline:
 
 
 def chunk_stream_host(blocks: Iterable[np.ndarray], p, tuning=None,
-                      device="cuda", block_bytes: int = 256 << 20) -> Iterator[np.ndarray]:
+                      device="cuda", block_bytes: int = 128 << 20) -> Iterator[np.ndarray]:
     """Chunk one stream given as host blocks (any sizes); yields the absolute
     cut offsets block by block (their concatenation is the stream's cut
     list), through a HostStreamPipeline (copies overlapped with chunking)."""

@@ -59,7 +59,7 @@ ALGO_AUTO = 0
 ALGO_MAP = 1
 ALGO_WALK = 2
 WALK_MIN_FILES = 256   # SEQCDC_WALK_MIN_FILES: AUTO takes the chain walk from here
-WALK_MIN_PIECES = 256  # SEQCDC_WALK_MIN_PIECES: ... or from this many full pieces
+WALK_MIN_PIECES = 1024  # SEQCDC_WALK_MIN_PIECES: ... or from this many full pieces
 
 
 class Tuning(ctypes.Structure):

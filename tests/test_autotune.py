@@ -36,7 +36,8 @@ def test_default_candidate_follows_auto_rule(seqcdc_lib):
     assert A.default_candidate(p, s.WALK_MIN_FILES - 1) == (65536, 256, s.ALGO_MAP, 0)
     assert A.default_candidate(p, 1000, batch=False)[2] == s.ALGO_MAP
     # a stream of at least SEQCDC_WALK_MIN_PIECES full pieces takes the walk
-    assert A.default_candidate(p, 1, False, 1 << 30)[2] == s.ALGO_WALK
+    assert A.default_candidate(p, 1, False, 2 << 30)[2] == s.ALGO_WALK
+    assert A.default_candidate(p, 1, False, 256 << 20)[2] == s.ALGO_MAP
 
 
 def test_workload_key_separates_shapes(seqcdc_lib):
