@@ -387,6 +387,7 @@ __device__ __forceinline__ Win load_win(const WGeom &g, uint64_t base) {
 // many chains in flight per SM the loads' latency is hidden (an L2 prefetch
 // of the next chunk's likely window, 1-3 KiB, measured no faster and moved
 // three to four times the bytes).
+template <uint32_t MODE, bool R5>
 __device__ uint64_t chunk_end_warp(const WGeom &g, const DevParams &p, uint64_t c,
                                    uint64_t fend, uint32_t &wins, bool &ok) {
   const int lane = threadIdx.x & 31;
@@ -424,11 +425,11 @@ __device__ uint64_t chunk_end_warp(const WGeom &g, const DevParams &p, uint64_t 
       uint32_t prev = __shfl_up_sync(kFull, v.w >> 24, 1);
       if (lane == 0) prev = carry_b;
       uint32_t Tw, Ow;
-      classify16(v, prev, p.mode, Tw, Ow);
+      classify16(v, prev, MODE, Tw, Ow);
       uint32_t pt = __shfl_up_sync(kFull, Tw, 1);
       if (lane == 0) pt = carry_t;
       // The run ends of this lane's 16 positions look back into the 16 before.
-      const uint32_t Ew = run_ends(0u, (Tw << 16) | (pt & 0xffffu), p.R) >> 16;
+      const uint32_t Ew = run_ends(0u, (Tw << 16) | (pt & 0xffffu), R5 ? 5u : p.R) >> 16;
       carry_b = __shfl_sync(kFull, v.w >> 24, 31);
       carry_t = __shfl_sync(kFull, Tw, 31);
       const uint32_t span = lim - hb;
@@ -530,6 +531,7 @@ __device__ __forceinline__ uint32_t seek(const uint32_t *sp, uint32_t ns, uint32
 // With `done` set, the piece's spec walk may still be running (another warp):
 // its cuts are compared once done[k] is set, the cuts walked before that
 // first, in order.  Returns whether the walk met the spec walk.
+template <uint32_t MODE, bool R5>
 __device__ bool junction_walk(const WGeom &g, const DevParams &p, const WPtrs &w,
                               uint32_t k, const Piece &pc, uint32_t x, const uint32_t *done,
                               uint32_t &chunks, uint32_t &wins, bool &ok) {
@@ -589,7 +591,7 @@ __device__ bool junction_walk(const WGeom &g, const DevParams &p, const WPtrs &w
         break;
       }
       if (have) checked = n;
-      rel = (uint32_t)(chunk_end_warp(g, p, pc.ps + rel, pc.fend, wins, ok) - pc.ps);
+      rel = (uint32_t)(chunk_end_warp<MODE, R5>(g, p, pc.ps + rel, pc.fend, wins, ok) - pc.ps);
       ++chunks;
     }
     if (!fin && jm == kUnmerged) ok = false;
@@ -611,6 +613,7 @@ __device__ bool junction_walk(const WGeom &g, const DevParams &p, const WPtrs &w
 // the exit is where the true chain enters the next piece whenever this
 // piece's own junction met its spec walk.
 // ---------------------------------------------------------------------------
+template <uint32_t MODE, bool R5>
 __global__ void __launch_bounds__(kWalkThreads, kWalkMinBlocks)
 walk_kernel(WGeom g, DevParams p, WPtrs w) {
   const int lane = threadIdx.x & 31;
@@ -629,7 +632,7 @@ walk_kernel(WGeom g, DevParams p, WPtrs w) {
     uint64_t c = pc.ps;
     uint32_t n = 0;
     do {
-      c = chunk_end_warp(g, p, c, pc.fend, wins, ok);
+      c = chunk_end_warp<MODE, R5>(g, p, c, pc.fend, wins, ok);
       if (n < pc.cap) {
         if (lane == 0) out[n] = (uint32_t)(c - pc.ps);
         ++n;
@@ -654,7 +657,7 @@ walk_kernel(WGeom g, DevParams p, WPtrs w) {
     chunks += n;
     if (k + 1 < w.piece_base[pc.file + 1]) {
       const Piece pn = piece_of(g, w, p, k + 1);
-      const bool met = junction_walk(g, p, w, k + 1, pn, (uint32_t)(c - pn.ps), w.sdone,
+      const bool met = junction_walk<MODE, R5>(g, p, w, k + 1, pn, (uint32_t)(c - pn.ps), w.sdone,
                                      jchunks, wins, ok);
       ++walks;
       unmerged += met ? 0u : 1u;
@@ -724,6 +727,7 @@ __global__ void wverify_kernel(WGeom g, DevParams p, WPtrs w, uint32_t round) {
 // it are claimed by the verify, so each piece has at most one writer per
 // round, and the piece a run's repair starts from is written by nobody.
 // What a round leaves inconsistent the next round's verify lists again.
+template <uint32_t MODE, bool R5>
 __global__ void __launch_bounds__(kWalkThreads)
 wrun_repair_kernel(WGeom g, DevParams p, WPtrs w, uint32_t round) {
   const int lane = threadIdx.x & 31;
@@ -752,7 +756,7 @@ wrun_repair_kernel(WGeom g, DevParams p, WPtrs w, uint32_t round) {
         if (lane == 0) old = atomicMax(&w.claim[k], tag);
         if (__shfl_sync(kFull, old, 0) >= tag) break;  // another run's piece
       }
-      junction_walk(g, p, w, k, pc, x, nullptr, chunks, wins, ok);
+      junction_walk<MODE, R5>(g, p, w, k, pc, x, nullptr, chunks, wins, ok);
       ++redone;
     }
   }
@@ -766,6 +770,7 @@ wrun_repair_kernel(WGeom g, DevParams p, WPtrs w, uint32_t round) {
 // piece on, every piece whose junction input differs from its predecessor's
 // exit walks again from that exit.  Pieces are taken in order, so each input
 // is the true exit of the piece before.
+template <uint32_t MODE, bool R5>
 __global__ void __launch_bounds__(kWalkThreads)
 wrepair_kernel(WGeom g, DevParams p, WPtrs w) {
   const int lane = threadIdx.x & 31;
@@ -781,7 +786,7 @@ wrepair_kernel(WGeom g, DevParams p, WPtrs w) {
       const Piece pc = piece_of(g, w, p, k);
       const uint32_t x = exit_of(w, k - 1u, pc.lb - g.fullcap) - g.P;
       if (x == w.jin[k]) continue;
-      junction_walk(g, p, w, k, pc, x, nullptr, chunks, wins, ok);
+      junction_walk<MODE, R5>(g, p, w, k, pc, x, nullptr, chunks, wins, ok);
       ++redone;
     }
   }
@@ -1014,7 +1019,16 @@ int run(const seqcdc_params_t *p, const uint8_t *d_data, uint64_t total,
   const uint64_t most = 16u * (uint64_t)sms;
   const unsigned wgrid = (unsigned)(want < most ? want : most);
   if (prof_begin) record_event(static_cast<cudaEvent_t>(prof_begin), st);
-  walk_kernel<<<wgrid, kWalkThreads, 0, st>>>(g, dp, w);
+  const int variant = (dp.mode ? 2 : 0) + (dp.R == 5u ? 1 : 0);
+  void (*const walk_fns[4])(WGeom, DevParams, WPtrs) = {
+      walk_kernel<0, false>, walk_kernel<0, true>, walk_kernel<1, false>, walk_kernel<1, true>};
+  void (*const run_fns[4])(WGeom, DevParams, WPtrs, uint32_t) = {
+      wrun_repair_kernel<0, false>, wrun_repair_kernel<0, true>, wrun_repair_kernel<1, false>,
+      wrun_repair_kernel<1, true>};
+  void (*const rep_fns[4])(WGeom, DevParams, WPtrs) = {
+      wrepair_kernel<0, false>, wrepair_kernel<0, true>, wrepair_kernel<1, false>,
+      wrepair_kernel<1, true>};
+  walk_fns[variant]<<<wgrid, kWalkThreads, 0, st>>>(g, dp, w);
   if (prof_end) record_event(static_cast<cudaEvent_t>(prof_end), st);
   const uint64_t vb = (l.npmax + 255) / 256;
   const unsigned vgrid = (unsigned)(vb < 4096 ? vb : 4096);
@@ -1026,12 +1040,12 @@ int run(const seqcdc_params_t *p, const uint8_t *d_data, uint64_t total,
   const unsigned rrgrid = (unsigned)(rwant < rmost ? (rwant ? rwant : 1) : rmost);
   for (uint32_t round = 0; round < kWalkRepairRounds; ++round) {
     wverify_kernel<<<vgrid, 256, 0, st>>>(g, dp, w, round);
-    wrun_repair_kernel<<<rrgrid, kWalkThreads, 0, st>>>(g, dp, w, round);
+    run_fns[variant]<<<rrgrid, kWalkThreads, 0, st>>>(g, dp, w, round);
   }
   wverify_kernel<<<vgrid, 256, 0, st>>>(g, dp, w, kWalkRepairRounds);
   const uint64_t rb = (nfiles + 3) / 4;
   const uint64_t rcap = 4u * (uint64_t)sms;
-  wrepair_kernel<<<(unsigned)(rb < rcap ? (rb ? rb : 1) : rcap), kWalkThreads, 0, st>>>(g, dp, w);
+  rep_fns[variant]<<<(unsigned)(rb < rcap ? (rb ? rb : 1) : rcap), kWalkThreads, 0, st>>>(g, dp, w);
   wcount_kernel<<<(unsigned)l.nctiles, kPieceTile, 0, st>>>(g, dp, w);
   wemit_kernel<<<(unsigned)l.nctiles, kEmitThreads, 0, st>>>(g, dp, w, d_cuts, cap,
                                                              d_cut_offsets, d_count);
