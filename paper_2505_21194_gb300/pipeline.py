@@ -152,10 +152,12 @@ class HostBatchPipeline:
         bad = [int(x) for x in self.h_status[:len(ranges)].numpy() if x != seqcdc.SEQCDC_OK]
         if bad:
             raise seqcdc.SeqCDCError(bad[0], "chunk_batch_host (device)")
+        # One copy out of the pinned buffers: the concatenation reads them
+        # directly (the buffers are reused by the next call, the result is not).
         parts, co_parts, base = [], [np.zeros(1, np.int64)], 0
         for k, (a, b) in enumerate(ranges):
             co = self.h_co[k][:b - a + 1].numpy()
-            parts.append(self.h_cuts[k][:int(co[-1])].numpy().copy())
+            parts.append(self.h_cuts[k][:int(co[-1])].numpy())
             co_parts.append(co[1:] + base)
             base += int(co[-1])
         return np.concatenate(parts), np.concatenate(co_parts)

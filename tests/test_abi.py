@@ -189,3 +189,50 @@ def test_walk_workspace_is_monotone(seqcdc_lib):
             t2 = t1 + int(rng.integers(0, 1 << 30))
             f2 = f1 + int(rng.integers(0, 5000))
             assert s.seqcdc_workspace_size(p, t1, f1, t) <= s.seqcdc_workspace_size(p, t2, f2, t)
+
+
+@pytest.mark.gpu
+def test_chunk_batch_in_a_cuda_graph_with_profile_events(gpu):
+    """The batched call captured into a CUDA graph (as bench.py times it):
+    replays give the direct call's cut list, and the measurement events,
+    recorded as external event nodes during capture, bracket the dominant
+    kernel on every replay."""
+    import torch
+    from paper_2505_21194_gb300 import workloads as W
+    s = gpu
+    data, offs = W.file_batch(300, seed=4)
+    d = torch.from_numpy(data).cuda()
+    o = torch.from_numpy(offs.astype(np.int64)).cuda()
+    p = s.seqcdc_params(8, 0)
+    ref = s.chunk_batch(d, o, p)
+    nf, total = o.numel() - 1, d.numel()
+    cap = total // p.min_size + nf
+    cuts = torch.full((cap,), -1, dtype=torch.int64, device="cuda")
+    co = torch.empty(nf + 1, dtype=torch.int64, device="cuda")
+    ws_bytes = s.seqcdc_workspace_size(p, total, nf)
+    ws = torch.empty(ws_bytes, dtype=torch.uint8, device="cuda")
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    for e in evs:
+        e.record()
+    gs = torch.cuda.Stream()
+    gs.wait_stream(torch.cuda.current_stream())
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(gs):
+        s.seqcdc_chunk_batch(p, d, total, o, nf, cuts, cap, co, ws, ws_bytes, None, gs)
+        gs.synchronize()
+        with torch.cuda.graph(graph, stream=gs):
+            for i in range(2):
+                s.seqcdc_profile_events(evs[2 * i], evs[2 * i + 1])
+                s.seqcdc_chunk_batch(p, d, total, o, nf, cuts, cap, co, ws, ws_bytes, None, gs)
+        s.seqcdc_profile_events(None, None)
+    torch.cuda.current_stream().wait_stream(gs)
+    for _ in range(2):
+        cuts.fill_(-1)
+        graph.replay()
+        torch.cuda.synchronize()
+        assert s.seqcdc_status(ws) == s.SEQCDC_OK
+        k = int(co[-1].item())
+        assert np.array_equal(co.cpu().numpy(), ref.cut_offsets.cpu().numpy())
+        assert np.array_equal(cuts[:k].cpu().numpy(), ref.cuts.cpu().numpy())
+        for i in range(2):
+            assert evs[2 * i].elapsed_time(evs[2 * i + 1]) > 0.0
