@@ -8,14 +8,15 @@ increasing mode.  Inputs are generated on the host from a fixed seed, copied
 to HBM once, and are far larger than L2 (no flush needed between steps).
 
 Printed: a `detail:` line with the verbose results, then the one JSON line.
-The JSON line carries the metric, the device-resident throughput (`value`,
-the path the autotuner picks: the chain walk for this batch), the end-to-end
-throughput through host buffers (`e2e`), the roofline of the dominant kernel
-(with the path and its sizes), clocks, the CPU oracle as a reported baseline,
-and flat scalar fields for the rest: the CUDA-graph step, the plain
-one-launch-per-file loop and the other path on the same batch; the single
-streams (16 MiB random, the 1 GiB backup-like stream, the 64 GiB adversarial
-stream) with their path and kernel roofline fraction; p50/p99 latency and
+The JSON line carries the metric, the device-resident throughput (`value`:
+the K timed steps as one CUDA graph, on the path the autotuner picks: the
+chain walk for this batch), the end-to-end throughput through host buffers
+(`e2e`), the roofline of the dominant kernel (with the path and its sizes),
+clocks, the CPU oracle as a reported baseline, and flat scalar fields for
+the rest: the same steps launched directly, the plain one-launch-per-file
+loop and the other path on the same batch; the single streams (16 MiB
+random, the 1 GiB backup-like stream, the 64 GiB adversarial stream) as a
+graph and as direct calls, with their path and kernel roofline fraction; p50/p99 latency and
 sustained GB/s of the continuous-batching server under open-loop Poisson
 arrivals at 25, 50, 100 and 200 GB/s offered load; the deduplication savings
 of the backup-like stream; SHA-256 fingerprinting; the mean chunk sizes of
@@ -659,6 +660,7 @@ def run_gpu(args):
         for name, r in ss.items():
             key = name.split("_")[0]
             line["%s_GBs" % key] = r["GBs"]
+            line["%s_direct_GBs" % key] = r["direct_GBs"]
             line["%s_path" % key] = r["path"]
             line["%s_kernel_frac" % key] = r["frac"]
             if "host_stream" in r:
@@ -745,8 +747,8 @@ def time_stream(dev, d, p, peak, reps=5, flush=None, tuning=None):
     stream = torch.cuda.current_stream(dev)
     algo = seqcdc.seqcdc_algorithm(p, n, 1, False, ws_bytes, tuning)
 
-    def call():
-        seqcdc.seqcdc_chunk(p, d, n, cuts, cap, cnt, ws, ws_bytes, tuning, stream)
+    def call(st=None):
+        seqcdc.seqcdc_chunk(p, d, n, cuts, cap, cnt, ws, ws_bytes, tuning, st or stream)
 
     for _ in range(3):
         call()
@@ -755,20 +757,43 @@ def time_stream(dev, d, p, peak, reps=5, flush=None, tuning=None):
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
     for e in ev:
         e.record(stream)
-    steps, kern = [], []
-    for _ in range(reps):
-        if flush is not None:
-            flush.add_(1)
-        ev[0].record(stream)
-        seqcdc.seqcdc_profile_events(ev[2], ev[3])
-        call()
+    # The call captured once in a CUDA graph (its kernels launched as one
+    # graph, the dominant kernel bracketed by events on every replay).
+    gs = torch.cuda.Stream(dev)
+    gs.wait_stream(stream)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(gs):
+        call(gs)
+        gs.synchronize()
+        with torch.cuda.graph(graph, stream=gs):
+            seqcdc.seqcdc_profile_events(ev[2], ev[3])
+            call(gs)
         seqcdc.seqcdc_profile_events(None, None)
-        ev[1].record(stream)
-        torch.cuda.synchronize(dev)
-        steps.append(ev[0].elapsed_time(ev[1]))
-        kern.append(ev[2].elapsed_time(ev[3]))
+    stream.wait_stream(gs)
+
+    def timed(use_graph):
+        steps, kern = [], []
+        for _ in range(reps):
+            if flush is not None:
+                flush.add_(1)
+            ev[0].record(stream)
+            if use_graph:
+                graph.replay()
+            else:
+                seqcdc.seqcdc_profile_events(ev[2], ev[3])
+                call()
+                seqcdc.seqcdc_profile_events(None, None)
+            ev[1].record(stream)
+            torch.cuda.synchronize(dev)
+            steps.append(ev[0].elapsed_time(ev[1]))
+            kern.append(ev[2].elapsed_time(ev[3]))
+        return steps, kern
+
+    dsteps, _ = timed(False)
+    steps, kern = timed(True)
     if seqcdc.seqcdc_status(ws, stream) != 0:
         raise RuntimeError("device status in the timed calls")
+    del graph
     k = int(cnt.item())
     ms, kms = statistics.median(steps), statistics.median(kern)
     walk = algo == seqcdc.ALGO_WALK
@@ -778,7 +803,10 @@ def time_stream(dev, d, p, peak, reps=5, flush=None, tuning=None):
     else:
         alg = n + 8 * k
     del ws, cuts
+    dms = statistics.median(dsteps)
     return {"GBs": round(n / (ms * 1e-3) / 1e9, 2), "ms": round(ms, 4),
+            "launch": "CUDA graph of one call",
+            "direct_GBs": round(n / (dms * 1e-3) / 1e9, 2), "direct_ms": round(dms, 4),
             "path": "chain walk" if walk else "segment map",
             "kernel": "walk_kernel" if walk else "map_kernel",
             "kernel_ms": round(kms, 4), "cuts": k, "bytes": n,
