@@ -429,7 +429,7 @@ def run_gpu(args):
     # The host-data entry point: file-aligned pieces with each piece's copy in
     # overlapped with the previous piece's chunking and copy out.
     from paper_2505_21194_gb300.pipeline import HostBatchPipeline, split_files
-    pieces = 16
+    pieces = 4
     pipe = HostBatchPipeline(p, tuning, str(dev))
     pipe.run(h_data, offs_np, pieces)
     pipe_s = []

@@ -100,7 +100,7 @@ class HostBatchPipeline:
         for s in self.pool:
             s.free = None
 
-    def run(self, h_data, h_offsets, pieces: int = 16):
+    def run(self, h_data, h_offsets, pieces: int = 4):
         """(cuts int64, cut_offsets int64) on the host, equal to
         ``chunk_batch`` of the same batch on the device."""
         torch, p, tuning = self.torch, self.p, self.tuning
@@ -147,23 +147,28 @@ class HostBatchPipeline:
                 s.free = torch.cuda.Event()
                 s.free.record(self.copy_out)
             done.append(s.free)
-        for e in done:
-            e.synchronize()
-        bad = [int(x) for x in self.h_status[:len(ranges)].numpy() if x != seqcdc.SEQCDC_OK]
-        if bad:
-            raise seqcdc.SeqCDCError(bad[0], "chunk_batch_host (device)")
-        # One copy out of the pinned buffers: the concatenation reads them
-        # directly (the buffers are reused by the next call, the result is not).
-        parts, co_parts, base = [], [np.zeros(1, np.int64)], 0
+        # Collect in order while the later pieces are still on the GPU: each
+        # piece's cuts go into one output array as soon as its copy back is
+        # over, so only the last piece's host copy is not overlapped.
+        out_cuts = np.empty(max(sum(caps), 1), dtype=np.int64)
+        out_co = np.zeros(nfiles + 1, dtype=np.int64)
+        base = 0
         for k, (a, b) in enumerate(ranges):
+            done[k].synchronize()
+            st = int(self.h_status[k])
+            if st != seqcdc.SEQCDC_OK:
+                for e in done[k + 1:]:   # leave no piece in flight in the slots
+                    e.synchronize()
+                raise seqcdc.SeqCDCError(st, "chunk_batch_host (device)")
             co = self.h_co[k][:b - a + 1].numpy()
-            parts.append(self.h_cuts[k][:int(co[-1])].numpy())
-            co_parts.append(co[1:] + base)
-            base += int(co[-1])
-        return np.concatenate(parts), np.concatenate(co_parts)
+            cnt = int(co[-1])
+            out_cuts[base:base + cnt] = self.h_cuts[k][:cnt].numpy()
+            out_co[a + 1:b + 1] = co[1:] + base
+            base += cnt
+        return out_cuts[:base], out_co
 
 
-def chunk_batch_host(h_data, h_offsets, p, pieces: int = 16, slots: int = 3,
+def chunk_batch_host(h_data, h_offsets, p, pieces: int = 4, slots: int = 3,
                      tuning=None, device="cuda"):
     """One-off use of ``HostBatchPipeline``: chunk a CSR batch held in pinned
     host memory; returns host (cuts int64, cut_offsets int64)."""
