@@ -444,6 +444,27 @@ def run_gpu(args):
     pr = split_files(offs_np.astype(np.int64), pieces)
     d2h_pipe = sum((b - a + 1) * 8 + (int(offs_np[b] - offs_np[a]) // p.min_size + (b - a)) * 8 + 4
                    for a, b in pr)
+    # The in-place entry point: the batch stays in pinned host memory and the
+    # kernels read it there over the host link (the walk loads only the half
+    # windows its scan reaches); the offsets go in, the cut lists come back.
+    from paper_2505_21194_gb300.pipeline import HostInPlace
+    # (library defaults: the tuning above is the device-resident batch's)
+    hip = HostInPlace(p, None, str(dev))
+    hip.run(h_data, offs_np)
+    inplace_s = []
+    for _ in range(e2e_steps):
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        hc, hco = hip.run(h_data, offs_np)
+        inplace_s.append(time.perf_counter() - t0)
+    assert int(hco[-1]) == ncuts and hc.size == ncuts
+    ip_stats = seqcdc.seqcdc_stats(hip.ws, walk=seqcdc.seqcdc_algorithm(
+        p, total, nfiles, True, hip.ws_bytes, None) == seqcdc.ALGO_WALK)
+    ip_path = "chain walk" if "windows" in ip_stats else "segment map"
+    # Bytes the kernels read from host memory: the 32-byte sectors the walk
+    # loaded, or every byte on the segment map.
+    ip_host_bytes = (ip_stats["windows"] * 32 if ip_path == "chain walk" else total)
+    inplace_gbs = total * world / statistics.median(inplace_s) / 1e9
     h2d_gbs = h2d_copy_gbs()
     # d_data now holds the batch again (the copies above wrote the same bytes)
 
@@ -620,11 +641,18 @@ def run_gpu(args):
         "data": "synthetic",
         "config": workload_config(total, nfiles),
         "parallelism": "1 GPU per rank, independent batches (weak scaling)",
-        "e2e": {"value": round(e2e_gbs, 2), "unit": "GB/s",
-                "h2d_bytes_per_step": int(total + (nfiles + 1) * 8),
-                "d2h_bytes_per_step": int(d2h_pipe),
-                "api": "pipeline.HostBatchPipeline.run (%d file-aligned pieces, copies "
-                       "overlapped with chunking)" % pieces,
+        "e2e": {"value": round(inplace_gbs, 2), "unit": "GB/s",
+                "h2d_bytes_per_step": int(ip_host_bytes + (nfiles + 1) * 8),
+                "d2h_bytes_per_step": int((nfiles + 1) * 8 + ncuts * 8 + 4),
+                "api": "pipeline.HostInPlace.run (batch in pinned host memory, read in "
+                       "place by the kernels; %s)" % ip_path,
+                "input_bytes_on_host": int(total),
+                "h2d_bytes": "bytes the kernels read from host memory (32-byte sectors, "
+                             "walk counter) + the offsets",
+                "copy_pipeline_GBs": round(e2e_gbs, 2),
+                "copy_pipeline_api": "pipeline.HostBatchPipeline.run (%d file-aligned pieces, "
+                                     "copies overlapped with chunking)" % pieces,
+                "copy_pipeline_h2d_bytes_per_step": int(total + (nfiles + 1) * 8),
                 "serial_GBs": round(total * world / e2e_serial_s / 1e9, 2),
                 "h2d_copy_GBs": round(h2d_before, 1),
                 "h2d_copy_GBs_after": round(h2d_gbs, 1),
@@ -663,6 +691,9 @@ def run_gpu(args):
             line["%s_direct_GBs" % key] = r["direct_GBs"]
             line["%s_path" % key] = r["path"]
             line["%s_kernel_frac" % key] = r["frac"]
+            if "host_in_place" in r:
+                line["%s_host_in_place_GBs" % key] = r["host_in_place"]["GBs"]
+                line["%s_host_in_place_same_cuts" % key] = r["host_in_place"]["same_cuts"]
             if "host_stream" in r:
                 line["%s_host_stream_GBs" % key] = r["host_stream"]["GBs"]
                 line["%s_host_h2d_copy_GBs" % key] = r["host_stream"]["h2d_copy_GBs"]
@@ -855,7 +886,21 @@ def single_streams(dev, backup, peak, with_cfg5=True):
         "h2d_copy_GBs": round(n / statistics.median(tc) / 1e9, 2),
         "same_cuts": same, "blocks": len(blocks),
         "api": "pipeline.HostStreamPipeline.run, 128 MiB pinned blocks, median of 3"}
-    del d, h, pipe
+    # The same pinned stream read in place by the kernels (no copy of it).
+    from paper_2505_21194_gb300.pipeline import HostInPlace
+    hip = HostInPlace(seqcdc.seqcdc_params(8, 0), device=str(dev))
+    hip.run_stream(h)
+    ti = []
+    for _ in range(3):
+        torch.cuda.synchronize(dev)
+        t = time.perf_counter()
+        got_ip = hip.run_stream(h)
+        ti.append(time.perf_counter() - t)
+    out["cfg2_1GiB_backup"]["host_in_place"] = {
+        "GBs": round(n / statistics.median(ti) / 1e9, 2),
+        "same_cuts": bool(np.array_equal(got_ip, ref)),
+        "api": "pipeline.HostInPlace.run_stream, median of 3"}
+    del d, h, pipe, hip
     if with_cfg5:
         block, nblocks = 16 << 20, 4096
         d = torch.empty(block * nblocks, dtype=torch.uint8, device=dev)

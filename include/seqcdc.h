@@ -100,7 +100,9 @@ typedef struct {
  *   piece_bytes    chain walk: bytes of a piece, the unit one warp walks
  *                  (rounded up to a multiple of 64 KiB; at least
  *                  4 x max_size, at most 64 MiB; default 768 KiB, or
- *                  384 x min_size when min_size exceeds 4 KiB).
+ *                  384 x min_size when min_size exceeds 4 KiB, and twice
+ *                  that for input read in place from host memory of at
+ *                  least 4,096 such doubled pieces).
  */
 #define SEQCDC_ALGO_AUTO 0u
 #define SEQCDC_ALGO_MAP  1u
@@ -148,15 +150,27 @@ size_t seqcdc_workspace_size(const seqcdc_params_t *p, uint64_t total_bytes,
 
 /*
  * The path (SEQCDC_ALGO_MAP or SEQCDC_ALGO_WALK) that a chunking call with
- * these arguments takes: seqcdc_chunk() for batch == 0 (nfiles = 1),
- * seqcdc_chunk_batch() otherwise, with a workspace of ws_bytes bytes.
- * Returns 0 for an invalid parameter set.  Makes no CUDA call.
+ * these arguments takes on input in device memory: seqcdc_chunk() for
+ * batch == 0 (nfiles = 1), seqcdc_chunk_batch() otherwise, with a workspace
+ * of ws_bytes bytes (input read in place from host memory takes the chain
+ * walk under AUTO whenever the workspace holds it).  Returns 0 for an invalid
+ * parameter set.  Makes no CUDA call.
  */
 int seqcdc_algorithm(const seqcdc_params_t *p, uint64_t total_bytes, uint64_t nfiles,
                      int batch, size_t ws_bytes, const seqcdc_tuning_t *tuning);
 
 /*
  * Chunk one byte stream d_in[0..n).
+ *   d_in     device memory, or pinned host memory that is mapped into the
+ *            device's address space (cudaHostAlloc / cudaHostRegister; on a
+ *            GB300 node every pinned allocation is), which the kernels then
+ *            read in place over the host link: AUTO takes the chain walk for
+ *            such input when the workspace allows it, and the walk loads
+ *            only the 16-byte words of a window from its scan region's start
+ *            on, when the scan reaches them, so only a fraction of the bytes
+ *            cross (Sec. III.B-C skip the rest).
+ *            Pageable host memory gives SEQCDC_EINVAL (after the size
+ *            checks, before any launch).  16-byte aligned.
  *   d_cuts   out: up to `cap` uint64 chunk end offsets.
  *   cap      capacity of d_cuts in entries; must be >= n / min_size + 1
  *            (always sufficient), else SEQCDC_ECAPACITY.
@@ -172,7 +186,9 @@ int seqcdc_chunk(const seqcdc_params_t *p, const uint8_t *d_in, uint64_t n,
                  void *stream);
 
 /*
- * Chunk a batch of files laid out back to back in d_data[0..total_bytes).
+ * Chunk a batch of files laid out back to back in d_data[0..total_bytes)
+ * (device memory or mapped pinned host memory, read in place, as d_in of
+ * seqcdc_chunk).
  *   d_offsets      nfiles+1 uint64 on the device: file f is
  *                  d_data[d_offsets[f] .. d_offsets[f+1]); d_offsets[0] == 0,
  *                  non-decreasing, d_offsets[nfiles] == total_bytes.
@@ -251,7 +267,8 @@ int seqcdc_status(const void *d_ws, void *stream);
  * found by the piece walks, [2] junction walks, [3] chunks the junction walks
  * took before meeting their piece's walk, [4] junction walks that left their
  * piece without meeting it, [5] pieces found inconsistent, [6] junction walks
- * redone by the repair pass, [7] 1 KiB windows the piece walks loaded.  The
+ * redone by the repair pass, [7] 1 KiB windows the piece walks loaded (32-byte
+ * sectors for input read in place from host memory).  The
  * counters describe which code paths ran; the output is exact either way.
  */
 int seqcdc_stats(const void *d_ws, void *stream, uint32_t *out, uint32_t n);

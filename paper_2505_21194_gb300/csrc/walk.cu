@@ -54,6 +54,10 @@ constexpr int kWalkThreads = 128;      // walk kernels: four warps per block
 #define SEQCDC_WALK_MIN_BLOCKS 16
 #endif
 constexpr int kWalkMinBlocks = SEQCDC_WALK_MIN_BLOCKS;
+// Lanes (16 bytes each) the walk over host-resident input loads at a time.
+#ifndef SEQCDC_HOST_GROW
+#define SEQCDC_HOST_GROW 8
+#endif
 constexpr int kFileTile = 1024;        // files per plan block
 constexpr int kPieceTile = 32;         // pieces per compaction tile (8 warps copy 4 each)
 constexpr int kEmitThreads = 256;
@@ -86,7 +90,8 @@ enum : uint32_t {
   WS_UNMERGED = 4,      // junction walks that left their piece without meeting
   WS_INCONSISTENT = 5,  // pieces whose junction input was wrong
   WS_REPAIRED = 6,      // junction walks redone by the repair pass
-  WS_WINDOWS = 7,       // 1 KiB windows the walks loaded
+  WS_WINDOWS = 7,       // 1 KiB windows the walks loaded (32-byte sectors when
+                        // the input is read in place from host memory)
 };
 
 struct WGeom {
@@ -388,8 +393,13 @@ __device__ __forceinline__ Win load_win(const WGeom &g, uint64_t base) {
 // of the next chunk's likely window, 1-3 KiB, measured no faster and moved
 // three to four times the bytes).
 template <uint32_t MODE, bool R5>
+__device__ uint64_t chunk_end_host(const WGeom &g, const DevParams &p, uint64_t c,
+                                   uint64_t fend, uint32_t &secs, bool &ok);
+
+template <uint32_t MODE, bool R5, bool LAZY>
 __device__ uint64_t chunk_end_warp(const WGeom &g, const DevParams &p, uint64_t c,
                                    uint64_t fend, uint32_t &wins, bool &ok) {
+  if (LAZY) return chunk_end_host<MODE, R5>(g, p, c, fend, wins, ok);
   const int lane = threadIdx.x & 31;
   const uint64_t rest = fend - c;
   const uint64_t lim_abs = c + (rest > p.mx ? p.mx : rest);
@@ -420,8 +430,8 @@ __device__ uint64_t chunk_end_warp(const WGeom &g, const DevParams &p, uint64_t 
     // A region that starts inside the second half skips classifying the
     // first (its first pair, (r, r + 1), then lies wholly in the second).
     for (int h = (r >= w0 + 512u) ? 1 : 0; h < 2; ++h) {
-      const uint4 v = h ? cur.b : cur.a;
       const uint32_t hb = w0 + 512u * h;  // half start (< lim)
+      const uint4 v = h ? cur.b : cur.a;
       uint32_t prev = __shfl_up_sync(kFull, v.w >> 24, 1);
       if (lane == 0) prev = carry_b;
       uint32_t Tw, Ow;
@@ -501,6 +511,131 @@ __device__ uint64_t chunk_end_warp(const WGeom &g, const DevParams &p, uint64_t 
   return cb + lim;
 }
 
+// End of the chunk that starts at absolute byte c, as chunk_end_warp, for
+// input read in place from host memory, where the bytes that cross the host
+// link bound the walk and instructions are cheap.  A scan step covers 512
+// bytes from the region's start (16 per lane), but loads them 128 bytes
+// (eight lanes) at a time and judges the region on what it has loaded: it
+// loads more only while no run end or skip has shown up, and never the bytes
+// before the region's start.  `secs` counts the 32-byte sectors read.
+template <uint32_t MODE, bool R5>
+__device__ uint64_t chunk_end_host(const WGeom &g, const DevParams &p, uint64_t c,
+                                   uint64_t fend, uint32_t &secs, bool &ok) {
+  constexpr uint32_t kGrow = SEQCDC_HOST_GROW;  // lanes loaded per step
+  const int lane = threadIdx.x & 31;
+  const uint64_t rest = fend - c;
+  const uint64_t lim_abs = c + (rest > p.mx ? p.mx : rest);
+  const uint64_t r_abs = c + (p.mn > p.R ? p.mn - p.R : 0u);
+  if (r_abs + 1 >= lim_abs) return lim_abs;
+  const uint64_t cb = r_abs & ~15ull;  // positions below are relative to cb
+  const uint32_t lim = (uint32_t)(lim_abs - cb);
+  uint32_t r = (uint32_t)(r_abs - cb);
+  const uint32_t skip = p.S < lim ? p.S : lim;
+  const int32_t lb = 16 * lane;
+  uint32_t opp = 0;                   // opposing pairs of the region before this step
+  uint32_t hb = r & ~15u;             // step start
+  uint32_t carry_b = 0, carry_t = 0;  // byte and T bits before the step (continued region)
+  // Each step ends the chunk, moves the region start SkipSize + 2 or more
+  // bytes on, or moves 512 bytes on; each pass of the inner loop loads eight
+  // more lanes or handles a skip.
+  for (uint32_t it = 0; it < p.mx + 8u; ++it) {
+    const uint32_t span = lim - hb;   // positions of the step below lim: [0, span)
+    uint4 v = make_uint4(0u, 0u, 0u, 0u);
+    uint32_t Tw = 0, Ow = 0;
+    uint32_t have = 0;                // lanes loaded
+    uint32_t upto = 0;                // lanes judged: [0, upto)
+    bool next = false;                // the region goes on into the next step
+    for (uint32_t pass = 0; pass < 64u + p.mx; ++pass) {
+      const int32_t rr = (int32_t)(r - hb);  // region start in the step (< 0: continued)
+      const uint32_t fl = rr > 0 ? (uint32_t)rr >> 4 : 0u;
+      if (upto <= fl) upto = min(32u, fl + kGrow);
+      const bool need = (uint32_t)lane >= fl && (uint32_t)lane < upto &&
+                        !((have >> lane) & 1u) && lb < (int32_t)span;
+      if (need) {
+        const uint64_t off = cb + hb + (uint32_t)lb;
+        v = off + 16u <= g.total ? __ldg(reinterpret_cast<const uint4 *>(g.data + off))
+                                 : load16(g.data, (int64_t)off, g.total);
+      }
+      const uint32_t nb = __ballot_sync(kFull, need);
+      if (nb) {
+        have |= nb;
+        secs += __popc((nb | (nb >> 1)) & 0x55555555u);
+        uint32_t prev = __shfl_up_sync(kFull, v.w >> 24, 1);
+        if (lane == 0) prev = carry_b;
+        classify16(v, prev, MODE, Tw, Ow);
+      }
+      uint32_t pt = __shfl_up_sync(kFull, Tw, 1);
+      if (lane == 0) pt = carry_t;
+      const uint32_t Ew = run_ends(0u, (Tw << 16) | (pt & 0xffffu), R5 ? 5u : p.R) >> 16;
+      // Positions judged: the lanes up to `upto`, below lim, from the region on.
+      const uint32_t vmask = (uint32_t)lane < upto ? low_bits((int32_t)span - lb) & 0xffffu : 0u;
+      const uint32_t em = Ew & vmask & ~low_bits(rr + (int32_t)p.R - 1 - lb);
+      const uint32_t om = Ow & vmask & ~low_bits(rr + 1 - lb);
+      const bool whole = upto == 32u || 16u * upto >= span;  // the step judged to its end
+      const uint32_t eb = __ballot_sync(kFull, em != 0u);
+      uint32_t need_k = 0;  // nonzero: the need_k-th opposing pair here fires a skip
+      if (eb) {
+        const int el = __ffs(eb) - 1;
+        const uint32_t ebit = __ffs(__shfl_sync(kFull, em, el)) - 1;
+        if (p.T) {
+          const uint32_t ob = lane < el ? om : (lane == el ? (om & ((1u << ebit) - 1u)) : 0u);
+          const uint32_t before = __reduce_add_sync(kFull, (uint32_t)__popc(ob));
+          if (opp + before >= p.T) need_k = p.T - opp;
+        }
+        if (!need_k) return cb + hb + 16u * el + ebit + 1u;
+      } else if (p.T) {
+        const uint32_t tot = __reduce_add_sync(kFull, (uint32_t)__popc(om));
+        if (opp + tot >= p.T) {
+          need_k = p.T - opp;
+        } else if (whole) {
+          opp += tot;  // the region goes on past this step
+          next = true;
+          break;
+        }
+      } else if (whole) {
+        next = true;
+        break;
+      }
+      if (!need_k) {  // nothing decided yet: judge eight more lanes
+        upto = min(32u, upto + kGrow);
+        continue;
+      }
+      // Skip: the need_k-th opposing pair fires; the next region starts
+      // SkipSize bytes after it.
+      const uint32_t cnt = __popc(om);
+      uint32_t sc = cnt;
+      for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t y = __shfl_up_sync(kFull, sc, d);
+        if (lane >= d) sc += y;
+      }
+      const int ol = __ffs(__ballot_sync(kFull, sc >= need_k)) - 1;
+      const uint32_t word = __shfl_sync(kFull, om, ol);
+      const uint32_t kth = __shfl_sync(kFull, need_k - (sc - cnt), ol);
+      const bool hit = ((word >> lane) & 1u) &&
+                       (uint32_t)__popc(word & (0xffffffffu >> (31 - lane))) == kth;
+      const uint32_t bp = __ffs(__ballot_sync(kFull, hit)) - 1;
+      r = hb + 16u * ol + bp + 1u + skip;
+      opp = 0;
+      if (r + 1 >= lim) return cb + lim;
+      if (r + 1 >= hb + 512u) break;  // the next region starts in a later step
+      // else the next region starts in this step: judged on what is loaded,
+      // its lanes loaded as it needs them
+    }
+    if (next) {
+      if (hb + 512u >= lim) return cb + lim;  // no run end before the limit
+      carry_b = __shfl_sync(kFull, v.w >> 24, 31);
+      carry_t = __shfl_sync(kFull, Tw, 31);
+      hb += 512u;
+    } else {
+      hb = r & ~15u;  // a fresh step at the new region's start
+      carry_b = 0;
+      carry_t = 0;
+    }
+  }
+  ok = false;
+  return cb + lim;
+}
+
 // ---------------------------------------------------------------------------
 // Junction walks.
 // ---------------------------------------------------------------------------
@@ -531,7 +666,7 @@ __device__ __forceinline__ uint32_t seek(const uint32_t *sp, uint32_t ns, uint32
 // With `done` set, the piece's spec walk may still be running (another warp):
 // its cuts are compared once done[k] is set, the cuts walked before that
 // first, in order.  Returns whether the walk met the spec walk.
-template <uint32_t MODE, bool R5>
+template <uint32_t MODE, bool R5, bool LAZY>
 __device__ bool junction_walk(const WGeom &g, const DevParams &p, const WPtrs &w,
                               uint32_t k, const Piece &pc, uint32_t x, const uint32_t *done,
                               uint32_t &chunks, uint32_t &wins, bool &ok) {
@@ -591,7 +726,7 @@ __device__ bool junction_walk(const WGeom &g, const DevParams &p, const WPtrs &w
         break;
       }
       if (have) checked = n;
-      rel = (uint32_t)(chunk_end_warp<MODE, R5>(g, p, pc.ps + rel, pc.fend, wins, ok) - pc.ps);
+      rel = (uint32_t)(chunk_end_warp<MODE, R5, LAZY>(g, p, pc.ps + rel, pc.fend, wins, ok) - pc.ps);
       ++chunks;
     }
     if (!fin && jm == kUnmerged) ok = false;
@@ -613,7 +748,7 @@ __device__ bool junction_walk(const WGeom &g, const DevParams &p, const WPtrs &w
 // the exit is where the true chain enters the next piece whenever this
 // piece's own junction met its spec walk.
 // ---------------------------------------------------------------------------
-template <uint32_t MODE, bool R5>
+template <uint32_t MODE, bool R5, bool LAZY>
 __global__ void __launch_bounds__(kWalkThreads, kWalkMinBlocks)
 walk_kernel(WGeom g, DevParams p, WPtrs w) {
   const int lane = threadIdx.x & 31;
@@ -632,7 +767,7 @@ walk_kernel(WGeom g, DevParams p, WPtrs w) {
     uint64_t c = pc.ps;
     uint32_t n = 0;
     do {
-      c = chunk_end_warp<MODE, R5>(g, p, c, pc.fend, wins, ok);
+      c = chunk_end_warp<MODE, R5, LAZY>(g, p, c, pc.fend, wins, ok);
       if (n < pc.cap) {
         if (lane == 0) out[n] = (uint32_t)(c - pc.ps);
         ++n;
@@ -657,7 +792,7 @@ walk_kernel(WGeom g, DevParams p, WPtrs w) {
     chunks += n;
     if (k + 1 < w.piece_base[pc.file + 1]) {
       const Piece pn = piece_of(g, w, p, k + 1);
-      const bool met = junction_walk<MODE, R5>(g, p, w, k + 1, pn, (uint32_t)(c - pn.ps), w.sdone,
+      const bool met = junction_walk<MODE, R5, LAZY>(g, p, w, k + 1, pn, (uint32_t)(c - pn.ps), w.sdone,
                                      jchunks, wins, ok);
       ++walks;
       unmerged += met ? 0u : 1u;
@@ -756,7 +891,7 @@ wrun_repair_kernel(WGeom g, DevParams p, WPtrs w, uint32_t round) {
         if (lane == 0) old = atomicMax(&w.claim[k], tag);
         if (__shfl_sync(kFull, old, 0) >= tag) break;  // another run's piece
       }
-      junction_walk<MODE, R5>(g, p, w, k, pc, x, nullptr, chunks, wins, ok);
+      junction_walk<MODE, R5, false>(g, p, w, k, pc, x, nullptr, chunks, wins, ok);
       ++redone;
     }
   }
@@ -786,7 +921,7 @@ wrepair_kernel(WGeom g, DevParams p, WPtrs w) {
       const Piece pc = piece_of(g, w, p, k);
       const uint32_t x = exit_of(w, k - 1u, pc.lb - g.fullcap) - g.P;
       if (x == w.jin[k]) continue;
-      junction_walk<MODE, R5>(g, p, w, k, pc, x, nullptr, chunks, wins, ok);
+      junction_walk<MODE, R5, false>(g, p, w, k, pc, x, nullptr, chunks, wins, ok);
       ++redone;
     }
   }
@@ -1001,7 +1136,8 @@ size_t workspace_bytes(const seqcdc_params_t *p, uint64_t total, uint64_t nfiles
 int run(const seqcdc_params_t *p, const uint8_t *d_data, uint64_t total,
         const uint64_t *d_offsets, uint64_t nfiles, uint64_t *d_cuts, uint64_t cap,
         uint64_t *d_cut_offsets, uint64_t *d_count, void *d_ws, size_t ws_bytes,
-        uint32_t piece, int sms, void *stream, void *prof_begin, void *prof_end) {
+        uint32_t piece, int sms, bool host_data, void *stream, void *prof_begin,
+        void *prof_end) {
   const WLayout l = make_wlayout(p, total, nfiles, piece);
   if (l.npmax >= 0xffffffffull || nfiles >= 0xffffffffull) return SEQCDC_ERANGE;
   if (ws_bytes < l.total) return SEQCDC_ECAPACITY;
@@ -1020,15 +1156,20 @@ int run(const seqcdc_params_t *p, const uint8_t *d_data, uint64_t total,
   const unsigned wgrid = (unsigned)(want < most ? want : most);
   if (prof_begin) record_event(static_cast<cudaEvent_t>(prof_begin), st);
   const int variant = (dp.mode ? 2 : 0) + (dp.R == 5u ? 1 : 0);
-  void (*const walk_fns[4])(WGeom, DevParams, WPtrs) = {
-      walk_kernel<0, false>, walk_kernel<0, true>, walk_kernel<1, false>, walk_kernel<1, true>};
+  // Input in host memory: the walks load each half window only when the
+  // scan reaches it (the bytes that cross to the GPU bound the walk there).
+  void (*const walk_fns[8])(WGeom, DevParams, WPtrs) = {
+      walk_kernel<0, false, false>, walk_kernel<0, true, false>,
+      walk_kernel<1, false, false>, walk_kernel<1, true, false>,
+      walk_kernel<0, false, true>,  walk_kernel<0, true, true>,
+      walk_kernel<1, false, true>,  walk_kernel<1, true, true>};
   void (*const run_fns[4])(WGeom, DevParams, WPtrs, uint32_t) = {
       wrun_repair_kernel<0, false>, wrun_repair_kernel<0, true>, wrun_repair_kernel<1, false>,
       wrun_repair_kernel<1, true>};
   void (*const rep_fns[4])(WGeom, DevParams, WPtrs) = {
       wrepair_kernel<0, false>, wrepair_kernel<0, true>, wrepair_kernel<1, false>,
       wrepair_kernel<1, true>};
-  walk_fns[variant]<<<wgrid, kWalkThreads, 0, st>>>(g, dp, w);
+  walk_fns[variant + (host_data ? 4 : 0)]<<<wgrid, kWalkThreads, 0, st>>>(g, dp, w);
   if (prof_end) record_event(static_cast<cudaEvent_t>(prof_end), st);
   const uint64_t vb = (l.npmax + 255) / 256;
   const unsigned vgrid = (unsigned)(vb < 4096 ? vb : 4096);

@@ -19,11 +19,14 @@ size_t workspace_bytes(const seqcdc_params_t *p, uint64_t total, uint64_t nfiles
                        uint32_t piece);
 
 // One chunking call (arguments as seqcdc_chunk / seqcdc_chunk_batch; the
-// parameters are already validated).  `prof_begin` / `prof_end` (may be null)
-// are recorded around the piece-walk kernel.
+// parameters are already validated).  `host_data`: d_data is pinned host
+// memory mapped into the device's address space (read in place).
+// `prof_begin` / `prof_end` (may be null) are recorded around the piece-walk
+// kernel.
 int run(const seqcdc_params_t *p, const uint8_t *d_data, uint64_t total,
         const uint64_t *d_offsets, uint64_t nfiles, uint64_t *d_cuts, uint64_t cap,
         uint64_t *d_cut_offsets, uint64_t *d_count, void *d_ws, size_t ws_bytes,
-        uint32_t piece, int sms, void *stream, void *prof_begin, void *prof_end);
+        uint32_t piece, int sms, bool host_data, void *stream, void *prof_begin,
+        void *prof_end);
 
 }  // namespace seqcdc_walk

@@ -17,6 +17,12 @@ after the previous block's last proven cut, kept on the device; the copy of a
 block to the device overlaps the chunking of the one before; the final cut of
 the last block is the stream end.
 
+``HostInPlace`` chunks a batch (or one stream) that stays in pinned host
+memory without copying it: the library's kernels read the bytes in place over
+the host link, and the chain walk they take loads only the half windows its
+scan reaches (Sec. III.B-C leave the rest unread), so a fraction of the input
+crosses.  Only the offsets go to the device and the cut lists come back.
+
 All chunking runs in the library's CUDA kernels; this module moves bytes and
 orders streams.
 """
@@ -173,6 +179,80 @@ def chunk_batch_host(h_data, h_offsets, p, pieces: int = 4, slots: int = 3,
     """One-off use of ``HostBatchPipeline``: chunk a CSR batch held in pinned
     host memory; returns host (cuts int64, cut_offsets int64)."""
     return HostBatchPipeline(p, tuning, device, slots).run(h_data, h_offsets, pieces)
+
+
+class HostInPlace:
+    """Chunking of input that stays in pinned host memory, read in place by
+    the kernels.  Device buffers (offsets, cut lists, workspace) and pinned
+    result buffers are kept between calls and grow when a larger call comes,
+    so a steady stream of calls allocates nothing."""
+
+    def __init__(self, p, tuning=None, device="cuda"):
+        import torch
+        self.torch = torch
+        self.p, self.tuning = p, tuning
+        self.dev = torch.device(device)
+        self.stream = torch.cuda.Stream(self.dev)
+        self.max_bytes = self.max_files = -1
+
+    def _grow(self, total: int, nfiles: int):
+        if total <= self.max_bytes and nfiles <= self.max_files:
+            return
+        torch, p, dev = self.torch, self.p, self.dev
+        self.max_bytes = max(total, self.max_bytes)
+        self.max_files = max(nfiles, self.max_files)
+        self.cap = self.max_bytes // p.min_size + self.max_files
+        self.d_offs = torch.empty(self.max_files + 1, dtype=torch.int64, device=dev)
+        self.d_cuts = torch.empty(max(self.cap, 1), dtype=torch.int64, device=dev)
+        self.d_co = torch.empty(self.max_files + 1, dtype=torch.int64, device=dev)
+        self.ws_bytes = seqcdc.seqcdc_workspace_size(p, self.max_bytes, self.max_files,
+                                                     self.tuning)
+        self.ws = torch.empty(self.ws_bytes, dtype=torch.uint8, device=dev)
+        self.h_offs = torch.empty(self.max_files + 1, dtype=torch.int64, pin_memory=True)
+        self.h_co = torch.empty(self.max_files + 1, dtype=torch.int64, pin_memory=True)
+        self.h_cuts = torch.empty(max(self.cap, 1), dtype=torch.int64, pin_memory=True)
+        self.h_status = torch.empty(1, dtype=torch.int32, pin_memory=True)
+
+    def run(self, h_data, h_offsets):
+        """(cuts int64, cut_offsets int64) on the host for a CSR batch whose
+        bytes ``h_data`` (a pinned uint8 tensor) stay on the host; equal to
+        ``chunk_batch`` of the same batch on the device.  The returned arrays
+        are views of buffers the next call reuses."""
+        torch = self.torch
+        if h_data.dtype != torch.uint8 or h_data.is_cuda or not h_data.is_pinned():
+            raise TypeError("HostInPlace.run needs a pinned uint8 host tensor")
+        h_data = h_data.view(-1)
+        offs = np.asarray(h_offsets.numpy() if hasattr(h_offsets, "numpy") else h_offsets,
+                          dtype=np.int64)
+        nfiles = offs.size - 1
+        total = int(h_data.numel())
+        if nfiles < 0 or int(offs[-1]) != total:
+            raise ValueError("offsets must end at the byte count")
+        self._grow(total, nfiles)
+        st = self.stream
+        self.h_offs[:nfiles + 1].numpy()[:] = offs
+        with torch.cuda.stream(st):
+            self.d_offs[:nfiles + 1].copy_(self.h_offs[:nfiles + 1], non_blocking=True)
+            seqcdc.seqcdc_chunk_batch(self.p, h_data, total, self.d_offs, nfiles, self.d_cuts,
+                                      self.cap, self.d_co, self.ws, self.ws_bytes, self.tuning,
+                                      st)
+            self.h_co[:nfiles + 1].copy_(self.d_co[:nfiles + 1], non_blocking=True)
+            self.h_status.copy_(self.ws[:4].view(torch.int32), non_blocking=True)
+        st.synchronize()
+        if int(self.h_status[0]) != 0:
+            seqcdc._check(int(self.h_status[0]), "HostInPlace.run (device)")
+        n = int(self.h_co[nfiles])
+        with torch.cuda.stream(st):
+            self.h_cuts[:n].copy_(self.d_cuts[:n], non_blocking=True)
+        st.synchronize()
+        return self.h_cuts[:n].numpy(), self.h_co[:nfiles + 1].numpy()
+
+    def run_stream(self, h_data):
+        """Cut offsets (int64, on the host) of one stream that stays in pinned
+        host memory; equal to ``chunk`` of the same bytes on the device."""
+        n = int(h_data.numel())
+        cuts, _ = self.run(h_data, np.array([0, n], dtype=np.int64))
+        return cuts
 
 
 class HostStreamPipeline:

@@ -306,19 +306,35 @@ def _on_stream(stream, device):
     return stream if stream is not None else torch.cuda.current_stream(device)
 
 
-def chunk(data, p: Params, tuning=None, stream=None, check: bool = True):
-    """Chunk one uint8 CUDA tensor; returns an int64 tensor of cut offsets."""
+def _input_device(data, what: str):
+    """The CUDA device that reads ``data``: its own for a CUDA tensor, the
+    current one for a pinned host tensor (read in place by the kernels)."""
     import torch
-    if not data.is_cuda or data.dtype != torch.uint8:
-        raise TypeError("chunk() needs a uint8 CUDA tensor")
+    if data.dtype != torch.uint8:
+        raise TypeError("%s needs uint8 data" % what)
+    if data.is_cuda:
+        return data.device
+    if data.is_pinned():
+        return torch.device("cuda", torch.cuda.current_device())
+    raise TypeError("%s needs a CUDA tensor or a pinned host tensor" % what)
+
+
+def chunk(data, p: Params, tuning=None, stream=None, check: bool = True):
+    """Chunk one uint8 tensor; returns an int64 CUDA tensor of cut offsets.
+
+    ``data`` is a CUDA tensor, or a pinned host tensor that the kernels read
+    in place (only the windows the scan reaches cross to the GPU).
+    """
+    import torch
+    dev = _input_device(data, "chunk()")
     data = data.contiguous().view(-1)
     n = data.numel()
     cap = n // p.min_size + 1
-    st = _on_stream(stream, data.device)
+    st = _on_stream(stream, dev)
     with torch.cuda.stream(st):
-        cuts = torch.empty(max(cap, 1), dtype=torch.int64, device=data.device)
-        count = torch.zeros(1, dtype=torch.int64, device=data.device)
-        ws, ws_bytes = _workspace(p, n, 1, tuning, data.device)
+        cuts = torch.empty(max(cap, 1), dtype=torch.int64, device=dev)
+        count = torch.zeros(1, dtype=torch.int64, device=dev)
+        ws, ws_bytes = _workspace(p, n, 1, tuning, dev)
         seqcdc_chunk(p, data, n, cuts, cap, count, ws, ws_bytes, tuning, st)
         if check:
             _check(seqcdc_status(ws, st), "seqcdc_chunk (device)")
@@ -328,22 +344,28 @@ def chunk(data, p: Params, tuning=None, stream=None, check: bool = True):
 
 def chunk_batch(data, offsets, p: Params, tuning=None, stream=None,
                 check: bool = True) -> BatchResult:
-    """Chunk a CSR batch: ``data`` uint8 CUDA, ``offsets`` int64 CUDA (nfiles+1)."""
+    """Chunk a CSR batch: ``data`` uint8, ``offsets`` int64 (nfiles+1).
+
+    ``data`` is a CUDA tensor, or a pinned host tensor that the kernels read
+    in place; ``offsets`` a CUDA tensor, or a host tensor (copied to the
+    device).  The results are CUDA tensors.
+    """
     import torch
-    if not data.is_cuda or data.dtype != torch.uint8:
-        raise TypeError("chunk_batch() needs uint8 CUDA data")
-    if not offsets.is_cuda or offsets.dtype != torch.int64:
-        raise TypeError("chunk_batch() needs int64 CUDA offsets")
+    dev = _input_device(data, "chunk_batch()")
+    if offsets.dtype != torch.int64:
+        raise TypeError("chunk_batch() needs int64 offsets")
     data = data.contiguous().view(-1)
     offsets = offsets.contiguous().view(-1)
     nfiles = offsets.numel() - 1
     total = data.numel()
     cap = total // p.min_size + nfiles
-    st = _on_stream(stream, data.device)
+    st = _on_stream(stream, dev)
     with torch.cuda.stream(st):
-        cuts = torch.empty(max(cap, 1), dtype=torch.int64, device=data.device)
-        cut_offsets = torch.empty(nfiles + 1, dtype=torch.int64, device=data.device)
-        ws, ws_bytes = _workspace(p, total, nfiles, tuning, data.device)
+        if not offsets.is_cuda:
+            offsets = offsets.to(dev, non_blocking=offsets.is_pinned())
+        cuts = torch.empty(max(cap, 1), dtype=torch.int64, device=dev)
+        cut_offsets = torch.empty(nfiles + 1, dtype=torch.int64, device=dev)
+        ws, ws_bytes = _workspace(p, total, nfiles, tuning, dev)
         seqcdc_chunk_batch(p, data, total, offsets, nfiles, cuts, cap, cut_offsets,
                            ws, ws_bytes, tuning, st)
         if check:

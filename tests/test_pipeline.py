@@ -1,6 +1,8 @@
 """Host-resident data: pipelined batches and resumable streams."""
 from __future__ import annotations
 
+import ctypes
+
 import numpy as np
 import pytest
 
@@ -117,3 +119,54 @@ def test_host_stream_pipeline_resumable_uneven_blocks(gpu):
         cut = np.unique(rng.integers(0, data.size, 7))
         blocks = np.split(data, cut)
         assert np.array_equal(pipe.run(blocks), exp)
+
+
+@pytest.mark.gpu
+def test_host_in_place_equals_device_and_oracle(gpu):
+    """Input read in place from pinned host memory: the same cuts as on the
+    device, on both paths (AUTO takes the walk for host input), for a batch
+    with an empty file and a stream; pageable input is refused."""
+    import torch
+    from paper_2505_21194_gb300.pipeline import HostInPlace
+    s = gpu
+    data, offs = W.file_batch(300, seed=21)
+    offs = np.insert(offs.astype(np.int64), 7, offs[7])   # an empty file
+    p = s.seqcdc_params(8, 0)
+    r = s.chunk_batch(torch.from_numpy(data).cuda(), torch.from_numpy(offs).cuda(), p)
+    exp_c, exp_co = r.cuts.cpu().numpy(), r.cut_offsets.cpu().numpy()
+    h = torch.from_numpy(data).pin_memory()
+    hp = HostInPlace(p)
+    for tuning in (None, s.Tuning(0, 0, s.ALGO_WALK, 262144), s.Tuning(0, 0, s.ALGO_MAP, 0)):
+        hp.tuning = tuning
+        hp.max_bytes = -1                                 # workspace for this tuning
+        c, co = hp.run(h, offs)
+        assert np.array_equal(co, exp_co) and np.array_equal(c, exp_c), tuning
+    # convenience entry points take the pinned tensor as it is
+    r2 = s.chunk_batch(h, torch.from_numpy(offs), p)
+    assert torch.equal(r2.cuts.cpu(), r.cuts.cpu())
+    a, b = int(offs[2]), int(offs[3])
+    ec = oracle.chunk(data[a:b], oracle.presets(8)).astype(np.int64)
+    assert np.array_equal(exp_c[exp_co[2]:exp_co[3]], ec)
+    # one stream, both modes
+    stream = W.mixed_base(24 << 20, 5)
+    hs = torch.from_numpy(stream).pin_memory()
+    for mode in (0, 1):
+        q = s.seqcdc_params(8, mode)
+        hq = HostInPlace(q)
+        got = hq.run_stream(hs)
+        want = s.chunk(torch.from_numpy(stream).cuda(), q).cpu().numpy()
+        assert np.array_equal(got, want), mode
+        assert np.array_equal(s.chunk(hs, q).cpu().numpy(), want)
+    # pageable host memory cannot be read by the device: refused, not launched
+    with pytest.raises(TypeError):
+        s.chunk(torch.from_numpy(stream), p)
+    lib = s.load_library()
+    pageable = torch.from_numpy(stream.copy())
+    n = pageable.numel()
+    ws_bytes = s.seqcdc_workspace_size(p, n, 1)
+    ws = torch.empty(ws_bytes, dtype=torch.uint8, device="cuda")
+    cuts = torch.empty(n // p.min_size + 1, dtype=torch.int64, device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    rc = lib.seqcdc_chunk(ctypes.byref(p), pageable.data_ptr(), n, cuts.data_ptr(),
+                          cuts.numel(), cnt.data_ptr(), ws.data_ptr(), ws_bytes, None, None)
+    assert rc == s.SEQCDC_EINVAL
