@@ -171,7 +171,9 @@ int seqcdc_algorithm(const seqcdc_params_t *p, uint64_t total_bytes, uint64_t nf
  *            cross (Sec. III.B-C skip the rest).
  *            Pageable host memory gives SEQCDC_EINVAL (after the size
  *            checks, before any launch).  16-byte aligned.
- *   d_cuts   out: up to `cap` uint64 chunk end offsets.
+ *   d_cuts   out: up to `cap` uint64 chunk end offsets (device memory, or
+ *            mapped pinned host memory that the kernels write to directly;
+ *            likewise d_count and, for batches, d_cut_offsets).
  *   cap      capacity of d_cuts in entries; must be >= n / min_size + 1
  *            (always sufficient), else SEQCDC_ECAPACITY.
  *   d_count  out: one uint64, the number of cuts written.

@@ -21,7 +21,8 @@ the last block is the stream end.
 memory without copying it: the library's kernels read the bytes in place over
 the host link, and the chain walk they take loads only the half windows its
 scan reaches (Sec. III.B-C leave the rest unread), so a fraction of the input
-crosses.  Only the offsets go to the device and the cut lists come back.
+crosses.  Only the offsets go to the device; the kernels write the cut lists
+straight into pinned host memory.
 
 All chunking runs in the library's CUDA kernels; this module moves bytes and
 orders streams.
@@ -203,8 +204,6 @@ class HostInPlace:
         self.max_files = max(nfiles, self.max_files)
         self.cap = self.max_bytes // p.min_size + self.max_files
         self.d_offs = torch.empty(self.max_files + 1, dtype=torch.int64, device=dev)
-        self.d_cuts = torch.empty(max(self.cap, 1), dtype=torch.int64, device=dev)
-        self.d_co = torch.empty(self.max_files + 1, dtype=torch.int64, device=dev)
         self.ws_bytes = seqcdc.seqcdc_workspace_size(p, self.max_bytes, self.max_files,
                                                      self.tuning)
         self.ws = torch.empty(self.ws_bytes, dtype=torch.uint8, device=dev)
@@ -233,18 +232,16 @@ class HostInPlace:
         self.h_offs[:nfiles + 1].numpy()[:] = offs
         with torch.cuda.stream(st):
             self.d_offs[:nfiles + 1].copy_(self.h_offs[:nfiles + 1], non_blocking=True)
-            seqcdc.seqcdc_chunk_batch(self.p, h_data, total, self.d_offs, nfiles, self.d_cuts,
-                                      self.cap, self.d_co, self.ws, self.ws_bytes, self.tuning,
+            # The cut lists and their index are written straight into pinned
+            # host memory (mapped, like the input): nothing to copy back.
+            seqcdc.seqcdc_chunk_batch(self.p, h_data, total, self.d_offs, nfiles, self.h_cuts,
+                                      self.cap, self.h_co, self.ws, self.ws_bytes, self.tuning,
                                       st)
-            self.h_co[:nfiles + 1].copy_(self.d_co[:nfiles + 1], non_blocking=True)
             self.h_status.copy_(self.ws[:4].view(torch.int32), non_blocking=True)
         st.synchronize()
         if int(self.h_status[0]) != 0:
             seqcdc._check(int(self.h_status[0]), "HostInPlace.run (device)")
         n = int(self.h_co[nfiles])
-        with torch.cuda.stream(st):
-            self.h_cuts[:n].copy_(self.d_cuts[:n], non_blocking=True)
-        st.synchronize()
         return self.h_cuts[:n].numpy(), self.h_co[:nfiles + 1].numpy()
 
     def run_stream(self, h_data):
