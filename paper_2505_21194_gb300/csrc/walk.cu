@@ -45,7 +45,6 @@
 
 namespace {
 
-constexpr uint32_t kWin = 1024;        // bytes per warp window (32 per lane)
 constexpr int kWalkThreads = 128;      // walk kernels: four warps per block
 // Blocks of the walk kernels resident per SM that the register budget is
 // sized for: 16 blocks of 4 warps, 32 registers per thread without spills
@@ -398,9 +397,19 @@ __device__ uint64_t chunk_end_host(const WGeom &g, const DevParams &p, uint64_t 
 
 template <uint32_t MODE, bool R5, bool LAZY>
 __device__ uint64_t chunk_end_warp(const WGeom &g, const DevParams &p, uint64_t c,
-                                   uint64_t fend, uint32_t &wins, bool &ok) {
+                                   uint64_t fend, uint32_t &wins, bool &ok, bool pf = false) {
   if (LAZY) return chunk_end_host<MODE, R5>(g, p, c, fend, wins, ok);
   const int lane = threadIdx.x & 31;
+  if (pf) {
+    // Ask L2 for 3 KiB where the next chunk's scan most likely starts (its
+    // cut is at least min_size on, its scan min_size - SeqLength after that),
+    // so that its first window does not wait for HBM.  Used only where the
+    // walk is bound by latency rather than issue: once no piece is left to
+    // take, and in the repairs (few warps).
+    const uint64_t a = ((c + 2ull * p.mn - p.R) & ~127ull) + 128u * (uint32_t)lane;
+    if (lane < 24 && a + 128u <= g.total)
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(g.data + a));
+  }
   const uint64_t rest = fend - c;
   const uint64_t lim_abs = c + (rest > p.mx ? p.mx : rest);
   const uint64_t r_abs = c + (p.mn > p.R ? p.mn - p.R : 0u);
@@ -669,7 +678,7 @@ __device__ __forceinline__ uint32_t seek(const uint32_t *sp, uint32_t ns, uint32
 template <uint32_t MODE, bool R5, bool LAZY>
 __device__ bool junction_walk(const WGeom &g, const DevParams &p, const WPtrs &w,
                               uint32_t k, const Piece &pc, uint32_t x, const uint32_t *done,
-                              uint32_t &chunks, uint32_t &wins, bool &ok) {
+                              uint32_t &chunks, uint32_t &wins, bool &ok, bool pf = false) {
   const int lane = threadIdx.x & 31;
   const uint32_t *sp = w.spec + pc.lb;
   uint32_t *jc = w.jcut + pc.lb;
@@ -726,7 +735,8 @@ __device__ bool junction_walk(const WGeom &g, const DevParams &p, const WPtrs &w
         break;
       }
       if (have) checked = n;
-      rel = (uint32_t)(chunk_end_warp<MODE, R5, LAZY>(g, p, pc.ps + rel, pc.fend, wins, ok) - pc.ps);
+      rel = (uint32_t)(chunk_end_warp<MODE, R5, LAZY>(g, p, pc.ps + rel, pc.fend, wins, ok, pf) -
+                       pc.ps);
       ++chunks;
     }
     if (!fin && jm == kUnmerged) ok = false;
@@ -766,8 +776,14 @@ walk_kernel(WGeom g, DevParams p, WPtrs w) {
     uint32_t *out = w.spec + pc.lb;
     uint64_t c = pc.ps;
     uint32_t n = 0;
+    bool pf = false;  // prefetch, once every piece is taken (see below)
     do {
-      c = chunk_end_warp<MODE, R5, LAZY>(g, p, c, pc.fend, wins, ok);
+      if (!LAZY && !pf && (n & 7u) == 0u) {
+        uint32_t drained = 0;
+        if (lane == 0) drained = __ldcg(&w.hdr->ticket) >= np ? 1u : 0u;
+        pf = __shfl_sync(kFull, drained, 0) != 0u;
+      }
+      c = chunk_end_warp<MODE, R5, LAZY>(g, p, c, pc.fend, wins, ok, pf);
       if (n < pc.cap) {
         if (lane == 0) out[n] = (uint32_t)(c - pc.ps);
         ++n;
@@ -792,8 +808,15 @@ walk_kernel(WGeom g, DevParams p, WPtrs w) {
     chunks += n;
     if (k + 1 < w.piece_base[pc.file + 1]) {
       const Piece pn = piece_of(g, w, p, k + 1);
+      // Once every piece is taken the SMs empty out and the walks left
+      // wait on memory rather than on issue: prefetch then.
+      if (!LAZY && !pf) {
+        uint32_t drained = 0;
+        if (lane == 0) drained = __ldcg(&w.hdr->ticket) >= np ? 1u : 0u;
+        pf = __shfl_sync(kFull, drained, 0) != 0u;
+      }
       const bool met = junction_walk<MODE, R5, LAZY>(g, p, w, k + 1, pn, (uint32_t)(c - pn.ps), w.sdone,
-                                     jchunks, wins, ok);
+                                     jchunks, wins, ok, pf);
       ++walks;
       unmerged += met ? 0u : 1u;
     }
@@ -891,7 +914,7 @@ wrun_repair_kernel(WGeom g, DevParams p, WPtrs w, uint32_t round) {
         if (lane == 0) old = atomicMax(&w.claim[k], tag);
         if (__shfl_sync(kFull, old, 0) >= tag) break;  // another run's piece
       }
-      junction_walk<MODE, R5, false>(g, p, w, k, pc, x, nullptr, chunks, wins, ok);
+      junction_walk<MODE, R5, false>(g, p, w, k, pc, x, nullptr, chunks, wins, ok, true);
       ++redone;
     }
   }
@@ -921,7 +944,7 @@ wrepair_kernel(WGeom g, DevParams p, WPtrs w) {
       const Piece pc = piece_of(g, w, p, k);
       const uint32_t x = exit_of(w, k - 1u, pc.lb - g.fullcap) - g.P;
       if (x == w.jin[k]) continue;
-      junction_walk<MODE, R5, false>(g, p, w, k, pc, x, nullptr, chunks, wins, ok);
+      junction_walk<MODE, R5, false>(g, p, w, k, pc, x, nullptr, chunks, wins, ok, true);
       ++redone;
     }
   }
