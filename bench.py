@@ -187,7 +187,8 @@ def workload_config(total: int, nfiles: int) -> dict:
 
 
 # Source files each dominant kernel is built from: a DRAM-traffic record
-# under profiles/ is used only while their hash still matches.
+# under profiles/ is used only while the hash of their code (comments
+# removed) still matches.
 KERNEL_SOURCES = {
     "walk_kernel": ("paper_2505_21194_gb300/csrc/walk.cu",
                     "paper_2505_21194_gb300/csrc/common.cuh"),
@@ -207,11 +208,36 @@ def _traffic_record(kernel: str):
     return d if d.get("source_sha256") == _source_hash(kernel) else None
 
 
+def _strip_comments(src: str) -> str:
+    """C/C++ source without its comments and blank lines: the code a traffic
+    record was measured on, unaffected by edits to comments alone."""
+    out, i, n = [], 0, len(src)
+    while i < n:
+        c = src[i]
+        if c == '"' or c == "'":
+            j = i + 1
+            while j < n and src[j] != c:
+                j += 2 if src[j] == "\\" else 1
+            out.append(src[i:j + 1])
+            i = j + 1
+        elif src.startswith("//", i):
+            j = src.find("\n", i)
+            i = n if j < 0 else j
+        elif src.startswith("/*", i):
+            j = src.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+        else:
+            out.append(c)
+            i += 1
+    lines = [l.rstrip() for l in "".join(out).splitlines()]
+    return "\n".join(l for l in lines if l)
+
+
 def _source_hash(kernel: str):
     h = hashlib.sha256()
     for rel in KERNEL_SOURCES[kernel]:
-        with open(os.path.join(ROOT, rel), "rb") as f:
-            h.update(f.read())
+        with open(os.path.join(ROOT, rel), encoding="utf-8") as f:
+            h.update(_strip_comments(f.read()).encode())
     return h.hexdigest()
 
 

@@ -524,7 +524,7 @@ __device__ uint64_t chunk_end_warp(const WGeom &g, const DevParams &p, uint64_t 
 // input read in place from host memory, where the bytes that cross the host
 // link bound the walk and instructions are cheap.  A scan step covers 512
 // bytes from the region's start (16 per lane), but loads them 128 bytes
-// (eight lanes) at a time and judges the region on what it has loaded: it
+// (eight lanes) at a time and decides the region on what it has loaded: it
 // loads more only while no run end or skip has shown up, and never the bytes
 // before the region's start.  `secs` counts the 32-byte sectors read.
 template <uint32_t MODE, bool R5>
@@ -552,7 +552,7 @@ __device__ uint64_t chunk_end_host(const WGeom &g, const DevParams &p, uint64_t 
     uint4 v = make_uint4(0u, 0u, 0u, 0u);
     uint32_t Tw = 0, Ow = 0;
     uint32_t have = 0;                // lanes loaded
-    uint32_t upto = 0;                // lanes judged: [0, upto)
+    uint32_t upto = 0;                // lanes decided on: [0, upto)
     bool next = false;                // the region goes on into the next step
     for (uint32_t pass = 0; pass < 64u + p.mx; ++pass) {
       const int32_t rr = (int32_t)(r - hb);  // region start in the step (< 0: continued)
@@ -576,11 +576,11 @@ __device__ uint64_t chunk_end_host(const WGeom &g, const DevParams &p, uint64_t 
       uint32_t pt = __shfl_up_sync(kFull, Tw, 1);
       if (lane == 0) pt = carry_t;
       const uint32_t Ew = run_ends(0u, (Tw << 16) | (pt & 0xffffu), R5 ? 5u : p.R) >> 16;
-      // Positions judged: the lanes up to `upto`, below lim, from the region on.
+      // Positions decided on: the lanes up to `upto`, below lim, from the region on.
       const uint32_t vmask = (uint32_t)lane < upto ? low_bits((int32_t)span - lb) & 0xffffu : 0u;
       const uint32_t em = Ew & vmask & ~low_bits(rr + (int32_t)p.R - 1 - lb);
       const uint32_t om = Ow & vmask & ~low_bits(rr + 1 - lb);
-      const bool whole = upto == 32u || 16u * upto >= span;  // the step judged to its end
+      const bool whole = upto == 32u || 16u * upto >= span;  // the step seen to its end
       const uint32_t eb = __ballot_sync(kFull, em != 0u);
       uint32_t need_k = 0;  // nonzero: the need_k-th opposing pair here fires a skip
       if (eb) {
@@ -605,7 +605,7 @@ __device__ uint64_t chunk_end_host(const WGeom &g, const DevParams &p, uint64_t 
         next = true;
         break;
       }
-      if (!need_k) {  // nothing decided yet: judge eight more lanes
+      if (!need_k) {  // nothing decided yet: eight more lanes
         upto = min(32u, upto + kGrow);
         continue;
       }
@@ -627,7 +627,7 @@ __device__ uint64_t chunk_end_host(const WGeom &g, const DevParams &p, uint64_t 
       opp = 0;
       if (r + 1 >= lim) return cb + lim;
       if (r + 1 >= hb + 512u) break;  // the next region starts in a later step
-      // else the next region starts in this step: judged on what is loaded,
+      // else the next region starts in this step: decided on what is loaded,
       // its lanes loaded as it needs them
     }
     if (next) {
