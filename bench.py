@@ -735,13 +735,26 @@ def run_gpu(args):
             line["serve_%d_sustained_GBs" % g] = lv["sustained_GBs"]
         line["serve_checked"] = sv["checked"]
         line["serve_mismatches"] = sv["mismatches"]
+        # Secondary: requests with config 3's log-normal sizes (median
+        # 256 KiB), drawn from the 10,000 files already in pinned memory.
+        sl = serve_levels(dev, p, None, SERVE_LOGNORMAL_GBS, (data_np, offs_np),
+                          pinned=h_data,
+                          requests_from="the 10,000 log-normal files of the batch")
+        detail["serve_lognormal"] = sl
+        for lv in sl["levels"]:
+            g = lv["offered_GBs"]
+            line["serve_lognormal_%d_p50_ms" % g] = lv["p50_ms"]
+            line["serve_lognormal_%d_p99_ms" % g] = lv["p99_ms"]
+            line["serve_lognormal_%d_sustained_GBs" % g] = lv["sustained_GBs"]
+        line["serve_lognormal_checked"] = sl["checked"]
+        line["serve_lognormal_mismatches"] = sl["mismatches"]
     if not args.no_dedup:
         dd = dedup_savings(dev, backup)
         sw = sweep_report(dev, backup)
         detail["dedup"], detail["sweep"] = dd, sw
         for r in dd["settings"]:
-            if r["mode"] == "increasing":
-                line["dedup_savings_%dKiB" % r["setting_KiB"]] = r["savings"]
+            suffix = "" if r["mode"] == "increasing" else "_decreasing"
+            line["dedup_savings_%dKiB%s" % (r["setting_KiB"], suffix)] = r["savings"]
         line["dedup_host_sha256_agrees"] = all(r["host_sha256_agrees"] for r in dd["settings"])
         sr = sw["search"]
         for reading in (0, 1):
@@ -785,6 +798,7 @@ def run_gpu(args):
 
 
 SERVE_LOADS_GBS = (25, 50, 100, 200)
+SERVE_LOGNORMAL_GBS = (10, 25)  # requests of config 3's sizes (many small ones)
 
 
 def time_stream(dev, d, p, peak, reps=5, flush=None, tuning=None):
@@ -1020,12 +1034,15 @@ def dedup_savings(dev, backup):
                     "host SHA-256 (hashlib) as the check", "settings": out}
 
 
-def serve_levels(dev, p, tuning, loads, backup, duration_s=1.0):
+def serve_levels(dev, p, tuning, loads, backup, duration_s=1.0, pinned=None,
+                 requests_from="64 versions (~16 MiB each) of the 1 GiB backup-like stream"):
     """Open-loop serving at each offered load (GB/s): Poisson arrivals of
-    requests drawn from the 64 versions (about 16 MiB each) of the backup-like
-    stream, admitted under a 64 GiB HBM budget, batched continuously.  One
-    request in a hundred is checked against the oracle and against the same
-    payload chunked alone."""
+    requests drawn from the payloads of ``backup`` (bytes, offsets: by
+    default the 64 versions, about 16 MiB each, of the backup-like stream;
+    ``pinned`` may hold the same bytes already in pinned memory), admitted
+    under a 64 GiB HBM budget, batched continuously.  One request in a
+    hundred is checked against the oracle and against the same payload
+    chunked alone."""
     import torch
     import oracle
     from paper_2505_21194_gb300 import seqcdc, workloads as W
@@ -1033,7 +1050,7 @@ def serve_levels(dev, p, tuning, loads, backup, duration_s=1.0):
     stream, voffs = backup
     voffs = voffs.astype(np.int64)
     sizes = np.diff(voffs)
-    pool = torch.from_numpy(stream).pin_memory()
+    pool = pinned if pinned is not None else torch.from_numpy(stream).pin_memory()
     srv = Server(p, pool, voffs, budget_bytes=64 << 30, max_batch_bytes=4 << 30,
                  tuning=tuning, device=str(dev))
     op = oracle.Params(p.mode, p.seq_length, p.skip_trigger, p.skip_size,
@@ -1061,7 +1078,7 @@ def serve_levels(dev, p, tuning, loads, backup, duration_s=1.0):
                        "sustained_GBs": round(st.sustained_gbs, 2),
                        "p50_ms": round(st.latency["p50_ms"], 3),
                        "p99_ms": round(st.latency["p99_ms"], 3)})
-    return {"requests_from": "64 versions (~16 MiB each) of the 1 GiB backup-like stream",
+    return {"requests_from": requests_from,
             "arrivals": "Poisson, open loop, %.1f s per level" % duration_s,
             "hbm_budget_GiB": 64, "max_batch_GiB": 4, "levels": levels,
             "checked": checked, "mismatches": bad,
