@@ -491,6 +491,9 @@ def run_gpu(args):
     # loaded, or every byte on the segment map.
     ip_host_bytes = (ip_stats["windows"] * 32 if ip_path == "chain walk" else total)
     inplace_gbs = total * world / statistics.median(inplace_s) / 1e9
+    # How busy the host link is: bytes read from host memory per second of
+    # the whole call, against the bare host-to-device copy rate.
+    ip_link_gbs = ip_host_bytes / statistics.median(inplace_s) / 1e9
     h2d_gbs = h2d_copy_gbs()
     # d_data now holds the batch again (the copies above wrote the same bytes)
 
@@ -673,6 +676,8 @@ def run_gpu(args):
                 "api": "pipeline.HostInPlace.run (batch in pinned host memory, read in "
                        "place by the kernels; %s)" % ip_path,
                 "input_bytes_on_host": int(total),
+                "host_read_GBs": round(ip_link_gbs, 1),
+                "host_read_frac_of_copy": round(ip_link_gbs / h2d_before, 3),
                 "h2d_bytes": "bytes the kernels read from host memory (32-byte sectors, "
                              "walk counter) + the offsets",
                 "copy_pipeline_GBs": round(e2e_gbs, 2),
