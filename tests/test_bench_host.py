@@ -55,3 +55,16 @@ def test_kernel_sources_exist_and_records_are_current_or_ignored():
             with open(path) as f:
                 assert json.load(f)["source_sha256"] == bench._source_hash(kernel)
             assert 0 < rec["dram_bytes_per_byte"] < 2
+
+
+def test_source_hash_ignores_comments_but_not_code():
+    """A traffic record stays valid across edits to comments alone, and no
+    longer matches once the code itself changes."""
+    src = ('// head\n#include <x.h>\n/* block\n comment */\nint a = 1;  // trailing\n'
+           'const char *s = "not // a comment";\nchar c = \'/\';\n\n')
+    stripped = bench._strip_comments(src)
+    assert stripped == ('#include <x.h>\nint a = 1;\nconst char *s = "not // a comment";\n'
+                        "char c = '/';")
+    reworded = src.replace("// trailing", "// reworded").replace("block", "other")
+    assert bench._strip_comments(reworded) == stripped
+    assert bench._strip_comments(src.replace("a = 1", "a = 2")) != stripped
