@@ -218,7 +218,8 @@ class HostInPlace:
         ``chunk_batch`` of the same batch on the device.  The returned arrays
         are views of buffers the next call reuses."""
         torch = self.torch
-        if h_data.dtype != torch.uint8 or h_data.is_cuda or not h_data.is_pinned():
+        if h_data.dtype != torch.uint8 or h_data.is_cuda or (
+                h_data.numel() and not h_data.is_pinned()):
             raise TypeError("HostInPlace.run needs a pinned uint8 host tensor")
         h_data = h_data.view(-1)
         offs = np.asarray(h_offsets.numpy() if hasattr(h_offsets, "numpy") else h_offsets,

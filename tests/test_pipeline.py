@@ -170,3 +170,25 @@ def test_host_in_place_equals_device_and_oracle(gpu):
     rc = lib.seqcdc_chunk(ctypes.byref(p), pageable.data_ptr(), n, cuts.data_ptr(),
                           cuts.numel(), cnt.data_ptr(), ws.data_ptr(), ws_bytes, None, None)
     assert rc == s.SEQCDC_EINVAL
+
+
+@pytest.mark.gpu
+def test_host_in_place_tiny_and_ragged_streams(gpu):
+    """Streams read in place whose sizes are empty, below a 16-byte load,
+    not a multiple of 16, and around min_size and max_size: the same cuts
+    as on the device, and the oracle's."""
+    import torch
+    from paper_2505_21194_gb300.pipeline import HostInPlace
+    s = gpu
+    p = s.seqcdc_params(8, 0)
+    hp = HostInPlace(p)
+    base = W.mixed_base(1 << 20, 11)
+    for n in (0, 1, 15, 17, 4095, 4096, 4097, 16383, 16384, 16385, 70001, (1 << 20) - 3):
+        data = base[:n].copy()
+        h = torch.from_numpy(data).pin_memory() if n else torch.empty(0, dtype=torch.uint8)
+        got = hp.run_stream(h)
+        want = oracle.chunk(data, oracle.presets(8)).astype(np.int64) if n else np.zeros(0, np.int64)
+        assert np.array_equal(got, want), n
+        if n:
+            dev = s.chunk(torch.from_numpy(data).cuda(), p).cpu().numpy()
+            assert np.array_equal(dev, want), n
