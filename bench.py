@@ -803,7 +803,7 @@ def run_gpu(args):
 
 
 SERVE_LOADS_GBS = (25, 50, 100, 200)
-SERVE_LOGNORMAL_GBS = (10, 25)  # requests of config 3's sizes (many small ones)
+SERVE_LOGNORMAL_GBS = (10, 25, 50, 100)  # requests of config 3's sizes (many small ones)
 
 
 def time_stream(dev, d, p, peak, reps=5, flush=None, tuning=None):

@@ -257,6 +257,21 @@ int seqcdc_chunk_noalloc(const seqcdc_params_t *p, const uint8_t *d_in,
 int seqcdc_status(const void *d_ws, void *stream);
 
 /*
+ * Copy n byte ranges, in order, each as one cudaMemcpyAsync on `stream`:
+ * dst[dst_off[i] .. dst_off[i] + len[i]) = src[src_off[i] .. + len[i]).
+ * dst and src are device memory or pinned host memory (any direction);
+ * dst_off, src_off and len are host arrays of n entries; ranges of length 0
+ * are skipped.  A batch of many requests is gathered into one buffer this
+ * way (the serving loop) without a runtime call per request from the
+ * caller's language.  Returns SEQCDC_EINVAL for n > 0 with a NULL pointer
+ * or array, SEQCDC_ECUDA if a copy cannot be enqueued (the copies before it
+ * stay enqueued).
+ */
+int seqcdc_copy_ranges(void *dst, const void *src, const uint64_t *dst_off,
+                       const uint64_t *src_off, const uint64_t *len, uint64_t n,
+                       void *stream);
+
+/*
  * Synchronise `stream` and copy up to `n` (<= 8) path counters of the last
  * call that used d_ws into out[].  Segment map: [0] segments processed,
  * [1] segments whose natural entries could not all be walked, [2] segments

@@ -1803,6 +1803,23 @@ int seqcdc_chunk_noalloc(const seqcdc_params_t *p, const uint8_t *d_in,
   return cudaGetLastError() == cudaSuccess ? SEQCDC_OK : SEQCDC_ECUDA;
 }
 
+int seqcdc_copy_ranges(void *dst, const void *src, const uint64_t *dst_off,
+                       const uint64_t *src_off, const uint64_t *len, uint64_t n,
+                       void *stream) {
+  if (n == 0) return SEQCDC_OK;
+  if (!dst || !src || !dst_off || !src_off || !len) return SEQCDC_EINVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  char *d = static_cast<char *>(dst);
+  const char *s = static_cast<const char *>(src);
+  for (uint64_t i = 0; i < n; ++i) {
+    if (!len[i]) continue;
+    if (cudaMemcpyAsync(d + dst_off[i], s + src_off[i], len[i], cudaMemcpyDefault, st) !=
+        cudaSuccess)
+      return SEQCDC_ECUDA;
+  }
+  return SEQCDC_OK;
+}
+
 int seqcdc_status(const void *d_ws, void *stream) {
   if (!d_ws) return SEQCDC_EINVAL;
   cudaStream_t st = static_cast<cudaStream_t>(stream);

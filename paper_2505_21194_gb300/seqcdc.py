@@ -110,6 +110,8 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
         lib.seqcdc_chunk_noalloc.restype = ctypes.c_int
         lib.seqcdc_status.argtypes = [vp, vp]
         lib.seqcdc_status.restype = ctypes.c_int
+        lib.seqcdc_copy_ranges.argtypes = [vp, vp, vp, vp, vp, u64, vp]
+        lib.seqcdc_copy_ranges.restype = ctypes.c_int
         lib.seqcdc_stats.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_uint32), u32]
         lib.seqcdc_stats.restype = ctypes.c_int
         lib.seqcdc_set_wait_limit_ns.argtypes = [u64]
@@ -236,6 +238,21 @@ def seqcdc_chunk_noalloc(p: Params, d_in, n: int, d_cuts, cap: int, d_count,
         ctypes.byref(p), _ptr(d_in), n, _ptr(d_cuts), cap, _ptr(d_count),
         _ptr(d_status), _tuning(tuning), _stream_handle(stream)),
         "seqcdc_chunk_noalloc")
+
+
+def seqcdc_copy_ranges(dst, src, dst_off, src_off, lens, stream=None) -> None:
+    """Raw entry point: copy ranges ``src[src_off[i]:+lens[i]]`` to
+    ``dst[dst_off[i]:]`` (tensors in device or pinned host memory; offsets
+    and lengths as host arrays), each as one async copy on ``stream``."""
+    import numpy as np
+    a = np.ascontiguousarray(dst_off, dtype=np.uint64)
+    b = np.ascontiguousarray(src_off, dtype=np.uint64)
+    c = np.ascontiguousarray(lens, dtype=np.uint64)
+    if not (a.size == b.size == c.size):
+        raise ValueError("seqcdc_copy_ranges: offset and length arrays differ in size")
+    _check(load_library().seqcdc_copy_ranges(
+        _ptr(dst), _ptr(src), a.ctypes.data, b.ctypes.data, c.ctypes.data, int(a.size),
+        _stream_handle(stream)), "seqcdc_copy_ranges")
 
 
 def seqcdc_status(d_ws, stream=None) -> int:

@@ -182,10 +182,12 @@ class Server:
         # The slot's previous batch has completed (it was popped as done), so
         # its staging and device buffers are free.
         s.h_offs[:nfiles + 1].copy_(torch.from_numpy(offs))
+        src_off = self.offs[np.fromiter((r.payload for r in reqs), dtype=np.int64,
+                                        count=nfiles)]
         with torch.cuda.stream(self.copy):
-            for r, o in zip(reqs, offs[:-1].tolist()):
-                src = self.pool[int(self.offs[r.payload]):int(self.offs[r.payload + 1])]
-                s.data[o:o + r.nbytes].copy_(src, non_blocking=True)
+            # every request's bytes into the slot, one async copy each,
+            # enqueued by the library in one call
+            seqcdc.seqcdc_copy_ranges(s.data, self.pool, offs[:-1], src_off, sizes, self.copy)
             s.offs[:nfiles + 1].copy_(s.h_offs[:nfiles + 1], non_blocking=True)
             copied = torch.cuda.Event()
             copied.record(self.copy)

@@ -100,6 +100,9 @@ def test_host_side_errors_before_launch(seqcdc_lib):
     assert lib.seqcdc_chunk_batch(P, fake, n, None, 1, fake, n, fake, fake, ws, None, None) == E.SEQCDC_EINVAL
     bad = E.Params(0, 1, 0, 0, 1, 1)
     assert lib.seqcdc_chunk(ctypes.byref(bad), fake, n, fake, n, fake, fake, ws, None, None) == E.SEQCDC_EINVAL
+    # range copies: NULL arrays or pointers with ranges to copy; nothing to copy is fine
+    assert lib.seqcdc_copy_ranges(fake, fake, None, None, None, 3, None) == E.SEQCDC_EINVAL
+    assert lib.seqcdc_copy_ranges(None, None, None, None, None, 0, None) == E.SEQCDC_OK
 
 
 def test_strerror(seqcdc_lib):
@@ -236,3 +239,25 @@ def test_chunk_batch_in_a_cuda_graph_with_profile_events(gpu):
         assert np.array_equal(cuts[:k].cpu().numpy(), ref.cuts.cpu().numpy())
         for i in range(2):
             assert evs[2 * i].elapsed_time(evs[2 * i + 1]) > 0.0
+
+
+@pytest.mark.gpu
+def test_copy_ranges_gathers_host_and_device_ranges(gpu):
+    """seqcdc_copy_ranges: ranges of a pinned host buffer gathered into a
+    device buffer in any order, including empty ranges, and back."""
+    import numpy as np
+    import torch
+    s = gpu
+    rng = np.random.default_rng(3)
+    pool = torch.from_numpy(rng.integers(0, 256, 1 << 20, dtype=np.uint8)).pin_memory()
+    lens = np.array([100, 0, 4096, 7, 65536, 1], dtype=np.uint64)
+    src = np.array([5, 17, 1000, 999_990, 200_000, 0], dtype=np.uint64)
+    dst = np.concatenate([[0], np.cumsum(lens)[:-1]]).astype(np.uint64)
+    d = torch.zeros(int(lens.sum()), dtype=torch.uint8, device="cuda")
+    st = torch.cuda.current_stream()
+    s.seqcdc_copy_ranges(d, pool, dst, src, lens, st)
+    back = torch.zeros(int(lens.sum()), dtype=torch.uint8).pin_memory()
+    s.seqcdc_copy_ranges(back, d, [0], [0], [int(lens.sum())], st)
+    st.synchronize()
+    want = np.concatenate([pool.numpy()[a:a + n] for a, n in zip(src.tolist(), lens.tolist())])
+    assert np.array_equal(back.numpy(), want)
