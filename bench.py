@@ -713,22 +713,6 @@ def run_gpu(args):
     if not args.no_serve or not args.no_dedup or not args.no_single:
         from paper_2505_21194_gb300 import workloads as W
         backup = W.backup_stream(SEED)
-    if not args.no_single:
-        ss = single_streams(dev, backup, peak, with_cfg5=not args.no_cfg5)
-        detail["single_stream"] = ss
-        for name, r in ss.items():
-            key = name.split("_")[0]
-            line["%s_GBs" % key] = r["GBs"]
-            line["%s_direct_GBs" % key] = r["direct_GBs"]
-            line["%s_path" % key] = r["path"]
-            line["%s_kernel_frac" % key] = r["frac"]
-            if "host_in_place" in r:
-                line["%s_host_in_place_GBs" % key] = r["host_in_place"]["GBs"]
-                line["%s_host_in_place_same_cuts" % key] = r["host_in_place"]["same_cuts"]
-            if "host_stream" in r:
-                line["%s_host_stream_GBs" % key] = r["host_stream"]["GBs"]
-                line["%s_host_h2d_copy_GBs" % key] = r["host_stream"]["h2d_copy_GBs"]
-                line["%s_host_stream_same_cuts" % key] = r["host_stream"]["same_cuts"]
     if not args.no_serve:
         # batches of a few ~16 MiB requests: the library's own choice per batch
         sv = serve_levels(dev, p, None, SERVE_LOADS_GBS, backup)
@@ -753,6 +737,22 @@ def run_gpu(args):
             line["serve_lognormal_%d_sustained_GBs" % g] = lv["sustained_GBs"]
         line["serve_lognormal_checked"] = sl["checked"]
         line["serve_lognormal_mismatches"] = sl["mismatches"]
+    if not args.no_single:
+        ss = single_streams(dev, backup, peak, with_cfg5=not args.no_cfg5)
+        detail["single_stream"] = ss
+        for name, r in ss.items():
+            key = name.split("_")[0]
+            line["%s_GBs" % key] = r["GBs"]
+            line["%s_direct_GBs" % key] = r["direct_GBs"]
+            line["%s_path" % key] = r["path"]
+            line["%s_kernel_frac" % key] = r["frac"]
+            if "host_in_place" in r:
+                line["%s_host_in_place_GBs" % key] = r["host_in_place"]["GBs"]
+                line["%s_host_in_place_same_cuts" % key] = r["host_in_place"]["same_cuts"]
+            if "host_stream" in r:
+                line["%s_host_stream_GBs" % key] = r["host_stream"]["GBs"]
+                line["%s_host_h2d_copy_GBs" % key] = r["host_stream"]["h2d_copy_GBs"]
+                line["%s_host_stream_same_cuts" % key] = r["host_stream"]["same_cuts"]
     if not args.no_dedup:
         dd = dedup_savings(dev, backup)
         sw = sweep_report(dev, backup)

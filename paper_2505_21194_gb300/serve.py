@@ -23,6 +23,7 @@ from __future__ import annotations
 
 import collections
 import dataclasses
+import gc
 import time
 from typing import Dict, Iterable, List, Optional, Sequence
 
@@ -210,7 +211,20 @@ class Server:
 
     # -- the serving loop --------------------------------------------------
     def run(self, arrivals: Iterable[Request], keep: Optional[set] = None,
-            poll_s: float = 50e-6) -> ServeStats:
+            poll_s: float = 0.0) -> ServeStats:
+        # The Python garbage collector is held off while serving: a full
+        # collection in a process with many live objects pauses the
+        # admission loop for tens to hundreds of milliseconds.
+        was_enabled = gc.isenabled()
+        gc.collect()
+        gc.disable()
+        try:
+            return self._run(arrivals, keep, poll_s)
+        finally:
+            if was_enabled:
+                gc.enable()
+
+    def _run(self, arrivals, keep, poll_s) -> ServeStats:
         torch = self.torch
         arrivals = sorted(arrivals, key=lambda r: r.arrival)
         keep = keep or set()
@@ -258,7 +272,9 @@ class Server:
                     inflight_bytes += b.nbytes
                     nbatches += 1
                     progressed = True
-            if not progressed:
+            if not progressed and poll_s > 0:
+                # (the default spins: a sleeping loop wakes up late on a busy
+                # host, and every wake-up is a request's latency)
                 time.sleep(poll_s)
         torch.cuda.synchronize(self.device)
         results = {}
