@@ -109,7 +109,7 @@ class _Batch:
     done: object          # CUDA event: the batch is chunked (latency ends here)
     ready: object         # CUDA event: its status word (and kept results) copied
     slot: int
-    kept: Optional[tuple]  # (cuts, cut offsets) device copies when a request is kept
+    kept: Optional[List[int]]  # places in the batch of the requests whose cuts are kept
 
 
 @dataclasses.dataclass
@@ -200,11 +200,7 @@ class Server:
             done.record(self.compute)
             # the batch's device status word (4 bytes back per batch)
             s.h_status.copy_(s.ws[:4].view(torch.int32), non_blocking=True)
-            kept = None
-            if any(r.rid in keep for r in reqs):
-                # requests the caller asked for: their cut lists stay on the
-                # device, copied out of the slot before it is reused
-                kept = (s.cuts[:max(cap, 1)].clone(), s.co[:nfiles + 1].clone())
+            kept = [j for j, r in enumerate(reqs) if r.rid in keep] or None
             ready = torch.cuda.Event()
             ready.record(self.compute)
         return _Batch(reqs, total, done, ready, k, kept)
@@ -231,8 +227,15 @@ class Server:
         queue: collections.deque = collections.deque()
         inflight: collections.deque = collections.deque()
         inflight_bytes = 0
-        lat, kept_batches = [], []
+        lat, results = [], {}
         nbatches, nbytes = 0, 0
+        # The cut lists the caller asks for stay on the device, in one buffer
+        # sized here for the requests kept (a request of n bytes has at most
+        # n / min_size + 1 cuts), so that the loop itself allocates nothing.
+        kept_cap = sum(r.nbytes // self.p.min_size + 1 for r in arrivals if r.rid in keep)
+        kept_buf = (torch.empty(kept_cap, dtype=torch.int64, device=self.device)
+                    if kept_cap else None)
+        kept_used = 0
         first_arrival = arrivals[0].arrival if arrivals else 0.0
         last_done = first_arrival
         torch.cuda.synchronize(self.device)
@@ -257,7 +260,18 @@ class Server:
                 if st != seqcdc.SEQCDC_OK:
                     raise seqcdc.SeqCDCError(st, "serve batch (device)")
                 if b.kept is not None:
-                    kept_batches.append(b)
+                    # copy the kept requests' cuts out of the slot before it
+                    # is reused (its next chunking is ordered after, on the
+                    # same stream)
+                    s = self._slots[b.slot]
+                    co_h = s.co[:len(b.reqs) + 1].cpu().numpy()
+                    with torch.cuda.stream(self.compute):
+                        for j in b.kept:
+                            a, e = int(co_h[j]), int(co_h[j + 1])
+                            dst = kept_buf[kept_used:kept_used + (e - a)]
+                            dst.copy_(s.cuts[a:e], non_blocking=True)
+                            results[b.reqs[j].rid] = dst
+                            kept_used += e - a
                 inflight_bytes -= b.nbytes
                 nbytes += b.nbytes
                 self._free.append(b.slot)
@@ -277,13 +291,6 @@ class Server:
                 # host, and every wake-up is a request's latency)
                 time.sleep(poll_s)
         torch.cuda.synchronize(self.device)
-        results = {}
-        for b in kept_batches:
-            cuts, co = b.kept
-            co_h = co.cpu().numpy()
-            for j, r in enumerate(b.reqs):
-                if r.rid in keep:
-                    results[r.rid] = cuts[int(co_h[j]):int(co_h[j + 1])]
         wall = max(last_done - first_arrival, 1e-9)
         return ServeStats(len(lat), nbatches, nbytes, wall, nbytes / wall / 1e9,
                           latency_stats(lat), results)

@@ -85,7 +85,8 @@ def test_server_results_equal_oracle_and_alone(gpu):
         assert got.is_cuda                       # cut lists stay on the device
         assert np.array_equal(got.cpu().numpy(), alone[r.payload]), r
     # Serving allocates nothing per batch: every buffer is in a slot made when
-    # the server was built (with no request kept, not even the result copies).
+    # the server was built, and kept cut lists go to one buffer made before
+    # the run's clock starts (none with no request kept).
     torch.cuda.synchronize()
     before = torch.cuda.memory_stats()["allocation.all.allocated"]
     st2 = srv.run(poisson_arrivals(400.0, 0.25, len(payloads), sizes, seed=5))
