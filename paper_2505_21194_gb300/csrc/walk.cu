@@ -29,6 +29,10 @@
 //             junctions in order from the first such piece.
 //   compact   count each piece's cuts, exclusive scan, copy to the caller's
 //             CSR output.
+// Input in pinned host memory is read in place over the host link; there the
+// bytes that cross bound the walk, and its chunk step (chunk_end_host) loads
+// 128 bytes at a time from each scan region's start instead of 1 KiB windows.
+//
 // Chains started at different positions meet after a few dozen chunks on
 // ordinary data, well within a piece.  In long stretches with no run ends
 // (constant bytes, where every cut is forced at max_size) they never meet,
@@ -100,6 +104,7 @@ struct WGeom {
   uint64_t nfiles;
   uint32_t P;               // piece bytes
   uint32_t fullcap;         // list entries of a full piece (P / min_size + 3)
+  uint32_t host;            // the data is pinned host memory read in place
 };
 
 struct WPtrs {
@@ -377,6 +382,10 @@ __device__ __forceinline__ Win load_win(const WGeom &g, uint64_t base) {
   return w;
 }
 
+template <uint32_t MODE, bool R5>
+__device__ uint64_t chunk_end_host(const WGeom &g, const DevParams &p, uint64_t c,
+                                   uint64_t fend, uint32_t &secs, bool &ok);
+
 // End of the chunk that starts at absolute byte c of a file ending at fend
 // (Sec. III.A-C, Sec. IV): the chunk limit is c + max_size (or the file end);
 // the scan starts min_size - SeqLength bytes in; a region ends at its first
@@ -388,13 +397,11 @@ __device__ __forceinline__ Win load_win(const WGeom &g, uint64_t base) {
 // the scan reaches it.  Lane l's word of a half holds the half's positions
 // 16 l .. 16 l + 15 in bits 0..15.  Positions are 32-bit offsets from the
 // first window's start.  Only the windows the scan reaches are read: with
-// many chains in flight per SM the loads' latency is hidden (an L2 prefetch
-// of the next chunk's likely window, 1-3 KiB, measured no faster and moved
-// three to four times the bytes).
-template <uint32_t MODE, bool R5>
-__device__ uint64_t chunk_end_host(const WGeom &g, const DevParams &p, uint64_t c,
-                                   uint64_t fend, uint32_t &secs, bool &ok);
-
+// many chains in flight per SM the loads' latency is hidden.  An L2 prefetch
+// of the next chunk's likely window on every chunk measured no faster and
+// moved three to four times the bytes, so it is taken (`pf`) only where the
+// walk waits on memory.  With LAZY (input in host memory) the chunk goes to
+// chunk_end_host instead.
 template <uint32_t MODE, bool R5, bool LAZY>
 __device__ uint64_t chunk_end_warp(const WGeom &g, const DevParams &p, uint64_t c,
                                    uint64_t fend, uint32_t &wins, bool &ok, bool pf = false) {
@@ -405,7 +412,7 @@ __device__ uint64_t chunk_end_warp(const WGeom &g, const DevParams &p, uint64_t 
     // cut is at least min_size on, its scan min_size - SeqLength after that),
     // so that its first window does not wait for HBM.  Used only where the
     // walk is bound by latency rather than issue: once no piece is left to
-    // take, and in the repairs (few warps).
+    // take, and in the repairs (few warps) of input in device memory.
     const uint64_t a = ((c + 2ull * p.mn - p.R) & ~127ull) + 128u * (uint32_t)lane;
     if (lane < 24 && a + 128u <= g.total)
       asm volatile("prefetch.global.L2 [%0];" ::"l"(g.data + a));
@@ -914,7 +921,7 @@ wrun_repair_kernel(WGeom g, DevParams p, WPtrs w, uint32_t round) {
         if (lane == 0) old = atomicMax(&w.claim[k], tag);
         if (__shfl_sync(kFull, old, 0) >= tag) break;  // another run's piece
       }
-      junction_walk<MODE, R5, false>(g, p, w, k, pc, x, nullptr, chunks, wins, ok, true);
+      junction_walk<MODE, R5, false>(g, p, w, k, pc, x, nullptr, chunks, wins, ok, !g.host);
       ++redone;
     }
   }
@@ -944,7 +951,7 @@ wrepair_kernel(WGeom g, DevParams p, WPtrs w) {
       const Piece pc = piece_of(g, w, p, k);
       const uint32_t x = exit_of(w, k - 1u, pc.lb - g.fullcap) - g.P;
       if (x == w.jin[k]) continue;
-      junction_walk<MODE, R5, false>(g, p, w, k, pc, x, nullptr, chunks, wins, ok, true);
+      junction_walk<MODE, R5, false>(g, p, w, k, pc, x, nullptr, chunks, wins, ok, !g.host);
       ++redone;
     }
   }
@@ -1166,7 +1173,7 @@ int run(const seqcdc_params_t *p, const uint8_t *d_data, uint64_t total,
   if (ws_bytes < l.total) return SEQCDC_ECAPACITY;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const WPtrs w = wptrs(d_ws, l);
-  const WGeom g{d_data, total, d_offsets, nfiles, l.P, l.fullcap};
+  const WGeom g{d_data, total, d_offsets, nfiles, l.P, l.fullcap, host_data ? 1u : 0u};
   const DevParams dp{p->mode, p->seq_length, p->skip_trigger, p->skip_size,
                      (uint32_t)p->min_size, (uint32_t)p->max_size};
   wplan_tiles_kernel<<<(unsigned)l.nftiles, 256, 0, st>>>(g, dp, w);

@@ -192,3 +192,25 @@ def test_host_in_place_tiny_and_ragged_streams(gpu):
         if n:
             dev = s.chunk(torch.from_numpy(data).cuda(), p).cpu().numpy()
             assert np.array_equal(dev, want), n
+
+
+@pytest.mark.gpu
+def test_host_in_place_other_seq_lengths_and_no_skipping(gpu):
+    """The host chunk step's general SeqLength path (not 5) and the path
+    without skipping (SkipTrigger 0): the same cuts as on the device and the
+    oracle's, in both modes."""
+    import torch
+    from paper_2505_21194_gb300.pipeline import HostInPlace
+    s = gpu
+    data = W.mixed_base(6 << 20, 13)
+    h = torch.from_numpy(data).pin_memory()
+    d = torch.from_numpy(data).cuda()
+    for mode in (0, 1):
+        for R, T, S in ((3, 40, 128), (8, 30, 256), (16, 0, 0), (5, 0, 0)):
+            p = s.Params(mode, R, T, S, 4096, 16384)
+            op = oracle.Params(mode, R, T, S, 4096, 16384)
+            want = oracle.chunk(data, op).astype(np.int64)
+            got = HostInPlace(p).run_stream(h)
+            assert np.array_equal(got, want), (mode, R, T, S)
+            walk = (0, 0, s.ALGO_WALK, 262144)
+            assert np.array_equal(s.chunk(d, p, walk).cpu().numpy(), want), (mode, R, T, S)
