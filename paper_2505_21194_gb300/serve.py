@@ -100,6 +100,7 @@ class _Slot:
     ws_bytes: int
     h_offs: object        # pinned staging for the offsets
     h_status: object      # pinned: the device status word of the slot's last batch
+    h_co: object          # pinned: the CSR index of the slot's last batch with kept requests
 
 
 @dataclasses.dataclass
@@ -166,7 +167,8 @@ class Server:
                              torch.empty(nf + 1, dtype=torch.int64, device=dev),
                              torch.empty(ws_bytes, dtype=torch.uint8, device=dev), ws_bytes,
                              torch.empty(nf + 1, dtype=torch.int64, pin_memory=True),
-                             torch.zeros(1, dtype=torch.int32, pin_memory=True))
+                             torch.zeros(1, dtype=torch.int32, pin_memory=True),
+                             torch.empty(nf + 1, dtype=torch.int64, pin_memory=True))
                        for _ in range(self.max_inflight)]
         self._free = list(range(self.max_inflight))
 
@@ -201,6 +203,10 @@ class Server:
             # the batch's device status word (4 bytes back per batch)
             s.h_status.copy_(s.ws[:4].view(torch.int32), non_blocking=True)
             kept = [j for j, r in enumerate(reqs) if r.rid in keep] or None
+            if kept is not None:
+                # the batch's CSR index comes back with the status word, so
+                # that taking the kept cut lists needs no synchronisation
+                s.h_co[:nfiles + 1].copy_(s.co[:nfiles + 1], non_blocking=True)
             ready = torch.cuda.Event()
             ready.record(self.compute)
         return _Batch(reqs, total, done, ready, k, kept)
@@ -264,7 +270,7 @@ class Server:
                     # is reused (its next chunking is ordered after, on the
                     # same stream)
                     s = self._slots[b.slot]
-                    co_h = s.co[:len(b.reqs) + 1].cpu().numpy()
+                    co_h = s.h_co[:len(b.reqs) + 1].numpy()  # written before `ready`
                     with torch.cuda.stream(self.compute):
                         for j in b.kept:
                             a, e = int(co_h[j]), int(co_h[j + 1])
