@@ -133,3 +133,21 @@ def test_ranges_on_the_library_equal_one_call(gpu):
             bufs = [d[slice(*ms.held_bytes(a, b, n, p))] for a, b in ranges]
             got, _ = ms.chunk_stream_ranges(bufs, ranges, n, p)
             assert np.array_equal(got, want), (mode, ranges)
+
+
+def test_ranges_shorter_than_max_size_equal_the_oracle():
+    """Ranges of a few KiB, below max_size: one chunk spans several ranges,
+    so a range is entered at or past its own end and passes that cut on."""
+    op = oracle.presets(8, 0)
+    rng = np.random.default_rng(9)
+    data = np.concatenate([rng.integers(0, 256, 150 * KIB, dtype=np.uint8),
+                           np.zeros(60 * KIB, dtype=np.uint8),
+                           rng.integers(0, 256, 50 * KIB + 3, dtype=np.uint8)])
+    n = data.size
+    want = oracle.chunk(data, op).astype(np.int64)
+    for world, align in ((20, 16), (37, 64), (64, 16)):
+        ranges = ms.split_ranges(n, world, align)
+        assert max(b - a for a, b in ranges) < op.max_size
+        bufs = [data[slice(*ms.held_bytes(a, b, n, op))] for a, b in ranges]
+        got, _ = ms.chunk_stream_ranges(bufs, ranges, n, op, _oracle_fn(op))
+        assert np.array_equal(got, want), world
