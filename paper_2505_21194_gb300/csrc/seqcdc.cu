@@ -60,7 +60,8 @@ constexpr uint32_t kCandPerLane = 3;  // chunk-step candidates per lane (map ker
 constexpr int kImgHash = 128;      // distinct-exit hash slots (power of two)
 constexpr int kMaxImage = 32;      // distinct exits published per item (one per lane)
 constexpr int kFileTile = 1024;    // files per plan block
-constexpr int kItemTile = 256;     // items per compaction block
+constexpr int kItemTile = 256;     // items per compaction tile
+constexpr int kEmitSplit = 8;      // emit blocks per compaction tile
 constexpr uint32_t kMaxSeqLength = 16;
 constexpr uint64_t kMaxMaxSize = 131072;
 constexpr uint64_t kWaitNs = SEQCDC_DEFAULT_WAIT_NS;  // default bound on a device wait
@@ -1294,6 +1295,9 @@ __global__ void count_tiles_kernel(WsPtrs ws) {
   }
 }
 
+// kEmitSplit blocks share each tile: every one scans the tile's counts and
+// copies kItemTile / kEmitSplit of its items, so that a short stream (a
+// tile or two) is not copied by one block.
 __global__ void emit_kernel(Geom g, WsPtrs ws, uint64_t *d_cuts, uint64_t cap,
                             uint64_t *d_cut_offsets, uint64_t *d_count) {
   __shared__ uint32_t scratch[32];
@@ -1301,9 +1305,10 @@ __global__ void emit_kernel(Geom g, WsPtrs ws, uint64_t *d_cuts, uint64_t cap,
   __shared__ uint64_t s_prefix;
   __shared__ uint32_t offs[kItemTile + 1];
   const uint32_t nitems = ws.hdr->nitems;
-  const uint64_t lo = (uint64_t)blockIdx.x * kItemTile;
+  const uint32_t tile = blockIdx.x / kEmitSplit, sub = blockIdx.x % kEmitSplit;
+  const uint64_t lo = (uint64_t)tile * kItemTile;
   uint64_t part = 0;
-  for (uint64_t t = threadIdx.x; t < blockIdx.x; t += blockDim.x) part += ws.itile[t];
+  for (uint64_t t = threadIdx.x; t < tile; t += blockDim.x) part += ws.itile[t];
   for (int d = 16; d; d >>= 1) part += __shfl_down_sync(0xffffffffu, part, d);
   if ((threadIdx.x & 31) == 0) red64[threadIdx.x >> 5] = part;
   __syncthreads();
@@ -1322,7 +1327,8 @@ __global__ void emit_kernel(Geom g, WsPtrs ws, uint64_t *d_cuts, uint64_t cap,
   __syncthreads();
   const uint64_t prefix = s_prefix;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int it = warp; it < kItemTile; it += blockDim.x >> 5) {
+  constexpr int kPerSub = kItemTile / kEmitSplit;
+  for (int it = sub * kPerSub + warp; it < (int)(sub + 1) * kPerSub; it += blockDim.x >> 5) {
     const uint64_t item = lo + it;
     if (item >= nitems) break;
     const uint32_t n = ws.count[item];
@@ -1335,9 +1341,10 @@ __global__ void emit_kernel(Geom g, WsPtrs ws, uint64_t *d_cuts, uint64_t cap,
     uint64_t *dst = d_cuts + at;
     for (uint32_t j = lane; j < n; j += 32) dst[j] = src[j];
   }
-  // CSR offsets of the files whose first item index falls in [lo, lo+tile).
+  // CSR offsets of the files whose first item index falls in [lo, lo+tile)
+  // (by the tile's first block).
   const uint64_t hi = lo + kItemTile;
-  if (lo <= nitems) {
+  if (sub == 0 && lo <= nitems) {
     uint64_t a = 0, b = g.nfiles + 1;  // lower_bound(seg_base, lo)
     while (a < b) {
       const uint64_t mid = (a + b) >> 1;
@@ -1669,7 +1676,7 @@ int run(const seqcdc_params_t *p, const uint8_t *d_data, uint64_t total,
   const uint64_t rcap = 4u * (uint64_t)sms;
   repair_kernel<<<(unsigned)(rblocks < rcap ? rblocks : rcap), threads, smem, st>>>(g, dp, w);
   count_tiles_kernel<<<(unsigned)l.nitiles, kItemTile, 0, st>>>(w);
-  emit_kernel<<<(unsigned)l.nitiles, kItemTile, 0, st>>>(g, w, d_cuts, cap,
+  emit_kernel<<<(unsigned)(l.nitiles * kEmitSplit), kItemTile, 0, st>>>(g, w, d_cuts, cap,
                                                           d_cut_offsets, d_count);
   return cudaGetLastError() == cudaSuccess ? SEQCDC_OK : SEQCDC_ECUDA;
 }
