@@ -151,3 +151,62 @@ def test_ranges_shorter_than_max_size_equal_the_oracle():
         bufs = [data[slice(*ms.held_bytes(a, b, n, op))] for a, b in ranges]
         got, _ = ms.chunk_stream_ranges(bufs, ranges, n, op, _oracle_fn(op))
         assert np.array_equal(got, want), world
+
+
+def _failing_rank_main(rank, world, port, q, how):
+    """Rank 1 fails between init and the exchange (``exit``: the process
+    ends; ``stall``: it never joins); rank 0 runs the exchange under a
+    5-second process-group timeout and reports what it got."""
+    import datetime
+    import time
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    from paper_2505_21194_gb300 import multistream as m
+    import oracle as orc
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world,
+                            timeout=datetime.timedelta(seconds=5))
+    if rank == 1:
+        if how == "exit":
+            os._exit(3)
+        time.sleep(15)
+        os._exit(4)
+    op = orc.presets(8, 0)
+    data = _stream(3)
+    n = data.size
+    a, b = m.split_ranges(n, world, 4096)[0]
+    buf = data[slice(*m.held_bytes(a, b, n, op))]
+    t0 = time.monotonic()
+    try:
+        m.chunk_stream_distributed(buf, a, b, n, op, _oracle_fn(op), device="cpu")
+        q.put(("returned", "", time.monotonic() - t0))
+    except Exception as e:  # the failure must surface as an exception
+        q.put(("raised", type(e).__name__, time.monotonic() - t0))
+    q.close()
+    q.join_thread()
+    os._exit(0)
+
+
+@pytest.mark.parametrize("how", ["exit", "stall"])
+def test_a_failed_rank_ends_the_exchange_with_an_error(how):
+    """A rank that exits, or stalls, before the exchange of exits: the other
+    rank's exchange ends with an exception within the process group's
+    timeout instead of waiting forever, and no cut list is returned."""
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_failing_rank_main, args=(r, 2, port, q, how))
+             for r in range(2)]
+    for pr in procs:
+        pr.start()
+    try:
+        kind, name, secs = q.get(timeout=150)
+    finally:
+        for pr in procs:
+            pr.join(timeout=60)
+            if pr.is_alive():
+                pr.kill()
+                pr.join()
+    assert kind == "raised", (kind, name)
+    assert secs < 60, secs
+    assert procs[0].exitcode == 0
