@@ -9,7 +9,8 @@
  * opposite order have been seen, the next SkipSize bytes are skipped,
  * Sec. III.C.  A chunk is cut at max_size when no run completes first,
  * Sec. IV and Sec. VI.  This library computes exactly the boundary list a
- * sequential scan produces, with CUDA kernels over device-resident bytes.
+ * sequential scan produces, with CUDA kernels over bytes in device memory
+ * (or in pinned host memory, read in place over the host link).
  * It has two paths with the same output (see seqcdc_tuning_t.algorithm):
  * a segment map that classifies every byte and resolves the chunk chain
  * across segments, and a chain walk that follows the chain one chunk after
@@ -18,7 +19,8 @@
  *
  * Conventions for every entry point:
  *   - "d_" pointers are CUDA device pointers (or managed memory) that the
- *     caller allocated and owns.  The library never allocates, never frees
+ *     caller allocated and owns; the chunking calls also take mapped pinned
+ *     host memory for their input and outputs (seqcdc_chunk).  The library never allocates, never frees
  *     and never synchronises the stream, except seqcdc_status() (which
  *     synchronises on purpose).  All work is enqueued on `stream` (a
  *     cudaStream_t passed as void*; NULL = the legacy default stream).
@@ -166,9 +168,9 @@ int seqcdc_algorithm(const seqcdc_params_t *p, uint64_t total_bytes, uint64_t nf
  *            GB300 node every pinned allocation is), which the kernels then
  *            read in place over the host link: AUTO takes the chain walk for
  *            such input when the workspace allows it, and the walk loads
- *            only the 16-byte words of a window from its scan region's start
- *            on, when the scan reaches them, so only a fraction of the bytes
- *            cross (Sec. III.B-C skip the rest).
+ *            a window 128 bytes at a time from its scan region's start, as
+ *            far as the scan reaches, so only a fraction of the bytes cross
+ *            (Sec. III.B-C skip the rest).
  *            Pageable host memory gives SEQCDC_EINVAL (after the size
  *            checks, before any launch).  16-byte aligned.
  *   d_cuts   out: up to `cap` uint64 chunk end offsets (device memory, or
