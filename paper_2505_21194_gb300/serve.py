@@ -63,6 +63,51 @@ def form_batch(queue: Sequence[Request], inflight_bytes: int, budget: int,
     return take
 
 
+def withdraw(queue, withdrawn) -> int:
+    """Remove from ``queue`` (a deque of requests; in place, order kept)
+    every request whose id is in ``withdrawn``; return how many went."""
+    stay = [r for r in queue if r.rid not in withdrawn]
+    gone = len(queue) - len(stay)
+    if gone:
+        queue.clear()
+        queue.extend(stay)
+    return gone
+
+
+class Cancellations:
+    """Client cancellations of a run: request id -> the time (seconds from
+    the start, like arrivals) at which the client withdraws the request.
+
+    ``tick(now, queue, narrived)`` is called by the serving loop after the
+    arrivals up to ``now`` (``narrived`` of them so far) have joined
+    ``queue``: every request whose cancellation time has come and that is
+    still queued, or arrives later, is removed before admission.  A request
+    admitted before its cancellation runs to completion; ``too_late`` counts
+    those."""
+
+    def __init__(self, cancels: Optional[Dict[int, float]] = None):
+        self.at = sorted((float(t), int(rid)) for rid, t in (cancels or {}).items())
+        self.rids = {rid for _, rid in self.at}
+        self.withdrawn: set = set()
+        self.next = self.seen = self.cancelled = 0
+
+    def __bool__(self) -> bool:
+        return bool(self.at)
+
+    def tick(self, now: float, queue, narrived: int) -> None:
+        grew = False
+        while self.next < len(self.at) and self.at[self.next][0] <= now:
+            self.withdrawn.add(self.at[self.next][1])
+            self.next += 1
+            grew = True
+        if self.withdrawn and (grew or narrived > self.seen):
+            self.cancelled += withdraw(queue, self.withdrawn)
+        self.seen = narrived
+
+    def too_late(self, arrivals: Sequence[Request]) -> int:
+        return sum(1 for r in arrivals if r.rid in self.rids) - self.cancelled
+
+
 def latency_stats(lat_s: Sequence[float]) -> Dict[str, float]:
     """p50 / p99 / mean / max of latencies given in seconds, in milliseconds."""
     a = np.asarray(lat_s, dtype=np.float64) * 1e3
@@ -122,6 +167,8 @@ class ServeStats:
     sustained_gbs: float
     latency: Dict[str, float]
     results: Dict[int, object]      # cut lists (device tensors) of the requests asked for
+    cancelled: int = 0              # requests withdrawn before admission (never chunked)
+    cancel_too_late: int = 0        # cancellations that came after admission (served)
 
 
 class Server:
@@ -213,7 +260,13 @@ class Server:
 
     # -- the serving loop --------------------------------------------------
     def run(self, arrivals: Iterable[Request], keep: Optional[set] = None,
-            poll_s: float = 0.0) -> ServeStats:
+            poll_s: float = 0.0, cancels: Optional[Dict[int, float]] = None) -> ServeStats:
+        """Serve ``arrivals``; keep the cut lists of the request ids in
+        ``keep``.  ``cancels`` maps request ids to the time (seconds from the
+        start, like arrivals) at which their client withdraws them: a request
+        still queued then (or not yet arrived) is dropped without being
+        chunked; one already admitted runs to completion, and the
+        cancellation is counted as too late."""
         # The Python garbage collector is held off while serving: a full
         # collection in a process with many live objects pauses the
         # admission loop for tens to hundreds of milliseconds.
@@ -221,12 +274,12 @@ class Server:
         gc.collect()
         gc.disable()
         try:
-            return self._run(arrivals, keep, poll_s)
+            return self._run(arrivals, keep, poll_s, cancels)
         finally:
             if was_enabled:
                 gc.enable()
 
-    def _run(self, arrivals, keep, poll_s) -> ServeStats:
+    def _run(self, arrivals, keep, poll_s, cancels=None) -> ServeStats:
         torch = self.torch
         arrivals = sorted(arrivals, key=lambda r: r.arrival)
         keep = keep or set()
@@ -242,6 +295,7 @@ class Server:
         kept_buf = (torch.empty(kept_cap, dtype=torch.int64, device=self.device)
                     if kept_cap else None)
         kept_used = 0
+        cancel = Cancellations(cancels)
         first_arrival = arrivals[0].arrival if arrivals else 0.0
         last_done = first_arrival
         torch.cuda.synchronize(self.device)
@@ -255,6 +309,8 @@ class Server:
             while i < len(arrivals) and arrivals[i].arrival <= now:
                 queue.append(arrivals[i])
                 i += 1
+            if cancel:
+                cancel.tick(now, queue, i)
             progressed = False
             while inflight and inflight[0].ready.query():
                 b = inflight.popleft()
@@ -299,4 +355,5 @@ class Server:
         torch.cuda.synchronize(self.device)
         wall = max(last_done - first_arrival, 1e-9)
         return ServeStats(len(lat), nbatches, nbytes, wall, nbytes / wall / 1e9,
-                          latency_stats(lat), results)
+                          latency_stats(lat), results, cancel.cancelled,
+                          cancel.too_late(arrivals))

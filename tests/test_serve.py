@@ -12,8 +12,8 @@ import pytest
 
 import oracle
 from paper_2505_21194_gb300 import workloads as W
-from paper_2505_21194_gb300.serve import (Request, form_batch, latency_stats,
-                                          poisson_arrivals)
+from paper_2505_21194_gb300.serve import (Cancellations, Request, form_batch, latency_stats,
+                                          poisson_arrivals, withdraw)
 
 
 def _reqs(sizes):
@@ -52,6 +52,63 @@ def test_poisson_arrivals_rate_and_order():
     assert gaps.mean() == pytest.approx(1 / 2000.0, rel=0.05)
     assert all(r.nbytes == sizes[r.payload] for r in a)
     assert [r.rid for r in a] == list(range(len(a)))
+
+
+def test_withdraw_keeps_order():
+    import collections
+    q = collections.deque(_reqs([1, 2, 3, 4, 5]))
+    assert withdraw(q, {1, 3, 9}) == 2
+    assert [r.rid for r in q] == [0, 2, 4]
+    assert withdraw(q, set()) == 0 and len(q) == 3
+
+
+def test_cancellations_in_a_simulated_serving_loop():
+    """The serving loop's order on a host-only model of the device
+    (arrivals join the queue, cancellations are applied, finished batches
+    leave, the next batch is admitted; one batch in flight, each taking a
+    fixed time): every request is either served once or cancelled, never
+    both; a cancelled request was never admitted and its time had come; a
+    served request with a cancellation was admitted before it."""
+    import collections
+    rng = np.random.default_rng(5)
+    sizes = rng.integers(1, 100, 400)
+    arrivals = poisson_arrivals(2000.0, 0.2, len(sizes), sizes, seed=6)
+    cancels = {r.rid: r.arrival + float(rng.uniform(-0.002, 0.01))
+               for r in arrivals if rng.random() < 0.3}
+    cancels[10 ** 6] = 0.05            # an id that never arrives changes nothing
+    cancel = Cancellations(cancels)
+    queue, admitted_at, served = collections.deque(), {}, []
+    i, now, busy_until, inflight = 0, 0.0, -1.0, []
+    removed_at = {}
+    while i < len(arrivals) or queue or inflight:
+        while i < len(arrivals) and arrivals[i].arrival <= now:
+            queue.append(arrivals[i])
+            i += 1
+        before = {r.rid for r in queue}
+        cancel.tick(now, queue, i)
+        for rid in before - {r.rid for r in queue}:
+            removed_at[rid] = now
+        if inflight and now >= busy_until:
+            served += inflight
+            inflight = []
+        if queue and not inflight:
+            k = form_batch(queue, 0, budget=10 ** 9, max_batch_bytes=500)
+            inflight = [queue.popleft() for _ in range(k)]
+            for r in inflight:
+                admitted_at[r.rid] = now
+            busy_until = now + 0.003
+        now = round(now + 0.0005, 7)
+    served_ids = [r.rid for r in served]
+    assert len(served_ids) == len(set(served_ids))
+    assert set(served_ids).isdisjoint(removed_at)
+    assert set(served_ids) | set(removed_at) == {r.rid for r in arrivals}
+    for rid, t in removed_at.items():
+        assert rid not in admitted_at and cancels[rid] <= t
+    late = [rid for rid in served_ids if rid in cancels]
+    assert all(admitted_at[rid] < cancels[rid] for rid in late)
+    assert cancel.cancelled == len(removed_at) > 0
+    assert cancel.too_late(arrivals) == len(late) > 0
+    assert not Cancellations(None) and not Cancellations({})
 
 
 @pytest.mark.gpu
@@ -93,3 +150,38 @@ def test_server_results_equal_oracle_and_alone(gpu):
     torch.cuda.synchronize()
     assert st2.batches > 0 and st2.results == {}
     assert torch.cuda.memory_stats()["allocation.all.allocated"] == before
+
+
+@pytest.mark.gpu
+def test_server_cancellations(gpu):
+    """Requests whose client cancels them before the run starts are never
+    chunked and have no result; requests cancelled only after the run ends
+    were admitted first, so they are served (cut lists equal to the
+    oracle's) and their cancellations are counted as too late."""
+    import torch
+    from paper_2505_21194_gb300.serve import Server
+    s = gpu
+    p = s.seqcdc_params(8, 0)
+    op = oracle.presets(8)
+    rng = np.random.default_rng(8)
+    sizes = rng.integers(1, 2 << 20, 8)
+    payloads = [W.mixed_base(int(n), 200 + k, block=4096) for k, n in enumerate(sizes)]
+    offs = np.zeros(len(payloads) + 1, dtype=np.int64)
+    np.cumsum(sizes, out=offs[1:])
+    pool = torch.from_numpy(np.concatenate(payloads)).pin_memory()
+    srv = Server(p, pool, offs, budget_bytes=64 << 20, max_batch_bytes=16 << 20)
+    arr = poisson_arrivals(400.0, 0.1, len(payloads), sizes, seed=9)
+    early = {r.rid for r in arr[::3]}
+    late = {r.rid for r in arr[1::3]}
+    assert early and late
+    cancels = {rid: -1.0 for rid in early}
+    cancels.update({rid: 1e9 for rid in late})
+    st = srv.run(arr, keep={r.rid for r in arr}, cancels=cancels)
+    assert st.cancelled == len(early) and st.cancel_too_late == len(late)
+    assert st.requests == len(arr) - len(early)
+    assert st.bytes == sum(r.nbytes for r in arr if r.rid not in early)
+    assert set(st.results) == {r.rid for r in arr} - early
+    want = {k: oracle.chunk(b, op).astype(np.int64) for k, b in enumerate(payloads)}
+    for r in arr:
+        if r.rid not in early:
+            assert np.array_equal(st.results[r.rid].cpu().numpy(), want[r.payload]), r
