@@ -296,6 +296,7 @@ class Server:
                     if kept_cap else None)
         kept_used = 0
         cancel = Cancellations(cancels)
+        cancelling = bool(cancel)
         first_arrival = arrivals[0].arrival if arrivals else 0.0
         last_done = first_arrival
         torch.cuda.synchronize(self.device)
@@ -309,7 +310,7 @@ class Server:
             while i < len(arrivals) and arrivals[i].arrival <= now:
                 queue.append(arrivals[i])
                 i += 1
-            if cancel:
+            if cancelling:
                 cancel.tick(now, queue, i)
             progressed = False
             while inflight and inflight[0].ready.query():
