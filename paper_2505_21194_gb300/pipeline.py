@@ -30,7 +30,7 @@ orders streams.
 from __future__ import annotations
 
 import collections
-from typing import Iterable, Iterator, List, Optional, Tuple
+from typing import Iterable, Iterator, List, Tuple
 
 import numpy as np
 

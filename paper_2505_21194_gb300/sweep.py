@@ -12,9 +12,7 @@ the run length (bytes or comparisons) gives Table I's targets on that data.
 """
 from __future__ import annotations
 
-from typing import Dict, Iterable, List, Optional, Tuple
-
-import numpy as np
+from typing import Dict, Iterable, List, Tuple
 
 from . import seqcdc
 
